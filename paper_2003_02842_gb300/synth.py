@@ -1,0 +1,218 @@
+"""Seeded synthetic event data shaped like the paper's workloads.
+
+This module only draws inputs: correlated geometric Brownian motions
+(Algorithm 1, Sec. 3 Eq. (16)) observed synchronously or at Poisson arrival
+times (Sec. 3, "arrival time representation"). It holds none of the
+estimator's arithmetic, and both the GPU library's tests and the CPU oracle
+consume exactly the arrays it returns.
+
+Every workload is returned in CSR form: ``offsets`` (int64, D+1),
+``t`` (float64 event times in seconds, strictly increasing per asset) and
+``logp`` (float64 log-prices at those times).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SECONDS_PER_DAY = 86400.0
+BASE_SEED = 20032842
+
+
+@dataclass
+class Events:
+    offsets: np.ndarray
+    t: np.ndarray
+    logp: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def D(self) -> int:
+        return len(self.offsets) - 1
+
+    @property
+    def n_events(self) -> int:
+        return int(self.offsets[-1])
+
+    def counts(self) -> np.ndarray:
+        return np.diff(self.offsets)
+
+    def asset(self, i):
+        a, b = self.offsets[i], self.offsets[i + 1]
+        return self.t[a:b], self.logp[a:b]
+
+
+def rng_for(*stream) -> np.random.Generator:
+    """Philox counter-based generator keyed by (base seed, stream ids)."""
+    key = [BASE_SEED] + [int(s) for s in stream]
+    return np.random.Generator(np.random.Philox(np.random.SeedSequence(key)))
+
+
+def from_lists(ts, ps) -> Events:
+    offs = np.zeros(len(ts) + 1, dtype=np.int64)
+    offs[1:] = np.cumsum([len(x) for x in ts])
+    t = np.concatenate([np.asarray(x, np.float64) for x in ts]) if ts else np.zeros(0)
+    p = np.concatenate([np.asarray(x, np.float64) for x in ps]) if ps else np.zeros(0)
+    return Events(offs, t, p)
+
+
+def gbm_grid(n, mu, cov_daily, rng, s0=100.0, dt_days=1.0 / SECONDS_PER_DAY):
+    """Algorithm 1: log S_{k+1} = log S_k + (mu - sigma^2/2) dt + sqrt(dt) A Z,
+    A the Cholesky factor of the daily covariance; n synchronous points
+    (times 0, 1, ..., n-1 seconds). Returns an (n, D) array of log-prices."""
+    cov = np.asarray(cov_daily, np.float64)
+    D = cov.shape[0]
+    mu = np.broadcast_to(np.asarray(mu, np.float64), (D,))
+    A = np.linalg.cholesky(cov)
+    Z = rng.standard_normal((n - 1, D))
+    inc = (mu - 0.5 * np.diag(cov)) * dt_days + np.sqrt(dt_days) * Z @ A.T
+    logp = np.empty((n, D))
+    logp[0] = np.log(s0)
+    logp[1:] = np.log(s0) + np.cumsum(inc, axis=0)
+    return logp
+
+
+def bivariate_cov(var1=0.1, var2=0.2, rho=0.35):
+    c = rho * np.sqrt(var1 * var2)
+    return np.array([[var1, c], [c, var2]])
+
+
+def poisson_grid_sample(n_grid, rate, rng):
+    """Arrival-time asynchrony on a 1-s grid: exponential inter-arrival times
+    with the given rate, each arrival moved up to the next grid second (never
+    into the past), repeated seconds merged. Returns sorted grid indices."""
+    mean_n = rate * n_grid
+    m = int(mean_n + 10 * np.sqrt(mean_n + 1) + 20)
+    arr = np.cumsum(rng.exponential(1.0 / rate, size=m))
+    while arr[-1] < n_grid - 1:
+        arr = np.concatenate([arr, arr[-1] + np.cumsum(rng.exponential(1.0 / rate, size=m))])
+    idx = np.ceil(arr[arr <= n_grid - 1]).astype(np.int64)
+    return np.unique(idx)
+
+
+def c1_sync(seed=0, n=1000):
+    """D=2 synchronous correlated GBM (mu = 0.01, sigma^2 = 0.1, 0.2,
+    rho = 0.35, dt = 1 s), n equally spaced times 0..n-1 s."""
+    rng = rng_for(1, seed)
+    lp = gbm_grid(n, 0.01, bivariate_cov(), rng)
+    t = np.arange(n, dtype=np.float64)
+    ev = from_lists([t, t], [lp[:, 0], lp[:, 1]])
+    ev.meta = {"workload": "c1_sync_gbm_D2_n1000", "N": n // 2}
+    return ev
+
+
+def c2_async(seed=0, T=28800, rates=(1 / 15, 1 / 20)):
+    """D=2 GBM on the 1-s grid over T seconds, each asset observed at Poisson
+    arrival times with the given rates; N = floor(min n / 2)."""
+    rng = rng_for(2, seed)
+    lp = gbm_grid(T, 0.01, bivariate_cov(), rng)
+    ts, ps = [], []
+    for j, r in enumerate(rates):
+        idx = poisson_grid_sample(T, r, rng)
+        ts.append(idx.astype(np.float64))
+        ps.append(lp[idx, j])
+    ev = from_lists(ts, ps)
+    ev.meta = {"workload": "c2_async_gbm_D2", "N": int(min(len(x) for x in ts) // 2)}
+    return ev
+
+
+def _continuous_poisson(T, rate, rng):
+    n = rng.poisson(rate * T)
+    return np.sort(rng.uniform(0.0, T, size=n))
+
+
+def block_factor_gbm(times_per_asset, sig2, mu, block_of, rho_in, rho_out, rng, s0=100.0):
+    """Correlated GBM observed at arbitrary (continuous) per-asset times, exact
+    in law: log p_i(t) = log s0 + (mu - sig2_i/2) t + sigma_i W_i(t) with
+    W_i = sqrt(rho_out) G + sqrt(rho_in - rho_out) B_block(i) + sqrt(1 - rho_in) E_i
+    (G, B_b, E_i independent Brownian motions; t in days). Pairwise correlation
+    rho_in inside a block and rho_out across blocks."""
+    D = len(times_per_asset)
+    nb = int(max(block_of)) + 1
+    allt = np.unique(np.concatenate([x for x in times_per_asset if len(x)] + [np.zeros(1)]))
+    days = allt / SECONDS_PER_DAY
+    dtd = np.diff(days, prepend=0.0)
+    sq = np.sqrt(dtd)[:, None]
+    G = np.cumsum(rng.standard_normal((len(allt), 1)) * sq, axis=0)[:, 0]
+    B = np.cumsum(rng.standard_normal((len(allt), nb)) * sq, axis=0)
+    ts, ps = [], []
+    for i in range(D):
+        ti = np.asarray(times_per_asset[i], np.float64)
+        pos = np.searchsorted(allt, ti)
+        di = ti / SECONDS_PER_DAY
+        ddi = np.diff(di, prepend=0.0)
+        E = np.cumsum(rng.standard_normal(len(ti)) * np.sqrt(ddi))
+        W = (np.sqrt(rho_out) * G[pos] + np.sqrt(max(rho_in - rho_out, 0.0)) * B[pos, block_of[i]]
+             + np.sqrt(1.0 - rho_in) * E)
+        s = np.sqrt(sig2[i])
+        ps.append(np.log(s0) + (mu - 0.5 * sig2[i]) * di + s * W)
+        ts.append(ti)
+    return ts, ps
+
+
+def c3_block(seed=0, D=100, T=28800.0, N=10000, n_blocks=10, rho_in=0.5, rho_out=0.1,
+             sig2_range=(0.05, 0.3), rate_range=(1 / 60, 1 / 2)):
+    """D correlated GBM assets with block correlation (n_blocks blocks, intra
+    rho_in, inter rho_out), sigma^2 ~ U(sig2_range), each observed at
+    continuous-time Poisson arrivals with rate ~ U(rate_range) per second over
+    T seconds."""
+    rng = rng_for(3, seed)
+    sig2 = rng.uniform(*sig2_range, size=D)
+    rates = rng.uniform(*rate_range, size=D)
+    block_of = np.arange(D) * n_blocks // D
+    times = [_continuous_poisson(T, r, rng) for r in rates]
+    ts, ps = block_factor_gbm(times, sig2, 0.01, block_of, rho_in, rho_out, rng)
+    ev = from_lists(ts, ps)
+    ev.meta = {"workload": f"c3_block_gbm_D{D}_N{N}", "N": N, "T": T,
+               "rates": rates, "sig2": sig2}
+    return ev
+
+
+def batch_replications(seed, reps, D=10, T=28800.0, rho=0.35, sig2_range=(0.1, 0.2),
+                       median_n=2000, sdlog=1.0, clip=(100, 50000)):
+    """Monte Carlo replications of D equicorrelated GBM assets; per-asset event
+    counts lognormal (median median_n, log-sd sdlog) clipped to `clip`, event
+    times uniform order statistics on [0, T] (a Poisson process given its
+    count). Returns one Events per replication."""
+    out = []
+    for r in range(reps):
+        rng = rng_for(4, seed, r)
+        sig2 = rng.uniform(*sig2_range, size=D)
+        n = np.clip(np.round(np.exp(np.log(median_n) + sdlog * rng.standard_normal(D))),
+                    clip[0], clip[1]).astype(np.int64)
+        times = [np.sort(rng.uniform(0.0, T, size=k)) for k in n]
+        ts, ps = block_factor_gbm(times, sig2, 0.01, np.zeros(D, np.int64), rho, rho, rng)
+        ev = from_lists(ts, ps)
+        ev.meta = {"rep": r}
+        out.append(ev)
+    return out
+
+
+def random_events(seed, D, n_range=(2, 50), T=1000.0, grid=None, scale=1e-2):
+    """Small random test inputs: per-asset event counts uniform in n_range,
+    times uniform on [0, T] (or distinct grid points if grid is an integer),
+    log-prices a random walk with step sd `scale`."""
+    rng = rng_for(9, seed)
+    ts, ps = [], []
+    for _ in range(D):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        if grid:
+            t = np.sort(rng.choice(grid, size=min(n, grid), replace=False)).astype(np.float64)
+        else:
+            t = np.sort(rng.uniform(0.0, T, size=n))
+        p = 4.6 + np.cumsum(scale * rng.standard_normal(len(t)))
+        ts.append(t)
+        ps.append(p)
+    return from_lists(ts, ps)
+
+
+def concat_events(evs):
+    """Stack several Events into one CSR set (replications side by side)."""
+    ts, ps = [], []
+    for ev in evs:
+        for i in range(ev.D):
+            a, b = ev.asset(i)
+            ts.append(a)
+            ps.append(b)
+    return from_lists(ts, ps)
