@@ -1,0 +1,388 @@
+"""Benchmark of the GB300 Malliavin-Mancino NUFFT covariance library.
+
+One step = the whole hot path on one synthetic problem already resident in
+HBM: time rescaling and returns (FP64), spreading, two-pass FFT with
+deconvolution, split-K contraction and correlation (mm_estimate). The default
+workload is the precision form: D = 100 block-correlated GBM assets observed at
+Poisson arrivals (rates U[1/60, 1/2] per second over 28,800 s, about 7.4e5
+events), N = 10,000, exponential-of-semicircle kernel at tol 1e-6, Dirichlet
+basis, split-bf16 contraction. The FP64 GPU path runs on the same inputs and
+the largest |dR| between the two is reported.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs its own replica (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "events/sec (NUFFT coeffs) & D×D corr matrices/sec vs FP64 GPU path at max|Δcorr|≤1e-4"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+# dram bytes (read + write) per launch of the dominant kernel, from the ncu
+# capture summarised in profiles/ (None until a capture of the current kernel)
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1"])
+    ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "3xtf32", "fp64"])
+    ap.add_argument("--kernel", default="es", choices=["gauss", "kb", "es"])
+    ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison path")
+    return ap.parse_args()
+
+
+def workload(name, seed):
+    from paper_2003_02842_gb300 import synth
+    if name == "c3":
+        ev = synth.c3_block(seed)
+        N = 10000
+    elif name == "c2":
+        ev = synth.c2_async(seed)
+        N = ev.meta["N"]
+    else:
+        ev = synth.c1_sync(seed)
+        N = 500
+    return ev, N
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return FALLBACK_PEAKS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as f:
+            for line in f:
+                c = [x.strip() for x in line.split(",")]
+                if len(c) >= 10:
+                    rows.append(c)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        load = [r for r in rows if num(r[4]) > 0] or rows
+        sm = [num(r[1]) for r in load]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in load:
+            for nm, v in zip(names, r[6:10]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.nanmedian(sm)), "sm_max_mhz": num(load[0][2]), "reasons": sorted(reasons),
+                "samples": len(rows), "samples_under_load": len(load)}
+
+
+def oracle_rate(ev, N, budget_s, offset=0):
+    """Time the oracle's direct sum of Eq. (4) (k = 0..N) on whole assets, one
+    after another from `offset`, until `budget_s` of wall time is spent.
+    Returns (events processed, seconds, assets, threads)."""
+    import oracle
+    roff, rt, rd = oracle.returns(ev.offsets, ev.t, ev.logp)
+    t0, t1 = oracle.bounds(ev.offsets, ev.t)
+    done, secs, assets = 0, 0.0, 0
+    D = ev.D
+    i = offset
+    while secs < budget_s and assets < D:
+        a, b = roff[i % D], roff[i % D + 1]
+        n_ev = int(ev.offsets[i % D + 1] - ev.offsets[i % D])
+        if b > a:
+            # bound one call to ~budget: take a block of modes if the asset is big
+            per_mode = (b - a) * 6e-8 / max(oracle.num_threads(), 1)
+            kmax = int(min(N, max(64, (budget_s - secs) / max(per_mode, 1e-12))))
+            s = time.perf_counter()
+            oracle.coeffs(rt[a:b], rd[a:b], t0, t1 - t0, 0, kmax)
+            secs += time.perf_counter() - s
+            done += n_ev * (kmax + 1) / (N + 1)
+        assets += 1
+        i += 1
+    return done, secs, assets, oracle.num_threads()
+
+
+def reference_arm(args):
+    """--impl reference: the CPU oracle timed on the machine's host cores, each step
+    a bounded sample of the same workload (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    ev, N = workload(args.workload, 0)
+    import oracle
+    oracle.build()
+    per_step = max(0.01, min(2.0, 150.0 / max(args.steps + args.warmup, 1)))
+    for w in range(args.warmup):
+        oracle_rate(ev, N, per_step, offset=w)
+    tot_ev, tot_s = 0.0, 0.0
+    assets = 0
+    for k in range(args.steps):
+        e, s, a, threads = oracle_rate(ev, N, per_step, offset=k)
+        tot_ev += e
+        tot_s += s
+        assets += a
+    value = tot_ev / tot_s if tot_s > 0 else 0.0
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded GBM / Poisson arrivals)",
+        "config": {"workload": ev.meta.get("workload", args.workload), "D": ev.D, "N": N,
+                   "events": ev.n_events},
+        "cpu_baseline": {"value": value, "unit": "events/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"direct sum of Eq. (4) for k=0..N on {assets} asset samples "
+                                   f"(~{per_step:.2f} s each step), scaled to events/s at N={N}"},
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__ as g
+    g.build()
+    import paper_2003_02842_gb300 as mm
+
+    ev, N = workload(args.workload, seed=rank)
+    off = torch.from_numpy(ev.offsets).to(dev)
+    tt = torch.from_numpy(ev.t).to(dev)
+    lp = torch.from_numpy(ev.logp).to(dev)
+    D = ev.D
+    tol = 1e-12 if args.prec == "fp64" else 1e-6
+    plan = mm.mm_plan_create(D=D, N_max=N, max_events=ev.n_events, tol=tol, kernel=args.kernel,
+                             basis="dirichlet", prec=args.prec)
+    coef = torch.empty((D, N + 1), dtype=torch.complex128 if args.prec == "fp64" else torch.complex64, device=dev)
+    rdt = torch.float64 if args.prec == "fp64" else torch.float32
+    S = torch.empty((D, D), dtype=rdt, device=dev)
+    R = torch.empty((D, D), dtype=rdt, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        mm.mm_estimate(plan, off, tt, lp, N, coeffs=coef, sigma=S, R=R)
+
+    # first call builds the per-cutoff tables; then check the status
+    step()
+    st = mm.mm_plan_sync(plan)
+    if st != 0:
+        raise SystemExit(f"bench workload returned status {mm.mm_status_string(st)}")
+
+    with ClockSampler(dev.index) as clk:
+        for _ in range(args.warmup):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+        launches0 = mm.mm_plan_get_info(plan)["launches"]
+        mm.mm_profile_read(plan, reset=True)
+        mm.mm_profile_enable(plan, True)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record()
+            step()
+            ends[k].record()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        mm.mm_profile_enable(plan, False)
+        launches = mm.mm_plan_get_info(plan)["launches"] - launches0
+        stages = mm.mm_profile_read(plan, reset=True)
+        total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+
+        # end to end through the host-buffer entry point (copies inside the timed region)
+        hoff = torch.from_numpy(ev.offsets).pin_memory()
+        ht = torch.from_numpy(ev.t).pin_memory()
+        hp = torch.from_numpy(ev.logp).pin_memory()
+        hS = torch.empty((D, D), dtype=rdt).pin_memory()
+        hR = torch.empty((D, D), dtype=rdt).pin_memory()
+        e2e_steps = max(3, min(args.steps, 50))
+        for _ in range(2):
+            mm.mm_estimate_host(plan, hoff, ht, hp, N, sigma=hS, R=hR)
+        e2e_ms = 0.0
+        for _ in range(e2e_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            mm.mm_estimate_host(plan, hoff, ht, hp, N, sigma=hS, R=hR)
+            b.record()
+            torch.cuda.synchronize()
+            e2e_ms += a.elapsed_time(b)
+    clocks = clk.summary()
+
+    # FP64 GPU path on the same inputs: throughput and max |dR| against it
+    fp64 = None
+    if args.prec != "fp64" and not args.no_fp64:
+        p64 = mm.mm_plan_create(D=D, N_max=N, max_events=ev.n_events, tol=1e-12, kernel=args.kernel,
+                                basis="dirichlet", prec="fp64")
+        c64 = torch.empty((D, N + 1), dtype=torch.complex128, device=dev)
+        S64 = torch.empty((D, D), dtype=torch.float64, device=dev)
+        R64 = torch.empty((D, D), dtype=torch.float64, device=dev)
+        mm.mm_estimate(p64, off, tt, lp, N, coeffs=c64, sigma=S64, R=R64)
+        torch.cuda.synchronize()
+        k64 = max(3, min(20, args.steps))
+        ms64 = 0.0
+        for _ in range(k64):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            mm.mm_estimate(p64, off, tt, lp, N, coeffs=c64, sigma=S64, R=R64)
+            b.record()
+        torch.cuda.synchronize()
+        ms64 = a.elapsed_time(b)  # last step (steady state)
+        dR = float((R.double() - R64).abs().max())
+        dF = float(((coef.to(torch.complex128) - c64).abs().pow(2).sum(1).sqrt()
+                    / c64.abs().pow(2).sum(1).sqrt().clamp_min(1e-300)).max())
+        fp64 = {"events_per_s": ev.n_events / (ms64 * 1e-3), "ms_per_step": ms64,
+                "max_abs_dcorr": dR, "max_rel_l2_dcoef": dF}
+        mm.mm_destroy(p64)
+
+    # max over ranks
+    t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms, e2e_ms = float(t[0]), float(t[1])
+    n_total = ev.n_events * world  # replicas are equal in size up to the Poisson draw
+    if world > 1:
+        ne = torch.tensor([float(ev.n_events)], dtype=torch.float64, device=dev)
+        dist.all_reduce(ne, op=dist.ReduceOp.SUM)
+        n_total = float(ne[0])
+
+    if rank == 0:
+        ms_step = total_ms / args.steps
+        value = n_total * args.steps / (total_ms * 1e-3)
+        peaks, peak_src = load_peaks()
+        info = mm.mm_plan_get_info(plan)
+        stage_ms = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in stages.items()}
+        dom = max((k for k in stages if k != "setup"), key=lambda k: stages[k][0])
+        # algorithmic bytes per launch ("Rooflines")
+        Mr = info["Mr"]
+        cbytes = 8 if args.prec != "fp64" else 16
+        gbytes = 4 if args.prec != "fp64" else 8
+        alg = {
+            "spread": 16.0 * ev.n_events + gbytes * Mr * D,
+            "fft_cols": 2.0 * gbytes * Mr * D,
+            "fft_rows": gbytes * Mr * D + cbytes * (N + 1) * D,
+            "gram": cbytes * (N + 1) * D,
+            "reduce": 0.0,
+            "prep": 16.0 * D,
+        }
+        avg_ms = stage_ms[dom]
+        achieved = alg.get(dom, 0.0) / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
+        traffic = NCU_TRAFFIC.get((dom, args.workload, args.prec, args.kernel))
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": f"{peak_src} hbm_gbs",
+                "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": alg.get(dom, 0.0)}
+        ev_c, secs, assets, threads = oracle_rate(ev, N, args.cpu_budget)
+        cpu = {"value": ev_c / secs if secs > 0 else 0.0, "unit": "events/s", "cores": threads, "kind": "oracle",
+               "sample": f"direct sum of Eq. (4), k=0..N, on {assets} of {D} assets (~{secs:.1f} s, "
+                         f"blocks of modes scaled to events/s at N={N}); coefficients only"}
+        h2d = 8 * (D + 1) + 16 * ev.n_events
+        d2h = 2 * D * D * (8 if args.prec == "fp64" else 4)
+        line = {
+            "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32",
+            "data": "synthetic (seeded GBM, Poisson arrivals)",
+            "config": {"workload": ev.meta.get("workload", args.workload), "D": D, "N": N,
+                       "events": ev.n_events, "kernel": args.kernel, "tol": tol, "basis": "dirichlet",
+                       "contraction": args.prec, "l2": "flushed between steps (256 MB write)",
+                       "grid_Mr": Mr, "fft": [info["fft_P"], info["fft_Q"]], "gram_splits": info["gram_splits"],
+                       "replicas": world},
+            "matrices_per_s": world * args.steps / (total_ms * 1e-3),
+            "stage_ms": stage_ms,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": n_total * e2e_steps / (e2e_ms * 1e-3), "unit": "events/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                    "ms_per_step": e2e_ms / e2e_steps},
+            "fp64_gpu_path": fp64,
+            "clocks": clocks,
+            "gpu_launches": int(launches),
+        }
+        print(json.dumps(line), flush=True)
+    mm.mm_destroy(plan)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * mm.h -- C ABI of the GB300 Malliavin-Mancino Fourier covariance library.
+ *
+ * The library computes, for D assets observed at asynchronous event times,
+ *   (1) the Fourier coefficients F(dp_i)(k), |k| <= N, of each asset's
+ *       log-price returns (Eq. (4), Sec. 2.2) with a type-1 NUFFT (Sec. 2.2.5:
+ *       spreading Eq. (12), FFT Eq. (13), deconvolution Eq. (14));
+ *   (2) the D x D integrated covariance Sigma under the Dirichlet (Eq. (2)) or
+ *       Fejer (Eq. (3)) basis and the correlation R (Algorithm 3).
+ * Citations name the paper: Chang, Pienaar & Gebbie, "Malliavin-Mancino
+ * estimators implemented with non-uniform fast Fourier transforms",
+ * arXiv:2003.02842. Equations are numbered in display order; algorithms in
+ * appendix order (Algorithm 2 Nyquist, 3 MM estimators, 4 time rescaling,
+ * 8-10 NUFFT with Gaussian, Kaiser-Bessel and ES kernels).
+ *
+ * Conventions shared by every call:
+ *  - Event data is CSR: offsets[D+1] (int64, non-decreasing, offsets[0] = 0,
+ *    offsets[D] <= desc.max_events); t[offsets[D]] event times (float64, any
+ *    unit, strictly increasing within an asset); logp[offsets[D]] log-prices
+ *    (float64). Asset i owns events offsets[i] .. offsets[i+1]-1. Its returns
+ *    delta_h = logp[h+1] - logp[h] sit at the left end point t[h] (Sec. 2.1);
+ *    an asset with fewer than two events has no returns and zero coefficients.
+ *  - Pointers named d_* are device pointers on the current device; h_* are
+ *    host pointers (pinned memory makes the copies asynchronous). The caller
+ *    owns every input and output buffer; the plan owns only its workspace.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device-side calls are asynchronous on it unless stated otherwise.
+ *  - Coefficients are Hermitian-half, F-convention (the 1/(2 pi) of Eq. (4)
+ *    included): d_coeffs[i * (N+1) + k] = F(dp_i)(k), k = 0..N; complex128
+ *    (interleaved double re, im) for MM_PREC_FP64, complex64 otherwise.
+ *    F(dp_i)(-k) = conj(F(dp_i)(k)).
+ *  - Sigma and R are D x D row-major, float64 for MM_PREC_FP64 and float32
+ *    otherwise. R_ii = 1 exactly; a zero-variance asset gives NaN in its row
+ *    and column of R and the non-fatal status MM_ERR_ZERO_VARIANCE at the
+ *    next mm_plan_sync.
+ *  - Errors found on the host are returned at once and nothing is launched.
+ *    Errors that need the data (unsorted or repeated times, non-finite
+ *    values, a bounded device wait that gave up) are recorded in a device
+ *    status word; mm_plan_sync returns and clears the first of them. All
+ *    device indexing is bounds-checked, so bad data gives bad numbers and a
+ *    status, never an out-of-bounds access.
+ *  - A plan is used by one host thread at a time. Calls that overlap on the
+ *    GPU through different streams must use different plans (they share the
+ *    plan's workspace).
+ */
+#ifndef MM_GB300_H
+#define MM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MM_OK = 0,
+  MM_ERR_INVALID_ARG = 1,     /* bad pointer, size or enum; bad offsets array */
+  MM_ERR_UNSORTED = 2,        /* event times decrease within an asset */
+  MM_ERR_DUPLICATE_TIME = 3,  /* two events of an asset share a time (Delta t0 = 0, Algorithm 2) */
+  MM_ERR_DEGENERATE_SPAN = 4, /* t_max <= t_min or non-finite bounds (Algorithm 4) */
+  MM_ERR_CUTOFF = 5,          /* N > N_max, N < 1 under Fejer, or no Nyquist cutoff */
+  MM_ERR_OOM = 6,             /* workspace allocation failed at plan creation */
+  MM_ERR_CUDA = 7,            /* a CUDA runtime call or launch failed */
+  MM_ERR_TIMEOUT = 8,         /* a bounded device-side wait gave up */
+  MM_ERR_ZERO_VARIANCE = 9,   /* non-fatal: Sigma_ii = 0 for some asset, R has NaN */
+  MM_ERR_NONFINITE = 10,      /* NaN or Inf time or log-price in the input */
+  MM_ERR_UNSUPPORTED = 11     /* request outside what this build supports */
+} mm_status;
+
+/* Basis kernel of the contraction: Dirichlet Eq. (2) / Algorithm 3 C.1,
+ * weights 1/(2N+1); Fejer Eq. (3) / Algorithm 3 C.2, weights
+ * (1 - |k|/N)/(N+1), taken literally (so Sigma_Fejer carries N/(N+1)). */
+typedef enum { MM_BASIS_DIRICHLET = 0, MM_BASIS_FEJER = 1 } mm_basis;
+
+/* Averaging kernel of the NUFFT (Sec. 2.2.5): Gaussian with the fast Gaussian
+ * gridding split (Eqs. (5)-(6), (17), Algorithm 8), Kaiser-Bessel
+ * (Eqs. (7)-(8), Algorithm 9), exponential of semicircle (Eqs. (9)-(10),
+ * Algorithm 10). The spreading half-width M_sp(tol) follows the rules of
+ * Sec. 2.2.5. */
+typedef enum { MM_KERNEL_GAUSS = 0, MM_KERNEL_KB = 1, MM_KERNEL_ES = 2 } mm_kernel;
+
+/* MM_PREC_FP64: every stage in float64. MM_PREC_MIXED_*: rescaling, phase
+ * reduction to grid offsets, differencing into returns and the diagonal
+ * normalisation in float64; spreading, FFT and deconvolution in float32; the
+ * contraction on the tensor cores as split bf16 (hi*hi + hi*lo + lo*hi) or
+ * split tf32 products with float32 accumulation. */
+typedef enum {
+  MM_PREC_FP64 = 0,
+  MM_PREC_MIXED_BF16X3 = 1,
+  MM_PREC_MIXED_3XTF32 = 2
+} mm_precision;
+
+typedef struct {
+  int32_t D;            /* number of assets, >= 1 */
+  int32_t N_max;        /* largest cutoff any call will use, >= 0 */
+  int64_t max_events;   /* upper bound on offsets[D]; sizes the host-staging buffers */
+  double tol;           /* NUFFT tolerance eps in (0, 0.5) (Sec. 2.2.5) */
+  mm_kernel kernel;
+  mm_basis basis;
+  mm_precision prec;
+  int32_t spread_tile;  /* grid cells per spreading block; 0 = library default */
+  int32_t reserved[6];  /* must be zero */
+} mm_plan_desc;
+
+typedef struct mm_plan_s* mm_plan;
+
+/* Per-stage timing and launch counters (device time from CUDA events on the
+ * launching stream, summed since the last reset). */
+enum { MM_STAGE_PREP = 0, MM_STAGE_SPREAD = 1, MM_STAGE_FFT_COLS = 2, MM_STAGE_FFT_ROWS = 3,
+       MM_STAGE_GRAM = 4, MM_STAGE_REDUCE = 5, MM_STAGE_SETUP = 6, MM_NUM_STAGES = 7 };
+
+typedef struct {
+  int32_t msp;           /* spreading half-width M_sp */
+  int32_t N;             /* cutoff of the last call */
+  int64_t Mr;            /* oversampled grid size of the last call */
+  int64_t fft_P, fft_Q;  /* Mr/2 = P * Q factorisation of the last call */
+  int64_t workspace_bytes;
+  int64_t launches;      /* kernels launched by this plan since creation */
+  int32_t gram_splits;   /* split-K factor of the last contraction */
+  int32_t reserved[5];
+} mm_plan_info;
+
+/* Create a plan: validates desc, allocates the workspace on the current
+ * device (grid, FFT tables, contraction partials, staging for the host-buffer
+ * entry point). Returns MM_ERR_INVALID_ARG for a bad desc, MM_ERR_OOM when an
+ * allocation fails. *out is NULL on failure. */
+mm_status mm_plan_create(const mm_plan_desc* desc, mm_plan* out);
+
+/* Release the plan and its workspace (synchronises the device first). */
+mm_status mm_destroy(mm_plan plan);
+
+/* Fourier coefficients F(dp_i)(k), k = 0..N, of every asset (Eq. (4)) by the
+ * type-1 NUFFT of Sec. 2.2.5.
+ *  N > 0: the cutoff (N <= N_max). N <= 0: the Nyquist cutoff of Algorithm 2,
+ *         N = min_i floor(span / (2 min-gap_i)); this form synchronises the
+ *         stream to read N back.
+ *  t0 < t1: rescale with that window, t~ = 2 pi (t - t0)/(t1 - t0) (events
+ *         must lie in [t0, t1]); otherwise t0, t1 are taken as the minimum
+ *         and maximum time over all assets (Algorithm 4).
+ *  d_coeffs: D * (N+1) complex elements (see conventions).
+ *  N_used: optional host pointer receiving the cutoff used. */
+mm_status mm_coeffs(mm_plan plan, const int64_t* d_offsets, const double* d_t,
+                    const double* d_logp, int32_t N, double t0, double t1,
+                    void* d_coeffs, int32_t* N_used, void* stream);
+
+/* Covariance from coefficients (Algorithm 3 step C, Eqs. (2)/(3)):
+ * Sigma_ij = sum_{|k|<=N} w_k (2 pi)^2 conj(F_i(k)) F_j(k), computed as a
+ * split-K Hermitian rank-(2N+1) update (tensor cores in the mixed
+ * precisions). d_coeffs as written by mm_coeffs for the same N. */
+mm_status mm_cov(mm_plan plan, const void* d_coeffs, int32_t N, void* d_sigma, void* stream);
+
+/* Covariance and correlation R_ij = Sigma_ij / (sqrt(Sigma_ii) sqrt(Sigma_jj))
+ * (Algorithm 3, last step), the normalisation in float64. d_sigma may be
+ * NULL when only R is wanted. */
+mm_status mm_corr(mm_plan plan, const void* d_coeffs, int32_t N, void* d_sigma_or_null,
+                  void* d_R, void* stream);
+
+/* Whole Algorithm 3 on device buffers: mm_coeffs followed by mm_corr.
+ * d_coeffs receives the coefficients (it is also the contraction's input). */
+mm_status mm_estimate(mm_plan plan, const int64_t* d_offsets, const double* d_t,
+                      const double* d_logp, int32_t N, double t0, double t1, void* d_coeffs,
+                      void* d_sigma_or_null, void* d_R, int32_t* N_used, void* stream);
+
+/* Whole Algorithm 3 from host buffers: copies h_offsets (D+1), h_t and h_logp
+ * (h_offsets[D] each, <= max_events) to the plan's device staging buffers,
+ * runs mm_estimate, copies Sigma and R (and the coefficients when h_coeffs is
+ * not NULL) back, and synchronises the stream before returning. Returns the
+ * device status word as mm_plan_sync would. */
+mm_status mm_estimate_host(mm_plan plan, const int64_t* h_offsets, const double* h_t,
+                           const double* h_logp, int32_t N, double t0, double t1,
+                           void* h_coeffs_or_null, void* h_sigma_or_null, void* h_R,
+                           int32_t* N_used, void* stream);
+
+/* Nyquist cutoff of Algorithm 2 on device data (synchronises the stream).
+ * Window as for mm_coeffs. Returns MM_ERR_CUTOFF when no asset has two
+ * events, MM_ERR_DUPLICATE_TIME when some gap is zero. */
+mm_status mm_nyquist(mm_plan plan, const int64_t* d_offsets, const double* d_t, double t0,
+                     double t1, int32_t* N_out, void* stream);
+
+/* Wait for the plan's work on its last stream and return (and clear) the
+ * first device-side status recorded since the last call (MM_OK if none). */
+mm_status mm_plan_sync(mm_plan plan);
+
+/* Plan facts for inspection and tests. */
+mm_status mm_plan_get_info(mm_plan plan, mm_plan_info* info);
+
+/* Stage timing: enable (1) / disable (0) CUDA-event timing of every stage;
+ * read the summed milliseconds and launch counts per stage (MM_NUM_STAGES
+ * entries each, either pointer may be NULL); reset clears them. Reading
+ * synchronises the events it reads. */
+mm_status mm_profile_enable(mm_plan plan, int32_t on);
+mm_status mm_profile_read(mm_plan plan, double* ms, int64_t* launches, int32_t reset);
+
+/* Static text for a status code. */
+const char* mm_status_string(mm_status s);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t mm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MM_GB300_H */

@@ -1,1 +1,258 @@
-"""GB300-native Malliavin-Mancino Fourier covariance estimator via type-1 NUFFTs."""
+"""GB300-native Malliavin-Mancino Fourier covariance estimator via type-1 NUFFTs.
+
+Thin Python binding over the C ABI of ``include/mm.h`` (library
+``lib/libmm_gb300.so``). The functions below carry the C names and only
+marshal arguments: torch tensors give device (or pinned host) pointers and
+the current CUDA stream; every step of the computation runs in the library's
+CUDA kernels. There is no CPU fallback.
+
+    plan = mm_plan_create(D=100, N_max=10000, max_events=2_000_000, tol=1e-6,
+                          kernel="es", basis="dirichlet", prec="bf16x3")
+    F, N = mm_coeffs(plan, offsets, t, logp, N=10000)   # D x (N+1) complex
+    Sigma, R = mm_corr(plan, F, N)
+    mm_destroy(plan)
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib
+from ._lib import BASES, KERNELS, PRECISIONS, STAGES, STATUS_NAMES
+
+__all__ = [
+    "MMError", "Plan", "mm_plan_create", "mm_destroy", "mm_coeffs", "mm_cov", "mm_corr", "mm_estimate",
+    "mm_estimate_host", "mm_nyquist", "mm_plan_sync", "mm_plan_get_info", "mm_profile_enable",
+    "mm_profile_read", "mm_status_string", "mm_version", "KERNELS", "BASES", "PRECISIONS", "STAGES",
+]
+
+
+class MMError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = int(status)
+        self.name = STATUS_NAMES.get(self.status, str(status))
+        super().__init__(f"{where}: {self.name} ({mm_status_string(self.status)})")
+
+
+def _check(st, where):
+    if st != 0:
+        raise MMError(st, where)
+
+
+def mm_status_string(status: int) -> str:
+    return _lib.load().mm_status_string(int(status)).decode()
+
+
+def mm_version() -> int:
+    return int(_lib.load().mm_version())
+
+
+class Plan:
+    """Owns an mm_plan handle plus the description it was created from."""
+
+    def __init__(self, handle, desc: dict):
+        self.handle = handle
+        self.desc = desc
+
+    @property
+    def fp64(self) -> bool:
+        return self.desc["prec"] == "fp64"
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                _lib.load().mm_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(x, dtype, name, device=True):
+    torch = _torch()
+    if not isinstance(x, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if x.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {x.dtype}")
+    if device and not x.is_cuda:
+        raise ValueError(f"{name} must live on the GPU")
+    if not device and x.is_cuda:
+        raise ValueError(f"{name} must live in host memory")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def mm_plan_create(D, N_max, max_events=0, tol=1e-6, kernel="es", basis="dirichlet", prec="bf16x3",
+                   spread_tile=0) -> Plan:
+    d = _lib.PlanDesc()
+    d.D, d.N_max, d.max_events, d.tol = int(D), int(N_max), int(max_events), float(tol)
+    d.kernel, d.basis, d.prec = KERNELS[kernel], BASES[basis], PRECISIONS[prec]
+    d.spread_tile = int(spread_tile)
+    h = ctypes.c_void_p()
+    _check(_lib.load().mm_plan_create(ctypes.byref(d), ctypes.byref(h)), "mm_plan_create")
+    return Plan(h, dict(D=int(D), N_max=int(N_max), max_events=int(max_events), tol=float(tol), kernel=kernel,
+                        basis=basis, prec=prec, spread_tile=int(spread_tile)))
+
+
+def mm_destroy(plan: Plan):
+    if plan.handle:
+        _check(_lib.load().mm_destroy(plan.handle), "mm_destroy")
+        plan.handle = None
+
+
+def _coef_dtype(plan):
+    torch = _torch()
+    return torch.complex128 if plan.fp64 else torch.complex64
+
+
+def _real_dtype(plan):
+    torch = _torch()
+    return torch.float64 if plan.fp64 else torch.float32
+
+
+def _events(offsets, t, logp):
+    torch = _torch()
+    return (_dptr(offsets, torch.int64, "offsets"), _dptr(t, torch.float64, "t"),
+            _dptr(logp, torch.float64, "logp"))
+
+
+def _alloc_coeffs(plan, N, device):
+    return _torch().empty((plan.desc["D"], N + 1), dtype=_coef_dtype(plan), device=device)
+
+
+def mm_nyquist(plan, offsets, t, window=None, stream=None) -> int:
+    torch = _torch()
+    t0, t1 = window if window is not None else (0.0, 0.0)
+    N = ctypes.c_int32()
+    _check(_lib.load().mm_nyquist(plan.handle, _dptr(offsets, torch.int64, "offsets"),
+                                  _dptr(t, torch.float64, "t"), float(t0), float(t1), ctypes.byref(N),
+                                  _stream(stream)), "mm_nyquist")
+    return int(N.value)
+
+
+def mm_coeffs(plan, offsets, t, logp, N=0, window=None, out=None, stream=None):
+    """F(dp_i)(k), k = 0..N, as a D x (N+1) complex tensor; N <= 0 uses the
+    Nyquist cutoff (and synchronises). Returns (coeffs, N_used)."""
+    if N <= 0:
+        N = mm_nyquist(plan, offsets, t, window, stream)
+    if out is None:
+        out = _alloc_coeffs(plan, N, t.device)
+    t0, t1 = window if window is not None else (0.0, 0.0)
+    Nu = ctypes.c_int32()
+    po, pt, pp = _events(offsets, t, logp)
+    _check(_lib.load().mm_coeffs(plan.handle, po, pt, pp, int(N), float(t0), float(t1),
+                                 _dptr(out, _coef_dtype(plan), "out"), ctypes.byref(Nu), _stream(stream)),
+           "mm_coeffs")
+    return out, int(Nu.value)
+
+
+def mm_cov(plan, coeffs, N, out=None, stream=None):
+    torch = _torch()
+    D = plan.desc["D"]
+    if out is None:
+        out = torch.empty((D, D), dtype=_real_dtype(plan), device=coeffs.device)
+    _check(_lib.load().mm_cov(plan.handle, _dptr(coeffs, _coef_dtype(plan), "coeffs"), int(N),
+                              _dptr(out, _real_dtype(plan), "sigma"), _stream(stream)), "mm_cov")
+    return out
+
+
+def mm_corr(plan, coeffs, N, sigma=True, R=None, stream=None):
+    """Returns (Sigma or None, R)."""
+    torch = _torch()
+    D = plan.desc["D"]
+    dt = _real_dtype(plan)
+    if R is None:
+        R = torch.empty((D, D), dtype=dt, device=coeffs.device)
+    S = None
+    if sigma is True:
+        S = torch.empty((D, D), dtype=dt, device=coeffs.device)
+    elif sigma is not None and sigma is not False:
+        S = sigma
+    ps = _dptr(S, dt, "sigma") if S is not None else ctypes.c_void_p(0)
+    _check(_lib.load().mm_corr(plan.handle, _dptr(coeffs, _coef_dtype(plan), "coeffs"), int(N), ps,
+                               _dptr(R, dt, "R"), _stream(stream)), "mm_corr")
+    return S, R
+
+
+def mm_estimate(plan, offsets, t, logp, N, window=None, coeffs=None, sigma=True, R=None, stream=None):
+    """Algorithm 3 on device tensors: returns (coeffs, Sigma or None, R, N_used).
+    N must be positive here (use mm_nyquist first for the Nyquist cutoff)."""
+    torch = _torch()
+    if N <= 0:
+        N = mm_nyquist(plan, offsets, t, window, stream)
+    D = plan.desc["D"]
+    dt = _real_dtype(plan)
+    if coeffs is None:
+        coeffs = _alloc_coeffs(plan, N, t.device)
+    if R is None:
+        R = torch.empty((D, D), dtype=dt, device=t.device)
+    if sigma is True:
+        S = torch.empty((D, D), dtype=dt, device=t.device)
+    elif sigma is None or sigma is False:
+        S = None
+    else:
+        S = sigma
+    ps = _dptr(S, dt, "sigma") if S is not None else ctypes.c_void_p(0)
+    t0, t1 = window if window is not None else (0.0, 0.0)
+    Nu = ctypes.c_int32()
+    po, pt, pp = _events(offsets, t, logp)
+    _check(_lib.load().mm_estimate(plan.handle, po, pt, pp, int(N), float(t0), float(t1),
+                                   _dptr(coeffs, _coef_dtype(plan), "coeffs"), ps, _dptr(R, dt, "R"),
+                                   ctypes.byref(Nu), _stream(stream)), "mm_estimate")
+    return coeffs, S, R, int(Nu.value)
+
+
+def mm_estimate_host(plan, offsets, t, logp, N, window=None, coeffs=None, sigma=None, R=None, stream=None,
+                     allow_status=()):
+    """Algorithm 3 from host tensors (pinned memory for asynchronous copies);
+    the library copies in and out and synchronises. Returns the status."""
+    torch = _torch()
+    dt = _real_dtype(plan)
+    pc = _dptr(coeffs, _coef_dtype(plan), "coeffs", device=False) if coeffs is not None else ctypes.c_void_p(0)
+    ps = _dptr(sigma, dt, "sigma", device=False) if sigma is not None else ctypes.c_void_p(0)
+    t0, t1 = window if window is not None else (0.0, 0.0)
+    Nu = ctypes.c_int32()
+    st = _lib.load().mm_estimate_host(plan.handle, _dptr(offsets, torch.int64, "offsets", device=False),
+                                      _dptr(t, torch.float64, "t", device=False),
+                                      _dptr(logp, torch.float64, "logp", device=False), int(N), float(t0),
+                                      float(t1), pc, ps, _dptr(R, dt, "R", device=False), ctypes.byref(Nu),
+                                      _stream(stream))
+    if st != 0 and st not in allow_status:
+        raise MMError(st, "mm_estimate_host")
+    return st, int(Nu.value)
+
+
+def mm_plan_sync(plan) -> int:
+    """Wait for the plan's work; returns (and clears) the device status code."""
+    return int(_lib.load().mm_plan_sync(plan.handle))
+
+
+def mm_plan_get_info(plan) -> dict:
+    info = _lib.PlanInfo()
+    _check(_lib.load().mm_plan_get_info(plan.handle, ctypes.byref(info)), "mm_plan_get_info")
+    return {k: getattr(info, k) for k, _ in _lib.PlanInfo._fields_ if k != "reserved"}
+
+
+def mm_profile_enable(plan, on=True):
+    _check(_lib.load().mm_profile_enable(plan.handle, 1 if on else 0), "mm_profile_enable")
+
+
+def mm_profile_read(plan, reset=False) -> dict:
+    ms = (ctypes.c_double * len(STAGES))()
+    nl = (ctypes.c_int64 * len(STAGES))()
+    _check(_lib.load().mm_profile_read(plan.handle, ms, nl, 1 if reset else 0), "mm_profile_read")
+    return {s: (ms[i], nl[i]) for i, s in enumerate(STAGES)}

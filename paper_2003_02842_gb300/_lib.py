@@ -1,0 +1,91 @@
+"""ctypes declarations of the C ABI in include/mm.h.
+
+This module only loads the in-tree ``lib/libmm_gb300.so`` and declares its
+entry points. There is no fallback: if the library is missing the import of
+any compute entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libmm_gb300.so")
+
+MM_OK = 0
+STATUS_NAMES = {
+    0: "MM_OK", 1: "MM_ERR_INVALID_ARG", 2: "MM_ERR_UNSORTED", 3: "MM_ERR_DUPLICATE_TIME",
+    4: "MM_ERR_DEGENERATE_SPAN", 5: "MM_ERR_CUTOFF", 6: "MM_ERR_OOM", 7: "MM_ERR_CUDA",
+    8: "MM_ERR_TIMEOUT", 9: "MM_ERR_ZERO_VARIANCE", 10: "MM_ERR_NONFINITE", 11: "MM_ERR_UNSUPPORTED",
+}
+KERNELS = {"gauss": 0, "kb": 1, "es": 2}
+BASES = {"dirichlet": 0, "fejer": 1}
+PRECISIONS = {"fp64": 0, "bf16x3": 1, "3xtf32": 2}
+STAGES = ["prep", "spread", "fft_cols", "fft_rows", "gram", "reduce", "setup"]
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [
+        ("D", ctypes.c_int32),
+        ("N_max", ctypes.c_int32),
+        ("max_events", ctypes.c_int64),
+        ("tol", ctypes.c_double),
+        ("kernel", ctypes.c_int),
+        ("basis", ctypes.c_int),
+        ("prec", ctypes.c_int),
+        ("spread_tile", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 6),
+    ]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [
+        ("msp", ctypes.c_int32),
+        ("N", ctypes.c_int32),
+        ("Mr", ctypes.c_int64),
+        ("fft_P", ctypes.c_int64),
+        ("fft_Q", ctypes.c_int64),
+        ("workspace_bytes", ctypes.c_int64),
+        ("launches", ctypes.c_int64),
+        ("gram_splits", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
+    ]
+
+
+_lib = None
+
+
+def load():
+    """Load libmm_gb300.so (built by paper_2003_02842_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"CUDA library {LIB_PATH} is missing; build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'` (there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    p, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    st = ctypes.c_int
+    sig = {
+        "mm_plan_create": ([ctypes.POINTER(PlanDesc), ctypes.POINTER(p)], st),
+        "mm_destroy": ([p], st),
+        "mm_coeffs": ([p, p, p, p, i32, d, d, p, ctypes.POINTER(i32), p], st),
+        "mm_cov": ([p, p, i32, p, p], st),
+        "mm_corr": ([p, p, i32, p, p, p], st),
+        "mm_estimate": ([p, p, p, p, i32, d, d, p, p, p, ctypes.POINTER(i32), p], st),
+        "mm_estimate_host": ([p, p, p, p, i32, d, d, p, p, p, ctypes.POINTER(i32), p], st),
+        "mm_nyquist": ([p, p, p, d, d, ctypes.POINTER(i32), p], st),
+        "mm_plan_sync": ([p], st),
+        "mm_plan_get_info": ([p, ctypes.POINTER(PlanInfo)], st),
+        "mm_profile_enable": ([p, i32], st),
+        "mm_profile_read": ([p, p, p, i32], st),
+        "mm_status_string": ([st], ctypes.c_char_p),
+        "mm_version": ([], i32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L

@@ -1,0 +1,638 @@
+// mm_api.cu -- the C ABI of include/mm.h: plans, per-cutoff configuration and
+// the stream-ordered launch sequence of the hot path
+//   bounds (Algorithm 4) -> spread (Eq. (12)) -> FFT pass 1 -> FFT pass 2 with
+//   unpack + deconvolution (Eqs. (13)-(14)) -> split-K Gram (Algorithm 3
+//   step C) -> FP64 reduce + correlation (Algorithm 3, last step).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "mm_common.cuh"
+
+using namespace mmgpu;
+
+namespace {
+
+constexpr int kSMs = 152;           // GB300: 2 dies x 76 SMs
+constexpr int kGlNodes = 128;       // Gauss-Legendre nodes for the ES transform
+constexpr int kMaxGramCtas = 2 * kSMs;
+
+struct Prof {
+  int stage;
+  cudaEvent_t a, b;
+};
+
+bool smooth235(int64_t x) {
+  for (int p : {2, 3, 5})
+    while (x % p == 0) x /= p;
+  return x == 1;
+}
+
+// Radix plan of an L-point FFT (L 5-smooth): radix 8 first, then 4, 2, 5, 3.
+int radix_plan(int L, int* rad) {
+  int n = 0;
+  while (L % 8 == 0) { rad[n++] = 8; L /= 8; }
+  while (L % 4 == 0) { rad[n++] = 4; L /= 4; }
+  while (L % 2 == 0) { rad[n++] = 2; L /= 2; }
+  while (L % 5 == 0) { rad[n++] = 5; L /= 5; }
+  while (L % 3 == 0) { rad[n++] = 3; L /= 3; }
+  return n;
+}
+
+// Smallest 5-smooth n >= nmin that splits as P * Q with P, Q <= kMaxFftLen;
+// P is the divisor closest to sqrt(n). Returns false when none exists.
+bool choose_fft(int64_t nmin, int64_t* n_out, int* P_out, int* Q_out) {
+  const int64_t cap = (int64_t)kMaxFftLen * kMaxFftLen;
+  for (int64_t n = std::max<int64_t>(nmin, 1); n <= cap; ++n) {
+    if (!smooth235(n)) continue;
+    int bestP = -1;
+    double best = 1e300;
+    for (int64_t P = 1; P <= kMaxFftLen && P <= n; ++P) {
+      if (n % P) continue;
+      int64_t Q = n / P;
+      if (Q > kMaxFftLen) continue;
+      double d = fabs(log((double)P) - log((double)Q));
+      if (d < best) { best = d; bestP = (int)P; }
+    }
+    if (bestP > 0) {
+      *n_out = n;
+      *P_out = bestP;
+      *Q_out = (int)(n / bestP);
+      return true;
+    }
+  }
+  return false;
+}
+
+// M_sp rules of Sec. 2.2.5 (sigma = 2).
+int msp_rule(mm_kernel k, double eps) {
+  const double sigma = 2.0;
+  if (k == MM_KERNEL_GAUSS) return (int)floor(-log(eps) * (sigma - 0.5) / (kPi * (sigma - 1.0)) + 0.5);
+  const int digits = (int)ceil(log10(1.0 / eps) - 1e-9);
+  const int m = (int)floor(0.5 * (double)(digits + 2));
+  return k == MM_KERNEL_ES ? m + 2 : m;
+}
+
+mm_status flags_to_status(int f) {
+  if (f & (ST_BAD_OFFSETS | ST_OUT_OF_WINDOW)) return MM_ERR_INVALID_ARG;
+  if (f & ST_SPAN) return MM_ERR_DEGENERATE_SPAN;
+  if (f & ST_UNSORTED) return MM_ERR_UNSORTED;
+  if (f & ST_DUPLICATE) return MM_ERR_DUPLICATE_TIME;
+  if (f & ST_NONFINITE) return MM_ERR_NONFINITE;
+  if (f & ST_CUTOFF) return MM_ERR_CUTOFF;
+  if (f & ST_TIMEOUT) return MM_ERR_TIMEOUT;
+  if (f & ST_ZERO_VAR) return MM_ERR_ZERO_VARIANCE;
+  return MM_OK;
+}
+
+}  // namespace
+
+struct mm_plan_s {
+  mm_plan_desc desc{};
+  int dev = 0;
+  bool fp64 = false;
+  size_t cs = 8;   // bytes per complex coefficient
+  size_t rs = 4;   // bytes per real grid cell / output element
+  int msp = 0, klo = 0, khi = 0;
+  int64_t n_max = 0;
+  // workspace
+  void* grid = nullptr;
+  void* W = nullptr;
+  void* U = nullptr;
+  void* decon = nullptr;
+  double* glx = nullptr;
+  double* glw = nullptr;
+  double* bounds = nullptr;
+  int* status = nullptr;  // [0] sticky flags, [1] gate, [2] Nyquist N
+  unsigned long long* gapbits = nullptr;
+  void* wsq = nullptr;
+  void* partial = nullptr;
+  size_t partial_bytes = 0;
+  int64_t* s_off = nullptr;
+  double* s_t = nullptr;
+  double* s_p = nullptr;
+  void* s_coef = nullptr;
+  void* s_sigma = nullptr;
+  void* s_R = nullptr;
+  int64_t workspace = 0;
+  // per-cutoff configuration
+  int cfg_N = -1;
+  int tab_N = -1;
+  int64_t Mr = 0;
+  FftParams fft{};
+  SpreadParams sp{};
+  double tau = 0;
+  int w_N = -1, w_basis = -1;
+  GramParams gram{};
+  cudaStream_t last = nullptr;
+  // instrumentation
+  bool prof = false;
+  std::vector<Prof> pending;
+  double ms[MM_NUM_STAGES] = {};
+  int64_t nl[MM_NUM_STAGES] = {};
+  int64_t launches = 0;
+};
+
+namespace {
+
+#define MM_CUDA(call)                                 \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return MM_ERR_CUDA;        \
+  } while (0)
+
+mm_status dalloc(mm_plan p, void** ptr, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return MM_ERR_OOM;
+  }
+  p->workspace += (int64_t)bytes;
+  return MM_OK;
+}
+
+void free_all(mm_plan p) {
+  void* ptrs[] = {p->grid, p->W, p->U, p->decon, p->glx, p->glw, p->bounds, p->status, p->gapbits, p->wsq,
+                  p->partial, p->s_off, p->s_t, p->s_p, p->s_coef, p->s_sigma, p->s_R};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  for (auto& e : p->pending) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  p->pending.clear();
+}
+
+// Stage timing helpers: when profiling is on, every launch is bracketed by a
+// pair of events on the launching stream.
+struct StageScope {
+  mm_plan p;
+  int stage;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  int count;
+  StageScope(mm_plan p_, int stage_, cudaStream_t s_, int count_ = 1) : p(p_), stage(stage_), s(s_), count(count_) {
+    if (p->prof) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~StageScope() {
+    p->launches += count;
+    p->nl[stage] += count;
+    if (p->prof) {
+      cudaEventRecord(b, s);
+      p->pending.push_back({stage, a, b});
+    }
+  }
+};
+
+// Per-cutoff configuration: grid size, FFT factorisation, tiles and the
+// kernel constants of Sec. 2.2.5 with sigma = M_r / M.
+mm_status configure(mm_plan p, int N) {
+  if (p->cfg_N == N) return MM_OK;
+  const int64_t M = 2 * (int64_t)N + 1;
+  int64_t n;
+  int P, Q;
+  if (!choose_fft(std::max<int64_t>(M, p->msp + 1), &n, &P, &Q)) return MM_ERR_UNSUPPORTED;
+  if (n > p->n_max) return MM_ERR_CUTOFF;
+  const int64_t Mr = 2 * n;
+  const double sigma = (double)Mr / (double)M;
+  FftParams f{};
+  f.n = n;
+  f.P = P;
+  f.Q = Q;
+  f.nrad_p = radix_plan(P, f.rad_p);
+  f.nrad_q = radix_plan(Q, f.rad_q);
+  const size_t cs = p->cs;
+  const size_t budget = 96 * 1024;
+  f.cols = 16;
+  while (f.cols > 1 && ((size_t)2 * P * f.cols + P) * cs > budget) f.cols >>= 1;
+  while (f.cols > 1 && f.cols / 2 >= Q) f.cols >>= 1;
+  f.H = P / 2 + 1;
+  f.rowblk = 16;
+  while (f.rowblk > 1 && ((size_t)4 * f.rowblk * Q + Q) * cs > budget) f.rowblk >>= 1;
+  while (f.rowblk > 1 && f.rowblk / 2 >= f.H) f.rowblk >>= 1;
+  f.N = N;
+
+  SpreadParams s{};
+  s.D = p->desc.D;
+  s.Mr = Mr;
+  s.msp = p->msp;
+  s.klo = p->klo;
+  s.khi = p->khi;
+  s.kernel = p->desc.kernel;
+  s.max_events = p->desc.max_events;
+  int tile = p->desc.spread_tile > 0 ? p->desc.spread_tile : (p->fp64 ? 2048 : 4096);
+  if (Mr <= (int64_t)tile + (s.khi - s.klo) + 1) {
+    tile = (int)Mr;
+    s.single_tile = 1;
+  }
+  if ((size_t)tile * p->rs > 200 * 1024) return MM_ERR_UNSUPPORTED;
+  s.tile = tile;
+  s.ntiles = (int)((Mr + tile - 1) / tile);
+  s.es_beta = 2.3 * 2.0 * p->msp;
+  s.es_inv_w = 1.0 / p->msp;
+  const double lam = sigma * p->msp / (sigma - 0.5);
+  s.g_t1 = kPi / lam;
+  s.kb_b = kPi * (2.0 - 1.0 / sigma);
+  s.kb_inv_phi0 = kPi * p->msp / sinh(s.kb_b * p->msp);
+  p->tau = kPi * lam / ((double)Mr * (double)Mr);
+  p->fft = f;
+  p->sp = s;
+  p->Mr = Mr;
+  p->cfg_N = N;
+  return MM_OK;
+}
+
+mm_status ensure_tables(mm_plan p, int N, cudaStream_t st) {
+  if (p->tab_N == N) return MM_OK;
+  StageScope sc(p, MM_STAGE_SETUP, st);
+  MM_CUDA(launch_setup_tables(p->desc.kernel, p->msp, p->Mr, N, p->fft.n, p->sp, p->tau, p->glx, p->glw, kGlNodes,
+                              p->W, p->U, p->decon, p->fp64, st));
+  p->tab_N = N;
+  return MM_OK;
+}
+
+mm_status check_plan(mm_plan p) {
+  if (!p) return MM_ERR_INVALID_ARG;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return MM_ERR_CUDA;
+  if (cur != p->dev && cudaSetDevice(p->dev) != cudaSuccess) return MM_ERR_CUDA;
+  return MM_OK;
+}
+
+GramParams gram_params(mm_plan p, int N) {
+  GramParams g{};
+  g.D = p->desc.D;
+  g.N = N;
+  g.ld = N + 1;
+  g.tile = p->fp64 ? 64 : 128;
+  g.ntiles = (g.D + g.tile - 1) / g.tile;
+  g.npairs = g.ntiles * (g.ntiles + 1) / 2;
+  g.chunk = p->fp64 ? 16 : (p->desc.prec == MM_PREC_MIXED_BF16X3 ? 32 : 16);
+  g.nchunks = (N + 1 + g.chunk - 1) / g.chunk;
+  // split K so that all SMs get work while the partial tiles stay a small
+  // fraction of the operand bytes
+  const double a_bytes = (double)g.D * 2.0 * (N + 1) * (p->fp64 ? 8.0 : 4.0);
+  const double tile_bytes = (double)g.tile * g.tile * (p->fp64 ? 8.0 : 4.0);
+  int s_traffic = (int)std::max(1.0, ceil(a_bytes / (4.0 * g.npairs * tile_bytes)));
+  int s_ctas = std::max(1, kMaxGramCtas / g.npairs);
+  int S = std::max(1, std::min({g.nchunks, s_ctas, s_traffic}));
+  g.chunks_per_split = (g.nchunks + S - 1) / S;
+  g.splits = (g.nchunks + g.chunks_per_split - 1) / g.chunks_per_split;
+  return g;
+}
+
+mm_status coeffs_impl(mm_plan p, const int64_t* off, const double* t, const double* logp, int N, double t0,
+                      double t1, void* coeffs, int32_t* N_used, cudaStream_t st) {
+  const int D = p->desc.D;
+  p->last = st;
+  {
+    StageScope sc(p, MM_STAGE_PREP, st);
+    MM_CUDA(launch_bounds(off, t, D, p->desc.max_events, t0, t1, p->bounds, p->status, st));
+  }
+  if (N <= 0) {
+    {
+      StageScope sc(p, MM_STAGE_PREP, st, 2);
+      MM_CUDA(launch_min_gap(off, t, D, p->bounds, p->gapbits, p->status + 2, p->status, st));
+    }
+    int hv[3];
+    MM_CUDA(cudaMemcpyAsync(hv, p->status, sizeof(hv), cudaMemcpyDeviceToHost, st));
+    MM_CUDA(cudaStreamSynchronize(st));
+    if (hv[1]) return hv[0] ? flags_to_status(hv[0]) : MM_ERR_INVALID_ARG;
+    if (hv[2] < 0) return MM_ERR_CUTOFF;
+    N = hv[2];
+  }
+  if (N > p->desc.N_max) return MM_ERR_CUTOFF;
+  if (p->desc.basis == MM_BASIS_FEJER && N < 1) return MM_ERR_CUTOFF;
+  mm_status r = configure(p, N);
+  if (r != MM_OK) return r;
+  r = ensure_tables(p, N, st);
+  if (r != MM_OK) return r;
+  {
+    StageScope sc(p, MM_STAGE_SPREAD, st);
+    if (p->fp64) MM_CUDA(launch_spread_f64(off, t, logp, p->bounds, p->sp, (double*)p->grid, p->status, st));
+    else MM_CUDA(launch_spread_f32(off, t, logp, p->bounds, p->sp, (float*)p->grid, p->status, st));
+  }
+  {
+    StageScope sc(p, MM_STAGE_FFT_COLS, st);
+    if (p->fp64) MM_CUDA(launch_fft_cols_f64((double*)p->grid, p->fft, D, p->W, p->status, st));
+    else MM_CUDA(launch_fft_cols_f32((float*)p->grid, p->fft, D, p->W, p->status, st));
+  }
+  {
+    StageScope sc(p, MM_STAGE_FFT_ROWS, st);
+    if (p->fp64)
+      MM_CUDA(launch_fft_rows_f64((const double*)p->grid, p->fft, D, p->W, p->U, p->decon, coeffs, p->status, st));
+    else
+      MM_CUDA(launch_fft_rows_f32((const float*)p->grid, p->fft, D, p->W, p->U, p->decon, coeffs, p->status, st));
+  }
+  if (N_used) *N_used = N;
+  return MM_OK;
+}
+
+mm_status corr_impl(mm_plan p, const void* coeffs, int N, void* sigma, void* R, cudaStream_t st) {
+  if (N < 0 || N > p->desc.N_max) return MM_ERR_CUTOFF;
+  if (p->desc.basis == MM_BASIS_FEJER && N < 1) return MM_ERR_CUTOFF;
+  p->last = st;
+  GramParams g = gram_params(p, N);
+  if ((size_t)g.npairs * g.splits * g.tile * g.tile * p->rs > p->partial_bytes) return MM_ERR_UNSUPPORTED;
+  if (p->w_N != N || p->w_basis != (int)p->desc.basis) {
+    StageScope sc(p, MM_STAGE_SETUP, st);
+    MM_CUDA(launch_gram_weights(p->desc.basis, N, p->fp64, p->wsq, st));
+    p->w_N = N;
+    p->w_basis = p->desc.basis;
+  }
+  {
+    StageScope sc(p, MM_STAGE_GRAM, st);
+    if (p->fp64) MM_CUDA(launch_gram_f64(coeffs, g, (const double*)p->wsq, (double*)p->partial, st));
+    else
+      MM_CUDA(launch_gram_tc(p->desc.prec == MM_PREC_MIXED_BF16X3 ? 0 : 1, coeffs, g, (const float*)p->wsq,
+                             (float*)p->partial, p->status, st));
+  }
+  {
+    StageScope sc(p, MM_STAGE_REDUCE, st);
+    MM_CUDA(launch_reduce_corr(p->fp64, p->partial, g, sigma, R, p->status, st));
+  }
+  p->gram = g;
+  return MM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t mm_version(void) { return 100; }
+
+const char* mm_status_string(mm_status s) {
+  switch (s) {
+    case MM_OK: return "ok";
+    case MM_ERR_INVALID_ARG: return "invalid argument";
+    case MM_ERR_UNSORTED: return "event times not increasing within an asset";
+    case MM_ERR_DUPLICATE_TIME: return "repeated event time within an asset";
+    case MM_ERR_DEGENERATE_SPAN: return "empty or degenerate time span";
+    case MM_ERR_CUTOFF: return "cutoff N out of range";
+    case MM_ERR_OOM: return "device allocation failed";
+    case MM_ERR_CUDA: return "CUDA error";
+    case MM_ERR_TIMEOUT: return "bounded device wait timed out";
+    case MM_ERR_ZERO_VARIANCE: return "zero-variance asset (NaN correlations)";
+    case MM_ERR_NONFINITE: return "non-finite time or log-price";
+    case MM_ERR_UNSUPPORTED: return "unsupported request";
+  }
+  return "unknown status";
+}
+
+mm_status mm_plan_create(const mm_plan_desc* desc, mm_plan* out) {
+  if (!out) return MM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!desc) return MM_ERR_INVALID_ARG;
+  const mm_plan_desc& d = *desc;
+  if (d.D < 1 || d.N_max < 0 || d.max_events < 0) return MM_ERR_INVALID_ARG;
+  if (!(d.tol > 0.0 && d.tol < 0.5)) return MM_ERR_INVALID_ARG;
+  if (d.kernel < MM_KERNEL_GAUSS || d.kernel > MM_KERNEL_ES) return MM_ERR_INVALID_ARG;
+  if (d.basis < MM_BASIS_DIRICHLET || d.basis > MM_BASIS_FEJER) return MM_ERR_INVALID_ARG;
+  if (d.prec < MM_PREC_FP64 || d.prec > MM_PREC_MIXED_3XTF32) return MM_ERR_INVALID_ARG;
+  if (d.spread_tile < 0 || d.spread_tile > 50000) return MM_ERR_INVALID_ARG;
+  for (int i = 0; i < 6; ++i)
+    if (d.reserved[i] != 0) return MM_ERR_INVALID_ARG;
+  const int msp = msp_rule(d.kernel, d.tol);
+  if (msp < 1 || msp > 30) return MM_ERR_UNSUPPORTED;
+
+  mm_plan p = new mm_plan_s();
+  p->desc = d;
+  p->fp64 = d.prec == MM_PREC_FP64;
+  p->cs = p->fp64 ? 16 : 8;
+  p->rs = p->fp64 ? 8 : 4;
+  p->msp = msp;
+  p->khi = msp;
+  p->klo = d.kernel == MM_KERNEL_GAUSS ? -msp + 1 : -msp;
+  int64_t n;
+  int P, Q;
+  if (!choose_fft(std::max<int64_t>(2 * (int64_t)d.N_max + 1, msp + 1), &n, &P, &Q)) {
+    delete p;
+    return MM_ERR_UNSUPPORTED;
+  }
+  p->n_max = n;
+  if (cudaGetDevice(&p->dev) != cudaSuccess) {
+    delete p;
+    return MM_ERR_CUDA;
+  }
+  const size_t D = (size_t)d.D;
+  const size_t Np1 = (size_t)d.N_max + 1;
+  mm_status r = MM_OK;
+  auto A = [&](void** ptr, size_t bytes) {
+    if (r == MM_OK) r = dalloc(p, ptr, bytes);
+  };
+  A(&p->grid, D * 2 * (size_t)n * p->rs);
+  A(&p->W, (size_t)n * p->cs);
+  A(&p->U, Np1 * p->cs);
+  A(&p->decon, Np1 * p->rs);
+  A((void**)&p->glx, kGlNodes * sizeof(double));
+  A((void**)&p->glw, kGlNodes * sizeof(double));
+  A((void**)&p->bounds, 2 * sizeof(double));
+  A((void**)&p->status, 4 * sizeof(int));
+  A((void**)&p->gapbits, sizeof(unsigned long long));
+  A(&p->wsq, Np1 * p->rs);
+  {
+    GramParams g = gram_params(p, d.N_max);
+    size_t ctas = std::max<size_t>((size_t)kMaxGramCtas, (size_t)g.npairs);
+    p->partial_bytes = ctas * g.tile * g.tile * p->rs;
+    A(&p->partial, p->partial_bytes);
+  }
+  if (d.max_events > 0) {
+    A((void**)&p->s_off, (D + 1) * sizeof(int64_t));
+    A((void**)&p->s_t, (size_t)d.max_events * sizeof(double));
+    A((void**)&p->s_p, (size_t)d.max_events * sizeof(double));
+    A(&p->s_coef, D * Np1 * p->cs);
+    A(&p->s_sigma, D * D * p->rs);
+    A(&p->s_R, D * D * p->rs);
+  }
+  if (r == MM_OK) {
+    if (cudaMemset(p->status, 0, 4 * sizeof(int)) != cudaSuccess) r = MM_ERR_CUDA;
+  }
+  if (r == MM_OK) {
+    if (launch_gl_nodes(kGlNodes, p->glx, p->glw, 0) != cudaSuccess) r = MM_ERR_CUDA;
+    p->launches += 1;
+    p->nl[MM_STAGE_SETUP] += 1;
+  }
+  if (r == MM_OK && cudaDeviceSynchronize() != cudaSuccess) r = MM_ERR_CUDA;
+  if (r != MM_OK) {
+    free_all(p);
+    delete p;
+    cudaGetLastError();
+    return r;
+  }
+  *out = p;
+  return MM_OK;
+}
+
+mm_status mm_destroy(mm_plan p) {
+  if (!p) return MM_ERR_INVALID_ARG;
+  int cur = -1;
+  const int dev = p->dev;
+  cudaGetDevice(&cur);
+  if (cur != dev) cudaSetDevice(dev);
+  cudaDeviceSynchronize();
+  free_all(p);
+  delete p;
+  if (cur >= 0 && cur != dev) cudaSetDevice(cur);
+  return MM_OK;
+}
+
+mm_status mm_coeffs(mm_plan p, const int64_t* d_offsets, const double* d_t, const double* d_logp, int32_t N,
+                    double t0, double t1, void* d_coeffs, int32_t* N_used, void* stream) {
+  mm_status r = check_plan(p);
+  if (r != MM_OK) return r;
+  if (!d_offsets || !d_t || !d_logp || !d_coeffs) return MM_ERR_INVALID_ARG;
+  if (!(isfinite(t0) && isfinite(t1))) return MM_ERR_INVALID_ARG;
+  return coeffs_impl(p, d_offsets, d_t, d_logp, N, t0, t1, d_coeffs, N_used, (cudaStream_t)stream);
+}
+
+mm_status mm_cov(mm_plan p, const void* d_coeffs, int32_t N, void* d_sigma, void* stream) {
+  mm_status r = check_plan(p);
+  if (r != MM_OK) return r;
+  if (!d_coeffs || !d_sigma) return MM_ERR_INVALID_ARG;
+  return corr_impl(p, d_coeffs, N, d_sigma, nullptr, (cudaStream_t)stream);
+}
+
+mm_status mm_corr(mm_plan p, const void* d_coeffs, int32_t N, void* d_sigma_or_null, void* d_R, void* stream) {
+  mm_status r = check_plan(p);
+  if (r != MM_OK) return r;
+  if (!d_coeffs || !d_R) return MM_ERR_INVALID_ARG;
+  return corr_impl(p, d_coeffs, N, d_sigma_or_null, d_R, (cudaStream_t)stream);
+}
+
+mm_status mm_estimate(mm_plan p, const int64_t* d_offsets, const double* d_t, const double* d_logp, int32_t N,
+                      double t0, double t1, void* d_coeffs, void* d_sigma_or_null, void* d_R, int32_t* N_used,
+                      void* stream) {
+  mm_status r = check_plan(p);
+  if (r != MM_OK) return r;
+  if (!d_offsets || !d_t || !d_logp || !d_coeffs || !d_R) return MM_ERR_INVALID_ARG;
+  if (!(isfinite(t0) && isfinite(t1))) return MM_ERR_INVALID_ARG;
+  int32_t Nu = 0;
+  r = coeffs_impl(p, d_offsets, d_t, d_logp, N, t0, t1, d_coeffs, &Nu, (cudaStream_t)stream);
+  if (r != MM_OK) return r;
+  if (N_used) *N_used = Nu;
+  return corr_impl(p, d_coeffs, Nu, d_sigma_or_null, d_R, (cudaStream_t)stream);
+}
+
+mm_status mm_estimate_host(mm_plan p, const int64_t* h_offsets, const double* h_t, const double* h_logp, int32_t N,
+                           double t0, double t1, void* h_coeffs_or_null, void* h_sigma_or_null, void* h_R,
+                           int32_t* N_used, void* stream) {
+  mm_status r = check_plan(p);
+  if (r != MM_OK) return r;
+  if (!h_offsets || !h_t || !h_logp || !h_R || !p->s_off) return MM_ERR_INVALID_ARG;
+  const int D = p->desc.D;
+  const int64_t ne = h_offsets[D];
+  if (h_offsets[0] != 0 || ne < 0 || ne > p->desc.max_events) return MM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  MM_CUDA(cudaMemcpyAsync(p->s_off, h_offsets, (size_t)(D + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  if (ne > 0) {
+    MM_CUDA(cudaMemcpyAsync(p->s_t, h_t, (size_t)ne * sizeof(double), cudaMemcpyHostToDevice, st));
+    MM_CUDA(cudaMemcpyAsync(p->s_p, h_logp, (size_t)ne * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  int32_t Nu = 0;
+  r = mm_estimate(p, p->s_off, p->s_t, p->s_p, N, t0, t1, p->s_coef, p->s_sigma, p->s_R, &Nu, stream);
+  if (r != MM_OK) {
+    cudaStreamSynchronize(st);
+    return r;
+  }
+  const size_t dd = (size_t)D * D * p->rs;
+  MM_CUDA(cudaMemcpyAsync(h_R, p->s_R, dd, cudaMemcpyDeviceToHost, st));
+  if (h_sigma_or_null) MM_CUDA(cudaMemcpyAsync(h_sigma_or_null, p->s_sigma, dd, cudaMemcpyDeviceToHost, st));
+  if (h_coeffs_or_null)
+    MM_CUDA(cudaMemcpyAsync(h_coeffs_or_null, p->s_coef, (size_t)D * (Nu + 1) * p->cs, cudaMemcpyDeviceToHost, st));
+  if (N_used) *N_used = Nu;
+  return mm_plan_sync(p);
+}
+
+mm_status mm_nyquist(mm_plan p, const int64_t* d_offsets, const double* d_t, double t0, double t1, int32_t* N_out,
+                     void* stream) {
+  mm_status r = check_plan(p);
+  if (r != MM_OK) return r;
+  if (!d_offsets || !d_t || !N_out) return MM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  p->last = st;
+  {
+    StageScope sc(p, MM_STAGE_PREP, st);
+    MM_CUDA(launch_bounds(d_offsets, d_t, p->desc.D, p->desc.max_events, t0, t1, p->bounds, p->status, st));
+  }
+  {
+    StageScope sc(p, MM_STAGE_PREP, st, 2);
+    MM_CUDA(launch_min_gap(d_offsets, d_t, p->desc.D, p->bounds, p->gapbits, p->status + 2, p->status, st));
+  }
+  int hv[3];
+  MM_CUDA(cudaMemcpyAsync(hv, p->status, sizeof(hv), cudaMemcpyDeviceToHost, st));
+  MM_CUDA(cudaStreamSynchronize(st));
+  if (hv[0] & (ST_DUPLICATE | ST_UNSORTED)) {
+    int z = 0;
+    cudaMemcpy(p->status, &z, sizeof(int), cudaMemcpyHostToDevice);
+    return flags_to_status(hv[0]);
+  }
+  if (hv[1]) return hv[0] ? flags_to_status(hv[0]) : MM_ERR_INVALID_ARG;
+  if (hv[2] < 0) return MM_ERR_CUTOFF;
+  *N_out = hv[2];
+  return MM_OK;
+}
+
+mm_status mm_plan_sync(mm_plan p) {
+  mm_status r = check_plan(p);
+  if (r != MM_OK) return r;
+  if (p->last) MM_CUDA(cudaStreamSynchronize(p->last));
+  else MM_CUDA(cudaDeviceSynchronize());
+  int f = 0;
+  MM_CUDA(cudaMemcpy(&f, p->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (f) MM_CUDA(cudaMemset(p->status, 0, sizeof(int)));
+  return flags_to_status(f);
+}
+
+mm_status mm_plan_get_info(mm_plan p, mm_plan_info* info) {
+  if (!p || !info) return MM_ERR_INVALID_ARG;
+  memset(info, 0, sizeof(*info));
+  info->msp = p->msp;
+  info->N = p->cfg_N;
+  info->Mr = p->Mr;
+  info->fft_P = p->fft.P;
+  info->fft_Q = p->fft.Q;
+  info->workspace_bytes = p->workspace;
+  info->launches = p->launches;
+  info->gram_splits = p->gram.splits;
+  return MM_OK;
+}
+
+mm_status mm_profile_enable(mm_plan p, int32_t on) {
+  if (!p) return MM_ERR_INVALID_ARG;
+  p->prof = on != 0;
+  return MM_OK;
+}
+
+mm_status mm_profile_read(mm_plan p, double* ms, int64_t* launches, int32_t reset) {
+  if (!p) return MM_ERR_INVALID_ARG;
+  for (auto& e : p->pending) {
+    float v = 0.f;
+    if (cudaEventSynchronize(e.b) == cudaSuccess && cudaEventElapsedTime(&v, e.a, e.b) == cudaSuccess)
+      p->ms[e.stage] += v;
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  p->pending.clear();
+  for (int i = 0; i < MM_NUM_STAGES; ++i) {
+    if (ms) ms[i] = p->ms[i];
+    if (launches) launches[i] = p->nl[i];
+  }
+  if (reset) {
+    for (int i = 0; i < MM_NUM_STAGES; ++i) {
+      p->ms[i] = 0;
+      p->nl[i] = 0;
+    }
+  }
+  cudaGetLastError();
+  return MM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+// mm_common.cuh -- shared device types, parameters and launch declarations of
+// the GB300 Malliavin-Mancino NUFFT library (internal; not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mm.h"
+
+namespace mmgpu {
+
+// Device status bits, OR-ed by kernels into the plan's status word; the host
+// maps the lowest set bit to an mm_status.
+enum : int {
+  ST_BAD_OFFSETS = 1 << 0,
+  ST_UNSORTED = 1 << 1,
+  ST_DUPLICATE = 1 << 2,
+  ST_SPAN = 1 << 3,
+  ST_NONFINITE = 1 << 4,
+  ST_TIMEOUT = 1 << 5,
+  ST_ZERO_VAR = 1 << 6,
+  ST_CUTOFF = 1 << 7,
+  ST_OUT_OF_WINDOW = 1 << 8,
+};
+
+template <typename T>
+struct Cplx {
+  T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ Cplx<T> cmul(Cplx<T> a, Cplx<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T>
+__device__ __forceinline__ Cplx<T> cadd(Cplx<T> a, Cplx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T>
+__device__ __forceinline__ Cplx<T> csub(Cplx<T> a, Cplx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T>
+__device__ __forceinline__ Cplx<T> cconj(Cplx<T> a) { return {a.x, -a.y}; }
+// multiply by -i
+template <typename T>
+__device__ __forceinline__ Cplx<T> cmul_mi(Cplx<T> a) { return {a.y, -a.x}; }
+
+constexpr int kMaxRadices = 12;
+constexpr int kMaxFftLen = 1024;   // largest P or Q of the two-pass FFT
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// Spreading parameters (Sec. 2.2.5 and Algorithms 8-10), all derived on the
+// host from (kernel, tol, N, M_r).
+struct SpreadParams {
+  int D;
+  int64_t Mr;        // grid size
+  int tile;          // cells per block
+  int ntiles;        // blocks per asset
+  int msp;           // M_sp
+  int klo, khi;      // stencil offsets k in [klo, khi] around b0
+  int kernel;        // mm_kernel
+  int single_tile;   // 1: one block covers the whole (small) grid
+  // kernel constants
+  double es_beta;    // ES: beta
+  double es_inv_w;   // ES: 1 / M_sp  (support half-width in cells)
+  double g_t1;       // Gaussian: t1 of Algorithm 8 (exponent per cell^2)
+  double kb_b;       // KB: b = pi (2 - 1/sigma)
+  double kb_inv_phi0;// KB: 1 / phi(0) (kernel normalised to peak 1)
+  int64_t max_events;
+};
+
+struct FftParams {
+  int64_t n;         // complex length = Mr / 2
+  int P, Q;          // n = P * Q
+  int nrad_p, nrad_q;
+  int rad_p[kMaxRadices], rad_q[kMaxRadices];
+  int cols;          // pass 1: columns (j2 values) per block
+  int rowblk;        // pass 2: lower rows per block
+  int H;             // pass 2: number of lower rows = P/2 + 1
+  int N;             // cutoff
+};
+
+struct GramParams {
+  int D;
+  int N;             // modes k = 0..N
+  int ld;            // leading dimension (complex elements) of the coefficients
+  int tile;          // output tile edge (128 tensor path, 64 fp64 path)
+  int ntiles;        // ceil(D / tile)
+  int npairs;        // ntiles (ntiles+1) / 2
+  int splits;        // split-K factor
+  int chunk;         // complex modes per K-chunk
+  int nchunks;       // ceil((N+1) / chunk)
+  int chunks_per_split;
+};
+
+// ---------------------------------------------------------------- launchers
+// Each returns cudaGetLastError() of its launch.
+cudaError_t launch_bounds(const int64_t* off, const double* t, int D, int64_t max_events,
+                          double w0, double w1, double* bounds, int* status, cudaStream_t s);
+cudaError_t launch_min_gap(const int64_t* off, const double* t, int D, const double* bounds,
+                           unsigned long long* gapbits, int* nyq, int* status, cudaStream_t s);
+cudaError_t launch_spread_f32(const int64_t* off, const double* t, const double* logp,
+                              const double* bounds, const SpreadParams& p, float* grid,
+                              int* status, cudaStream_t s);
+cudaError_t launch_spread_f64(const int64_t* off, const double* t, const double* logp,
+                              const double* bounds, const SpreadParams& p, double* grid,
+                              int* status, cudaStream_t s);
+
+cudaError_t launch_gl_nodes(int nq, double* x, double* w, cudaStream_t s);
+cudaError_t launch_setup_tables(int kernel, int msp, int64_t Mr, int N, int64_t n,
+                                const SpreadParams& sp, double tau, const double* glx,
+                                const double* glw, int nq, void* W, void* U, void* decon,
+                                bool fp64, cudaStream_t s);
+cudaError_t launch_fft_cols_f32(float* grid, const FftParams& f, int D, const void* W, const int* status, cudaStream_t s);
+cudaError_t launch_fft_cols_f64(double* grid, const FftParams& f, int D, const void* W, const int* status, cudaStream_t s);
+cudaError_t launch_fft_rows_f32(const float* grid, const FftParams& f, int D, const void* W,
+                                const void* U, const void* decon, void* coeffs, const int* status, cudaStream_t s);
+cudaError_t launch_fft_rows_f64(const double* grid, const FftParams& f, int D, const void* W,
+                                const void* U, const void* decon, void* coeffs, const int* status, cudaStream_t s);
+size_t fft_cols_smem(const FftParams& f, bool fp64);
+size_t fft_rows_smem(const FftParams& f, bool fp64);
+
+cudaError_t launch_gram_weights(int basis, int N, bool fp64, void* wsq, cudaStream_t s);
+cudaError_t launch_gram_f64(const void* coeffs, const GramParams& g, const double* wsq,
+                            double* partial, cudaStream_t s);
+cudaError_t launch_gram_tc(int mode, const void* coeffs, const GramParams& g, const float* wsq,
+                           float* partial, int* status, cudaStream_t s);
+cudaError_t launch_reduce_corr(bool fp64, const void* partial, const GramParams& g,
+                               void* sigma, void* R, int* status, cudaStream_t s);
+size_t gram_tc_smem(int mode, bool two_tiles);
+
+}  // namespace mmgpu

@@ -1,0 +1,453 @@
+// mm_gram.cu -- stage (d) of the hot path: the covariance of Algorithm 3
+// step C (Eqs. (2)/(3)) as a Hermitian rank-(2N+1) update of the
+// coefficients, and the correlation of its last step.
+//
+// With F-convention coefficients F_i(k) (k = 0..N) and basis weights w_k,
+//   Sigma_ij = (2 pi)^2 sum_{|k|<=N} w_k conj(F_i(k)) F_j(k)
+//            = sum_{k=0..N} W_k (Re F_i Re F_j + Im F_i Im F_j) (2 pi)^2,
+// W_0 = w_0, W_k = 2 w_k (k >= 1), because the terms of k and -k are complex
+// conjugates. So Sigma = A A^T for the real D x 2(N+1) matrix A whose row i
+// is (F_i(k) interleaved re, im) scaled by s_k = 2 pi sqrt(W_k): a real SYRK
+// whose K-major operand is exactly the complex64 coefficient array.
+//
+// Mixed precision: one CTA per (output tile pair, K-split) stages 128-row
+// tiles of A in shared memory (converted to split bf16 or split tf32 in the
+// canonical 128-byte-swizzled K-major layout), and one thread issues
+// tcgen05.mma (hi*hi + hi*lo + lo*hi) into a TMEM accumulator; commits are
+// tracked by mbarriers so the next tile is staged while the tensor core runs.
+// Every wait is bounded: after ~1 s it records MM_ERR_TIMEOUT and the CTA
+// drains and frees its TMEM.
+// FP64: a CUDA-core tiled kernel. Both write per-split partial tiles that
+// k_reduce_corr sums in FP64 before the FP64 correlation normalisation.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "mm_common.cuh"
+
+namespace mmgpu {
+
+// ------------------------------------------------------------ weights
+template <typename T>
+__global__ void k_gram_weights(int basis, int N, T* wsq) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > N) return;
+  const double w = (basis == MM_BASIS_DIRICHLET) ? 1.0 / (2.0 * N + 1.0)
+                                                 : (1.0 - (double)k / (double)N) / (N + 1.0);
+  const double W = (k == 0) ? w : 2.0 * w;
+  wsq[k] = (T)(2.0 * kPi * sqrt(fmax(W, 0.0)));
+}
+
+cudaError_t launch_gram_weights(int basis, int N, bool fp64, void* wsq, cudaStream_t s) {
+  const int blocks = (N + 1 + 255) / 256;
+  if (fp64) k_gram_weights<double><<<blocks, 256, 0, s>>>(basis, N, (double*)wsq);
+  else k_gram_weights<float><<<blocks, 256, 0, s>>>(basis, N, (float*)wsq);
+  return cudaGetLastError();
+}
+
+__device__ __forceinline__ void pair_of(int p, int nt, int& I, int& J) {
+  int i = 0;
+  while (p >= nt - i) {
+    p -= nt - i;
+    ++i;
+  }
+  I = i;
+  J = i + p;
+}
+
+// ------------------------------------------------------------ FP64 path
+// 64 x 64 output tile per block, 256 threads with a 4 x 4 micro-tile each,
+// K in chunks of 16 complex modes.
+__global__ void __launch_bounds__(256) k_gram_f64(const double2* __restrict__ F, GramParams g,
+                                                  const double* __restrict__ wsq, double* __restrict__ partial) {
+  __shared__ double As[32][65];
+  __shared__ double Bs[32][65];
+  int I, J;
+  pair_of(blockIdx.y, g.ntiles, I, J);
+  const int s = blockIdx.x;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  const int c0 = s * g.chunks_per_split;
+  const int c1 = min(c0 + g.chunks_per_split, g.nchunks);
+  for (int c = c0; c < c1; ++c) {
+    const int kb = c * 16;
+    for (int idx = threadIdx.x; idx < 2 * 64 * 16; idx += 256) {
+      const int which = idx >> 10;  // 0: A rows, 1: B rows
+      const int r = (idx >> 4) & 63, kk = idx & 15;
+      const int row = (which ? J : I) * 64 + r;
+      const int k = kb + kk;
+      double2 v = {0.0, 0.0};
+      if (row < g.D && k <= g.N) {
+        v = F[(int64_t)row * g.ld + k];
+        const double sc = wsq[k];
+        v.x *= sc;
+        v.y *= sc;
+      }
+      if (which) { Bs[2 * kk][r] = v.x; Bs[2 * kk + 1][r] = v.y; }
+      else { As[2 * kk][r] = v.x; As[2 * kk + 1][r] = v.y; }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kr = 0; kr < 32; ++kr) {
+      double a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { a[q] = As[kr][ty * 4 + q]; b[q] = Bs[kr][tx * 4 + q]; }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+    }
+    __syncthreads();
+  }
+  double* out = partial + ((int64_t)blockIdx.y * g.splits + s) * 64 * 64;
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) out[(ty * 4 + x) * 64 + tx * 4 + y] = acc[x][y];
+}
+
+cudaError_t launch_gram_f64(const void* coeffs, const GramParams& g, const double* wsq, double* partial,
+                            cudaStream_t s) {
+  dim3 grd(g.splits, g.npairs);
+  k_gram_f64<<<grd, 256, 0, s>>>((const double2*)coeffs, g, wsq, partial);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ tcgen05 path
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred P;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, P;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase with the given parity to complete; gives up after
+// limit_ns and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+  }
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand in the canonical
+// 128-byte-swizzle layout (8-row atoms of 128-byte rows, atoms 1024 B apart).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);        // start address
+  d |= (uint64_t)1 << 16;                           // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024u >> 4) << 32;                // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;                           // descriptor version
+  d |= (uint64_t)2 << 61;                           // 128-byte swizzle
+  return d;
+}
+
+template <int MODE>
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if (MODE == 0) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t f32_to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+constexpr int kTcThreads = 128;
+constexpr int kTile = 128;                 // rows per operand tile
+constexpr int kTileBytes = kTile * 128;    // 128-byte rows
+constexpr uint32_t kTmemCols = 128;
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
+
+size_t gram_tc_smem(int, bool two_tiles) {
+  return (size_t)2 /*stages*/ * (two_tiles ? 4 : 2) * kTileBytes + 1024 /*alignment slack*/;
+}
+
+// Byte offset of the 4-byte (bf16 pair) or 8-byte (tf32 pair) element at
+// row r, byte column cb of a 128B-swizzled K-major tile.
+__device__ __forceinline__ uint32_t sw128_off(int r, int cb) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((cb >> 4) ^ (r & 7)) << 4) | (cb & 15)));
+}
+
+// Stage one K-chunk of `rows` coefficient rows (starting at row0) into the
+// hi / lo tiles. MODE 0: 32 complex modes per chunk as bf16 pairs;
+// MODE 1: 16 complex modes per chunk as tf32 pairs.
+template <int MODE>
+__device__ __forceinline__ void stage_tile(const float2* __restrict__ F, const GramParams& g,
+                                           const float* __restrict__ wsq, int row0, int kbase,
+                                           uint8_t* hi, uint8_t* lo) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (MODE == 0) {
+    const int k = kbase + lane;
+    const bool kin = k <= g.N;
+    const float sc = kin ? wsq[k] : 0.0f;
+#pragma unroll 4
+    for (int rr = 0; rr < 32; ++rr) {
+      const int r = warp * 32 + rr;
+      const int row = row0 + r;
+      float2 v = {0.f, 0.f};
+      if (kin && row < g.D) v = F[(int64_t)row * g.ld + k];
+      const float xr = v.x * sc, xi = v.y * sc;
+      const __nv_bfloat16 hr = __float2bfloat16_rn(xr), hi_ = __float2bfloat16_rn(xi);
+      const __nv_bfloat16 lr = __float2bfloat16_rn(xr - __bfloat162float(hr));
+      const __nv_bfloat16 li = __float2bfloat16_rn(xi - __bfloat162float(hi_));
+      __nv_bfloat162 H, L;
+      H.x = hr; H.y = hi_;
+      L.x = lr; L.y = li;
+      const uint32_t off = sw128_off(r, lane * 4);
+      *reinterpret_cast<__nv_bfloat162*>(hi + off) = H;
+      *reinterpret_cast<__nv_bfloat162*>(lo + off) = L;
+    }
+  } else {
+    const int half = lane >> 4, l = lane & 15;
+    const int k = kbase + l;
+    const bool kin = k <= g.N;
+    const float sc = kin ? wsq[k] : 0.0f;
+#pragma unroll 4
+    for (int rr = 0; rr < 16; ++rr) {
+      const int r = warp * 32 + rr * 2 + half;
+      const int row = row0 + r;
+      float2 v = {0.f, 0.f};
+      if (kin && row < g.D) v = F[(int64_t)row * g.ld + k];
+      const float xr = v.x * sc, xi = v.y * sc;
+      const uint32_t hr = f32_to_tf32(xr), hi_ = f32_to_tf32(xi);
+      const uint32_t lr = f32_to_tf32(xr - __uint_as_float(hr));
+      const uint32_t li = f32_to_tf32(xi - __uint_as_float(hi_));
+      const uint32_t off = sw128_off(r, l * 8);
+      *reinterpret_cast<uint2*>(hi + off) = make_uint2(hr, hi_);
+      *reinterpret_cast<uint2*>(lo + off) = make_uint2(lr, li);
+    }
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restrict__ F, GramParams g,
+                                                           const float* __restrict__ wsq,
+                                                           float* __restrict__ partial, int* status) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+
+  int I, J;
+  pair_of(blockIdx.y, g.ntiles, I, J);
+  const bool two = I != J;
+  const int s = blockIdx.x;
+  const int c0 = s * g.chunks_per_split;
+  const int c1 = min(c0 + g.chunks_per_split, g.nchunks);
+  const int nit = c1 - c0;
+
+  // 1024-byte aligned staging area: per stage [A_hi][A_lo]([B_hi][B_lo])
+  const uint32_t base_s = smem_u32(smem_raw);
+  uint8_t* base = smem_raw + (((base_s + 1023u) & ~1023u) - base_s);
+  const int tiles_per_stage = two ? 4 : 2;
+
+  const int rowsJ = min(kTile, g.D - J * kTile);
+  const int Nmma = two ? ((rowsJ + 15) / 16) * 16 : ((min(kTile, g.D - I * kTile) + 15) / 16) * 16;
+  const uint32_t fmt = (MODE == 0) ? 1u : 2u;  // bf16 / tf32 operands
+  const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(Nmma >> 3) << 17) |
+                         ((uint32_t)(kTile >> 4) << 24);
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+
+  const int chunk = g.chunk;
+  bool ok = true;
+  for (int it = 0; it < nit; ++it) {
+    const int st = it & 1;
+    if (it >= 2) {
+      if (!mbar_wait(&bars[st], (uint32_t)(((it >> 1) - 1) & 1), kWaitLimitNs)) ok = false;
+    }
+    if (__syncthreads_or(!ok)) { ok = false; break; }
+    uint8_t* stg = base + (size_t)st * tiles_per_stage * kTileBytes;
+    const int kbase = (c0 + it) * chunk;
+    stage_tile<MODE>(F, g, wsq, I * kTile, kbase, stg, stg + kTileBytes);
+    if (two) stage_tile<MODE>(F, g, wsq, J * kTile, kbase, stg + 2 * kTileBytes, stg + 3 * kTileBytes);
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+      const uint32_t a_hi = smem_u32(stg), a_lo = a_hi + kTileBytes;
+      const uint32_t b_hi = two ? a_hi + 2 * kTileBytes : a_hi;
+      const uint32_t b_lo = two ? a_hi + 3 * kTileBytes : a_lo;
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {  // four 32-byte K steps per 128-byte row
+        const uint32_t o = ks * 32;
+        tc_mma<MODE>(tmem, sw128_desc(a_hi + o), sw128_desc(b_hi + o), idesc, (it > 0 || ks > 0) ? 1u : 0u);
+        tc_mma<MODE>(tmem, sw128_desc(a_hi + o), sw128_desc(b_lo + o), idesc, 1u);
+        tc_mma<MODE>(tmem, sw128_desc(a_lo + o), sw128_desc(b_hi + o), idesc, 1u);
+      }
+      tc_commit(&bars[st]);
+    }
+  }
+  // drain: the last commit covers every MMA issued before it
+  if (nit > 0) {
+    const int last = nit - 1;
+    if (!mbar_wait(&bars[last & 1], (uint32_t)((last >> 1) & 1), ok ? kWaitLimitNs : kWaitLimitNs / 4)) ok = false;
+  }
+  if (!ok) atomicOr(&s_fail, 1);
+  tc_fence_after();
+  __syncthreads();
+
+  float* out = partial + ((int64_t)blockIdx.y * g.splits + s) * kTile * kTile;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = warp * 32 + lane;
+  if (!s_fail && nit > 0) {
+    for (int c = 0; c < Nmma; c += 16) {
+      uint32_t v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+      float4* o4 = reinterpret_cast<float4*>(out + (int64_t)r * kTile + c);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        o4[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                            __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+    }
+  } else {
+    for (int c = 0; c < Nmma; ++c) out[(int64_t)r * kTile + c] = (nit > 0) ? __int_as_float(0x7fc00000) : 0.f;
+    if (threadIdx.x == 0 && nit > 0) atomicOr(status, ST_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+cudaError_t launch_gram_tc(int mode, const void* coeffs, const GramParams& g, const float* wsq, float* partial,
+                           int* status, cudaStream_t s) {
+  const bool two = g.ntiles > 1;
+  const size_t smem = gram_tc_smem(mode, two);
+  dim3 grd(g.splits, g.npairs);
+  cudaError_t e;
+  if (mode == 0) {
+    e = cudaFuncSetAttribute(k_gram_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gram_tc<0><<<grd, kTcThreads, smem, s>>>((const float2*)coeffs, g, wsq, partial, status);
+  } else {
+    e = cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gram_tc<1><<<grd, kTcThreads, smem, s>>>((const float2*)coeffs, g, wsq, partial, status);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ reduce + R
+// Sums the split partials in FP64 for a 16 x 16 block of (i, j), i-block <=
+// j-block, and writes Sigma and R = Sigma_ij / (sqrt(Sigma_ii) sqrt(Sigma_jj))
+// to both triangles. R_ii is exactly 1; zero variance gives NaN and a status.
+template <typename TP>
+__device__ __forceinline__ double sum_splits(const TP* __restrict__ partial, const GramParams& g, int i, int j) {
+  const int I = i / g.tile, J = j / g.tile;
+  const int p = I * g.ntiles - I * (I - 1) / 2 + (J - I);
+  const int64_t base = (int64_t)p * g.splits * g.tile * g.tile + (int64_t)(i % g.tile) * g.tile + (j % g.tile);
+  const int64_t step = (int64_t)g.tile * g.tile;
+  double acc = 0.0;
+  for (int s = 0; s < g.splits; ++s) acc += (double)partial[base + s * step];
+  return acc;
+}
+
+template <typename TP, typename TO>
+__global__ void __launch_bounds__(256) k_reduce_corr(const TP* __restrict__ partial, GramParams g,
+                                                     TO* __restrict__ sigma, TO* __restrict__ R, int* status) {
+  __shared__ double s_di[16], s_dj[16];
+  const int nb = (g.D + 15) / 16;
+  int bi, bj;
+  pair_of(blockIdx.x, nb, bi, bj);
+  const int li = threadIdx.x >> 4, lj = threadIdx.x & 15;
+  if (threadIdx.x < 32) {
+    const int q = threadIdx.x & 15;
+    const int d = (threadIdx.x < 16 ? bi : bj) * 16 + q;
+    const double v = (d < g.D) ? sum_splits(partial, g, d, d) : 1.0;
+    if (threadIdx.x < 16) s_di[q] = v;
+    else s_dj[q] = v;
+  }
+  __syncthreads();
+  const int i = bi * 16 + li, j = bj * 16 + lj;
+  if (i >= g.D || j >= g.D || (bi == bj && j < i)) return;
+  const double v = (i == j) ? s_di[li] : sum_splits(partial, g, i, j);
+  const double a = s_di[li], b = s_dj[lj];
+  double r;
+  if (a > 0.0 && b > 0.0) r = (i == j) ? 1.0 : v / (sqrt(a) * sqrt(b));
+  else {
+    r = __longlong_as_double(0x7ff8000000000000ll);
+    atomicOr(status, ST_ZERO_VAR);
+  }
+  if (sigma) {
+    sigma[(int64_t)i * g.D + j] = (TO)v;
+    sigma[(int64_t)j * g.D + i] = (TO)v;
+  }
+  if (R) {
+    R[(int64_t)i * g.D + j] = (TO)r;
+    R[(int64_t)j * g.D + i] = (TO)r;
+  }
+}
+
+cudaError_t launch_reduce_corr(bool fp64, const void* partial, const GramParams& g, void* sigma, void* R,
+                               int* status, cudaStream_t s) {
+  const int nb = (g.D + 15) / 16;
+  const int blocks = nb * (nb + 1) / 2;
+  if (fp64)
+    k_reduce_corr<double, double><<<blocks, 256, 0, s>>>((const double*)partial, g, (double*)sigma, (double*)R,
+                                                          status);
+  else
+    k_reduce_corr<float, float><<<blocks, 256, 0, s>>>((const float*)partial, g, (float*)sigma, (float*)R, status);
+  return cudaGetLastError();
+}
+
+}  // namespace mmgpu

@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle
+on the same seeded inputs.
+
+Tolerances (stated for the method, not tuned): coefficients, relative l2
+error per asset (Eq. (15)) <= 1e-10 at tol 1e-12 on the FP64 path and <= 1e-5
+at tol 1e-6 on the FP32 path; Sigma, max |dSigma_ij| / sqrt(Sigma_ii Sigma_jj)
+<= 1e-9 (FP64) and <= 1e-4 (mixed); correlation max |dR| <= 1e-9 (FP64) and
+<= 1e-4 (mixed precision contraction).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2003_02842_gb300 import synth
+
+from gpu_helpers import rel_l2_rows, run, sigma_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": dict(tol=1e-12, coef=1e-10, sig=1e-9, R=1e-9),
+       "bf16x3": dict(tol=1e-6, coef=1e-5, sig=1e-4, R=1e-4),
+       "3xtf32": dict(tol=1e-6, coef=1e-5, sig=1e-4, R=1e-4)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _ragged(seed=3):
+    # assets with 0, 1, 2 and many events, times on a continuum
+    ev = synth.random_events(seed, D=6, n_range=(3, 300), T=5000.0)
+    ts = [ev.asset(i)[0] for i in range(ev.D)]
+    ps = [ev.asset(i)[1] for i in range(ev.D)]
+    ts[1], ps[1] = ts[1][:0], ps[1][:0]
+    ts[2], ps[2] = ts[2][:1], ps[2][:1]
+    ts[3], ps[3] = ts[3][:2], ps[3][:2]
+    return synth.from_lists(ts, ps)
+
+
+WORKLOADS = {
+    "c1_sync": lambda: (synth.c1_sync(0), 500),
+    "c2_async": lambda: (lambda e: (e, e.meta["N"]))(synth.c2_async(0)),
+    "ragged": lambda: (_ragged(), 97),
+}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("kernel", ["gauss", "kb", "es"])
+@pytest.mark.parametrize("wl", list(WORKLOADS))
+def test_coefficients_match_direct_sum(prec, kernel, wl):
+    ev, N = WORKLOADS[wl]()
+    tl = TOL[prec]
+    out = run(dict(tol=tl["tol"], kernel=kernel, basis="dirichlet", prec=prec), ev, N)
+    no_returns = np.any(np.diff(ev.offsets) < 2)
+    assert out["status"] == (9 if no_returns else 0)  # MM_ERR_ZERO_VARIANCE for assets without returns
+    ref = oracle.coeffs_F(ev.offsets, ev.t, ev.logp, N)
+    err = rel_l2_rows(out["F"], ref)
+    assert np.all(err <= tl["coef"]), err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "3xtf32"])
+@pytest.mark.parametrize("basis", ["dirichlet", "fejer"])
+@pytest.mark.parametrize("wl", list(WORKLOADS))
+def test_covariance_and_correlation(prec, basis, wl):
+    ev, N = WORKLOADS[wl]()
+    tl = TOL[prec]
+    out = run(dict(tol=tl["tol"], kernel="es", basis=basis, prec=prec), ev, N)
+    ref = oracle.estimate(ev.offsets, ev.t, ev.logp, N=N, basis=basis)
+    ok = np.diag(ref["Sigma"]) > 0
+    if not ok.all():
+        assert out["status"] == 9  # MM_ERR_ZERO_VARIANCE: NaN rows of R are expected
+    else:
+        assert out["status"] == 0
+    S = out["S"].astype(np.float64)
+    assert sigma_err(S, ref["Sigma"]) <= tl["sig"]
+    R = out["R"].astype(np.float64)
+    sub = np.ix_(ok, ok)
+    assert np.max(np.abs(R[sub] - ref["R"][sub])) <= tl["R"]
+    assert np.all(np.diag(R)[ok] == 1.0)
+    assert np.all(np.isnan(R[~ok, :]))
+    assert np.array_equal(S, S.T) and np.array_equal(R, R.T, equal_nan=True)
+
+
+@pytest.mark.parametrize("tile", [64, 257, 1000])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_many_tiles_and_periodic_halos(tile, prec):
+    # small spreading tiles: most events feed two tiles and the first and last
+    # tiles exchange halos across the periodic wrap
+    ev = synth.c2_async(1)
+    N = 333
+    tl = TOL[prec]
+    for kernel in ("gauss", "kb", "es"):
+        out = run(dict(tol=tl["tol"], kernel=kernel, basis="dirichlet", prec=prec, spread_tile=tile), ev, N)
+        assert out["status"] == 0
+        ref = oracle.coeffs_F(ev.offsets, ev.t, ev.logp, N)
+        assert np.all(rel_l2_rows(out["F"], ref) <= tl["coef"])
+
+
+@pytest.mark.parametrize("N", [1, 2, 7, 15, 64, 121, 1000])
+def test_cutoffs_small_and_non_smooth(N):
+    ev = synth.random_events(11, D=3, n_range=(50, 400), T=2000.0)
+    for prec in ("fp64", "bf16x3"):
+        tl = TOL[prec]
+        out = run(dict(tol=tl["tol"], kernel="es", basis="fejer", prec=prec), ev, N)
+        ref = oracle.estimate(ev.offsets, ev.t, ev.logp, N=N, basis="fejer")
+        assert np.all(rel_l2_rows(out["F"], ref["F"]) <= tl["coef"])
+        assert np.max(np.abs(out["R"].astype(np.float64) - ref["R"])) <= tl["R"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "3xtf32"])
+def test_many_assets_multi_tile_contraction(prec):
+    # D > 128 exercises off-diagonal 128 x 128 (64 x 64 for FP64) output tiles
+    ev = synth.random_events(21, D=300, n_range=(2, 60), T=3000.0)
+    N = 60
+    tl = TOL[prec]
+    out = run(dict(tol=tl["tol"], kernel="es", basis="dirichlet", prec=prec), ev, N)
+    ref = oracle.estimate(ev.offsets, ev.t, ev.logp, N=N, basis="dirichlet")
+    assert sigma_err(out["S"], ref["Sigma"]) <= tl["sig"]
+    assert np.max(np.abs(out["R"].astype(np.float64) - ref["R"])) <= tl["R"]
+
+
+def test_single_asset_and_tiny_problem():
+    ev = synth.from_lists([[0.0, 1.0, 3.5]], [[4.6, 4.61, 4.59]])
+    for prec in ("fp64", "bf16x3"):
+        tl = TOL[prec]
+        out = run(dict(tol=tl["tol"], kernel="gauss", basis="dirichlet", prec=prec), ev, 3)
+        ref = oracle.estimate(ev.offsets, ev.t, ev.logp, N=3)
+        assert np.all(rel_l2_rows(out["F"], ref["F"]) <= tl["coef"])
+        assert out["R"][0, 0] == 1.0
+
+
+def test_window_rescaling():
+    ev = synth.random_events(31, D=4, n_range=(20, 80), T=900.0)
+    win = (-50.0, 1000.0)
+    for prec in ("fp64", "bf16x3"):
+        tl = TOL[prec]
+        out = run(dict(tol=tl["tol"], kernel="es", basis="dirichlet", prec=prec), ev, 40, window=win)
+        ref = oracle.estimate(ev.offsets, ev.t, ev.logp, N=40, window=win)
+        assert np.all(rel_l2_rows(out["F"], ref["F"]) <= tl["coef"])
+
+
+def test_nyquist_cutoff_matches_oracle():
+    import paper_2003_02842_gb300 as mm
+    for ev in (synth.c1_sync(0), synth.c2_async(0), synth.random_events(41, D=5, n_range=(2, 50))):
+        t0, t1 = oracle.bounds(ev.offsets, ev.t)
+        want = oracle.nyquist(ev.offsets, ev.t, t0, t1)
+        plan = mm.mm_plan_create(D=ev.D, N_max=max(want, 1), max_events=ev.n_events, tol=1e-6)
+        off, t, p = to_dev(ev)
+        assert mm.mm_nyquist(plan, off, t) == want
+        F, Nu = mm.mm_coeffs(plan, off, t, p, N=0)
+        assert Nu == want
+        mm.mm_destroy(plan)
+
+
+@pytest.mark.parametrize("bad,code", [("unsorted", 2), ("duplicate", 3), ("nan", 10)])
+def test_bad_event_data_reports_status(bad, code):
+    import paper_2003_02842_gb300 as mm
+    ev = synth.random_events(51, D=3, n_range=(30, 60), T=100.0)
+    t = ev.t.copy()
+    lp = ev.logp.copy()
+    a = int(ev.offsets[1]) + 5
+    if bad == "unsorted":
+        t[a], t[a + 1] = t[a + 1], t[a]
+    elif bad == "duplicate":
+        t[a + 1] = t[a]
+    else:
+        lp[a] = np.nan
+    ev2 = synth.Events(ev.offsets.copy(), t, lp)
+    plan = mm.mm_plan_create(D=3, N_max=20, max_events=ev.n_events, tol=1e-6)
+    off, tt, p = to_dev(ev2)
+    mm.mm_estimate(plan, off, tt, p, 20)
+    assert mm.mm_plan_sync(plan) == code
+    assert mm.mm_plan_sync(plan) == 0  # the status word was cleared
+    mm.mm_destroy(plan)
+
+
+def test_bad_offsets_rejected_without_touching_events():
+    import torch
+    import paper_2003_02842_gb300 as mm
+    plan = mm.mm_plan_create(D=2, N_max=10, max_events=10, tol=1e-6)
+    off = torch.tensor([0, 7, 5], dtype=torch.int64, device="cuda")  # decreasing
+    t = torch.arange(10, dtype=torch.float64, device="cuda")
+    p = torch.zeros(10, dtype=torch.float64, device="cuda")
+    mm.mm_estimate(plan, off, t, p, 10)
+    assert mm.mm_plan_sync(plan) == 1
+    off2 = torch.tensor([0, 5, 50], dtype=torch.int64, device="cuda")  # beyond max_events
+    mm.mm_estimate(plan, off2, t, p, 10)
+    assert mm.mm_plan_sync(plan) == 1
+    mm.mm_destroy(plan)
+
+
+def test_host_buffer_entry_point_matches_device_path():
+    import torch
+    import paper_2003_02842_gb300 as mm
+    ev = synth.c2_async(2)
+    N = ev.meta["N"]
+    plan = mm.mm_plan_create(D=2, N_max=N, max_events=ev.n_events, tol=1e-6, kernel="es", prec="bf16x3")
+    off, t, p = to_dev(ev)
+    F, S, R, _ = mm.mm_estimate(plan, off, t, p, N)
+    hoff = torch.from_numpy(ev.offsets).pin_memory()
+    ht = torch.from_numpy(ev.t).pin_memory()
+    hp = torch.from_numpy(ev.logp).pin_memory()
+    hR = torch.empty((2, 2), dtype=torch.float32).pin_memory()
+    hS = torch.empty((2, 2), dtype=torch.float32).pin_memory()
+    hF = torch.empty((2, N + 1), dtype=torch.complex64).pin_memory()
+    st, Nu = mm.mm_estimate_host(plan, hoff, ht, hp, N, coeffs=hF, sigma=hS, R=hR)
+    assert st == 0 and Nu == N
+    # shared-memory atomics make the FP32 spreading order vary between runs,
+    # so the two paths agree to rounding, not bit for bit
+    assert torch.allclose(hF, F.cpu(), rtol=0, atol=1e-6 * float(F.abs().max()))
+    assert torch.allclose(hS, S.cpu(), rtol=1e-5, atol=0)
+    assert torch.allclose(hR, R.cpu(), rtol=0, atol=1e-6)
+    mm.mm_destroy(plan)
+
+
+def test_profiling_counts_launches():
+    import paper_2003_02842_gb300 as mm
+    ev = synth.c1_sync(0)
+    plan = mm.mm_plan_create(D=2, N_max=500, max_events=ev.n_events, tol=1e-6)
+    off, t, p = to_dev(ev)
+    mm.mm_estimate(plan, off, t, p, 500)
+    mm.mm_profile_enable(plan, True)
+    mm.mm_profile_read(plan, reset=True)
+    for _ in range(3):
+        mm.mm_estimate(plan, off, t, p, 500)
+    prof = mm.mm_profile_read(plan)
+    for stage in ("prep", "spread", "fft_cols", "fft_rows", "gram", "reduce"):
+        assert prof[stage][1] == 3 and prof[stage][0] > 0
+    assert prof["setup"][1] == 0  # tables are cached per cutoff
+    mm.mm_destroy(plan)
