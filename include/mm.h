@@ -155,6 +155,26 @@ mm_status mm_cov(mm_plan plan, const void* d_coeffs, int32_t N, void* d_sigma, v
 mm_status mm_corr(mm_plan plan, const void* d_coeffs, int32_t N, void* d_sigma_or_null,
                   void* d_R, void* stream);
 
+/* mm_corr without a plan and without allocating anything, for callers that
+ * cannot call cudaMalloc (their device memory is owned by a pool or an
+ * allocator they must not bypass, or an allocation may not fail at that
+ * point). The paper has no counterpart; this is a deployment convenience.
+ * It runs the same contraction as mm_corr on coefficients laid out as
+ * mm_coeffs writes them (D x (N+1), complex128 for MM_PREC_FP64, complex64
+ * otherwise) and writes Sigma (optional) and R as mm_corr does. Its scratch
+ * (weights, split-K partial tiles, a status word) is one file-scope device
+ * array of about 2 MB that every GPU loading the library keeps until the
+ * process exits. Limits: 1 <= D <= 128 and 0 <= N <= 65535; larger sizes
+ * return MM_ERR_UNSUPPORTED. The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture. All calls share the array, and the array keeps the
+ * last call's contents, so calls that overlap on the GPU race: order them
+ * (one stream, or explicit synchronisation). The call synchronises the
+ * stream and returns the contraction's device status (MM_OK,
+ * MM_ERR_ZERO_VARIANCE or MM_ERR_TIMEOUT). */
+mm_status mm_corr_noalloc(int32_t D, int32_t N, mm_basis basis, mm_precision prec, const void* d_coeffs,
+                          void* d_sigma_or_null, void* d_R, void* stream);
+
 /* Whole Algorithm 3 on device buffers: mm_coeffs followed by mm_corr.
  * d_coeffs receives the coefficients (it is also the contraction's input). */
 mm_status mm_estimate(mm_plan plan, const int64_t* d_offsets, const double* d_t,

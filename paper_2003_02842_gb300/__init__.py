@@ -22,7 +22,7 @@ from ._lib import BASES, KERNELS, PRECISIONS, STAGES, STATUS_NAMES
 __all__ = [
     "MMError", "Plan", "mm_plan_create", "mm_destroy", "mm_coeffs", "mm_cov", "mm_corr", "mm_estimate",
     "mm_estimate_host", "mm_nyquist", "mm_plan_sync", "mm_plan_get_info", "mm_profile_enable",
-    "mm_profile_read", "mm_status_string", "mm_version", "KERNELS", "BASES", "PRECISIONS", "STAGES",
+    "mm_profile_read", "mm_status_string", "mm_version", "mm_corr_noalloc", "KERNELS", "BASES", "PRECISIONS", "STAGES",
 ]
 
 
@@ -186,6 +186,30 @@ def mm_corr(plan, coeffs, N, sigma=True, R=None, stream=None):
     _check(_lib.load().mm_corr(plan.handle, _dptr(coeffs, _coef_dtype(plan), "coeffs"), int(N), ps,
                                _dptr(R, dt, "R"), _stream(stream)), "mm_corr")
     return S, R
+
+
+def mm_corr_noalloc(coeffs, N, basis="dirichlet", prec="bf16x3", sigma=True, R=None, stream=None):
+    """Sigma and R from coefficients without a plan and without any device
+    allocation inside the library (its scratch is a fixed device array; see
+    include/mm.h). Synchronises the stream; returns (status, Sigma or None, R).
+    Only D <= 128 and N <= 65535 are accepted."""
+    torch = _torch()
+    D = int(coeffs.shape[0])
+    fp64 = prec == "fp64"
+    cdt = torch.complex128 if fp64 else torch.complex64
+    dt = torch.float64 if fp64 else torch.float32
+    if R is None:
+        R = torch.empty((D, D), dtype=dt, device=coeffs.device)
+    if sigma is True:
+        S = torch.empty((D, D), dtype=dt, device=coeffs.device)
+    elif sigma is None or sigma is False:
+        S = None
+    else:
+        S = sigma
+    ps = _dptr(S, dt, "sigma") if S is not None else ctypes.c_void_p(0)
+    st = _lib.load().mm_corr_noalloc(D, int(N), BASES[basis], PRECISIONS[prec], _dptr(coeffs, cdt, "coeffs"),
+                                     ps, _dptr(R, dt, "R"), _stream(stream))
+    return int(st), S, R
 
 
 def mm_estimate(plan, offsets, t, logp, N, window=None, coeffs=None, sigma=True, R=None, stream=None):
