@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--kernel", default="es", choices=["gauss", "kb", "es"])
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison path")
+    ap.add_argument("--spread-algo", default="default", choices=["default", "scatter", "gather"])
     return ap.parse_args()
 
 
@@ -222,7 +223,7 @@ def main():
     D = ev.D
     tol = 1e-12 if args.prec == "fp64" else 1e-6
     plan = mm.mm_plan_create(D=D, N_max=N, max_events=ev.n_events, tol=tol, kernel=args.kernel,
-                             basis="dirichlet", prec=args.prec)
+                             basis="dirichlet", prec=args.prec, spread_algo=args.spread_algo)
     coef = torch.empty((D, N + 1), dtype=torch.complex128 if args.prec == "fp64" else torch.complex64, device=dev)
     rdt = torch.float64 if args.prec == "fp64" else torch.float32
     S = torch.empty((D, D), dtype=rdt, device=dev)
@@ -244,8 +245,6 @@ def main():
             step()
         torch.cuda.synchronize()
         launches0 = mm.mm_plan_get_info(plan)["launches"]
-        mm.mm_profile_read(plan, reset=True)
-        mm.mm_profile_enable(plan, True)
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         if world > 1:
@@ -259,10 +258,20 @@ def main():
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-        mm.mm_profile_enable(plan, False)
         launches = mm.mm_plan_get_info(plan)["launches"] - launches0
-        stages = mm.mm_profile_read(plan, reset=True)
         total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+
+        # the same steps again with the library's per-stage CUDA events on the
+        # launching stream (kept out of the headline loop above)
+        mm.mm_profile_read(plan, reset=True)
+        mm.mm_profile_enable(plan, True)
+        prof_steps = max(3, min(args.steps, 100))
+        for k in range(prof_steps):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+        mm.mm_profile_enable(plan, False)
+        stages = mm.mm_profile_read(plan, reset=True)
 
         # end to end through the host-buffer entry point (copies inside the timed region)
         hoff = torch.from_numpy(ev.offsets).pin_memory()
@@ -336,13 +345,14 @@ def main():
         Mr = info["Mr"]
         cbytes = 8 if args.prec != "fp64" else 16
         gbytes = 4 if args.prec != "fp64" else 8
+        rbytes = 4 + 2 * gbytes  # per-event record of the prep kernel (cell, offset, return)
         alg = {
-            "spread": 16.0 * ev.n_events + gbytes * Mr * D,
-            "fft_cols": 2.0 * gbytes * Mr * D,
+            "prep": (16.0 + rbytes) * ev.n_events,           # t, logp in; records out
+            "spread": rbytes * ev.n_events + gbytes * Mr * D,  # records in; grid out
+            "fft_cols": 2.0 * gbytes * Mr * D,                 # grid in and out
             "fft_rows": gbytes * Mr * D + cbytes * (N + 1) * D,
-            "gram": cbytes * (N + 1) * D,
+            "gram": cbytes * (N + 1) * D,                      # coefficients in
             "reduce": 0.0,
-            "prep": 16.0 * D,
         }
         avg_ms = stage_ms[dom]
         achieved = alg.get(dom, 0.0) / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
@@ -365,6 +375,7 @@ def main():
                        "events": ev.n_events, "kernel": args.kernel, "tol": tol, "basis": "dirichlet",
                        "contraction": args.prec, "l2": "flushed between steps (256 MB write)",
                        "grid_Mr": Mr, "fft": [info["fft_P"], info["fft_Q"]], "gram_splits": info["gram_splits"],
+                       "spread_algo": args.spread_algo,
                        "replicas": world},
             "matrices_per_s": world * args.steps / (total_ms * 1e-3),
             "stage_ms": stage_ms,

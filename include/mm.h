@@ -99,7 +99,9 @@ typedef struct {
   mm_basis basis;
   mm_precision prec;
   int32_t spread_tile;  /* grid cells per spreading block; 0 = library default */
-  int32_t reserved[6];  /* must be zero */
+  int32_t spread_algo;  /* 0 library default, 1 scatter into a shared-memory tile,
+                           2 gather per grid cell (both compute Eq. (12) exactly) */
+  int32_t reserved[5];  /* must be zero */
 } mm_plan_desc;
 
 typedef struct mm_plan_s* mm_plan;

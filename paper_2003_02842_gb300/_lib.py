@@ -21,6 +21,7 @@ STATUS_NAMES = {
 KERNELS = {"gauss": 0, "kb": 1, "es": 2}
 BASES = {"dirichlet": 0, "fejer": 1}
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "3xtf32": 2}
+SPREAD_ALGOS = {"default": 0, "scatter": 1, "gather": 2}
 STAGES = ["prep", "spread", "fft_cols", "fft_rows", "gram", "reduce", "setup"]
 
 
@@ -34,7 +35,8 @@ class PlanDesc(ctypes.Structure):
         ("basis", ctypes.c_int),
         ("prec", ctypes.c_int),
         ("spread_tile", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 6),
+        ("spread_algo", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
     ]
 
 

@@ -100,17 +100,23 @@ struct mm_plan_s {
   int64_t n_max = 0;
   // workspace
   void* grid = nullptr;
+  int* rec_b0 = nullptr;          // per-event records of the prep kernel
+  void* rec_d = nullptr;
+  void* rec_v = nullptr;
   void* W = nullptr;
   void* U = nullptr;
   void* decon = nullptr;
   double* glx = nullptr;
   double* glw = nullptr;
-  double* bounds = nullptr;
+  Rescale* bounds = nullptr;
   int* status = nullptr;  // [0] sticky flags, [1] gate, [2] Nyquist N
   unsigned long long* gapbits = nullptr;
   void* wsq = nullptr;
-  void* partial = nullptr;
+  void* partial = nullptr;        // FP64 path: per-split partial tiles
   size_t partial_bytes = 0;
+  float* acc[2] = {nullptr, nullptr};  // mixed path: FP32 accumulators, used alternately
+  int acc_sel = 0;
+  bool acc_dirty = true;          // clear both before the next contraction
   int64_t* s_off = nullptr;
   double* s_t = nullptr;
   double* s_p = nullptr;
@@ -131,6 +137,7 @@ struct mm_plan_s {
   // instrumentation
   bool prof = false;
   std::vector<Prof> pending;
+  std::vector<cudaEvent_t> pool;  // reusable timing events
   double ms[MM_NUM_STAGES] = {};
   int64_t nl[MM_NUM_STAGES] = {};
   int64_t launches = 0;
@@ -156,8 +163,8 @@ mm_status dalloc(mm_plan p, void** ptr, size_t bytes) {
 }
 
 void free_all(mm_plan p) {
-  void* ptrs[] = {p->grid, p->W, p->U, p->decon, p->glx, p->glw, p->bounds, p->status, p->gapbits, p->wsq,
-                  p->partial, p->s_off, p->s_t, p->s_p, p->s_coef, p->s_sigma, p->s_R};
+  void* ptrs[] = {p->grid, p->rec_b0, p->rec_d, p->rec_v, p->W, p->U, p->decon, p->glx, p->glw, p->bounds, p->status, p->gapbits, p->wsq,
+                  p->partial, p->acc[0], p->acc[1], p->s_off, p->s_t, p->s_p, p->s_coef, p->s_sigma, p->s_R};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& e : p->pending) {
@@ -165,6 +172,19 @@ void free_all(mm_plan p) {
     cudaEventDestroy(e.b);
   }
   p->pending.clear();
+  for (cudaEvent_t e : p->pool) cudaEventDestroy(e);
+  p->pool.clear();
+}
+
+cudaEvent_t take_event(mm_plan p) {
+  if (!p->pool.empty()) {
+    cudaEvent_t e = p->pool.back();
+    p->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
 }
 
 // Stage timing helpers: when profiling is on, every launch is bracketed by a
@@ -177,8 +197,8 @@ struct StageScope {
   int count;
   StageScope(mm_plan p_, int stage_, cudaStream_t s_, int count_ = 1) : p(p_), stage(stage_), s(s_), count(count_) {
     if (p->prof) {
-      cudaEventCreate(&a);
-      cudaEventCreate(&b);
+      a = take_event(p);
+      b = take_event(p);
       cudaEventRecord(a, s);
     }
   }
@@ -210,14 +230,17 @@ mm_status configure(mm_plan p, int N) {
   f.nrad_p = radix_plan(P, f.rad_p);
   f.nrad_q = radix_plan(Q, f.rad_q);
   const size_t cs = p->cs;
-  const size_t budget = 96 * 1024;
-  f.cols = 16;
-  while (f.cols > 1 && ((size_t)2 * P * f.cols + P) * cs > budget) f.cols >>= 1;
-  while (f.cols > 1 && f.cols / 2 >= Q) f.cols >>= 1;
+  const size_t budget = 48 * 1024;  // about four blocks per SM
+  int lg = 4;                       // pass 1: up to 16 adjacent columns (128 B per row in FP32)
+  while (lg > 0 && ((size_t)2 * P * ((size_t)1 << lg) + P) * cs > budget) --lg;
+  while (lg > 0 && (1 << (lg - 1)) >= Q) --lg;
+  f.lg_cols = lg;
   f.H = P / 2 + 1;
-  f.rowblk = 16;
-  while (f.rowblk > 1 && ((size_t)4 * f.rowblk * Q + Q) * cs > budget) f.rowblk >>= 1;
+  f.rowblk = 8;
+  auto rows_lg = [](int rb) { int l = 0; while ((1 << l) < 2 * rb) ++l; return l; };
+  while (f.rowblk > 1 && ((size_t)2 * ((size_t)1 << rows_lg(f.rowblk)) * Q + Q) * cs > budget) f.rowblk >>= 1;
   while (f.rowblk > 1 && f.rowblk / 2 >= f.H) f.rowblk >>= 1;
+  f.lg_rowcols = rows_lg(f.rowblk);
   f.N = N;
 
   SpreadParams s{};
@@ -228,12 +251,13 @@ mm_status configure(mm_plan p, int N) {
   s.khi = p->khi;
   s.kernel = p->desc.kernel;
   s.max_events = p->desc.max_events;
-  int tile = p->desc.spread_tile > 0 ? p->desc.spread_tile : (p->fp64 ? 2048 : 4096);
-  if (Mr <= (int64_t)tile + (s.khi - s.klo) + 1) {
+  const int tmax = spread_max_tile(p->fp64);
+  int tile = p->desc.spread_tile > 0 ? std::min(p->desc.spread_tile, tmax) : tmax;
+  if (Mr <= (int64_t)tile) {
     tile = (int)Mr;
     s.single_tile = 1;
   }
-  if ((size_t)tile * p->rs > 200 * 1024) return MM_ERR_UNSUPPORTED;
+  s.algo = p->desc.spread_algo == 2 ? 1 : 0;
   s.tile = tile;
   s.ntiles = (int)((Mr + tile - 1) / tile);
   s.es_beta = 2.3 * 2.0 * p->msp;
@@ -272,18 +296,25 @@ GramParams gram_params(mm_plan p, int N) {
   g.D = p->desc.D;
   g.N = N;
   g.ld = N + 1;
+  g.Dp = (g.D + 3) / 4 * 4;
   g.tile = p->fp64 ? 64 : 128;
   g.ntiles = (g.D + g.tile - 1) / g.tile;
   g.npairs = g.ntiles * (g.ntiles + 1) / 2;
   g.chunk = p->fp64 ? 16 : (p->desc.prec == MM_PREC_MIXED_BF16X3 ? 32 : 16);
   g.nchunks = (N + 1 + g.chunk - 1) / g.chunk;
-  // split K so that all SMs get work while the partial tiles stay a small
-  // fraction of the operand bytes
-  const double a_bytes = (double)g.D * 2.0 * (N + 1) * (p->fp64 ? 8.0 : 4.0);
-  const double tile_bytes = (double)g.tile * g.tile * (p->fp64 ? 8.0 : 4.0);
-  int s_traffic = (int)std::max(1.0, ceil(a_bytes / (4.0 * g.npairs * tile_bytes)));
-  int s_ctas = std::max(1, kMaxGramCtas / g.npairs);
-  int S = std::max(1, std::min({g.nchunks, s_ctas, s_traffic}));
+  int S;
+  if (p->fp64) {
+    // split K so that all SMs get work while the partial tiles stay a small
+    // fraction of the operand bytes
+    const double a_bytes = (double)g.D * 2.0 * (N + 1) * 8.0;
+    const double tile_bytes = (double)g.tile * g.tile * 8.0;
+    const int s_traffic = (int)std::max(1.0, ceil(a_bytes / (4.0 * g.npairs * tile_bytes)));
+    S = std::max(1, std::min({g.nchunks, std::max(1, kMaxGramCtas / g.npairs), s_traffic}));
+  } else {
+    // about two CTAs per SM, at least two K-chunks each (the partial sums meet
+    // in L2 through vector reductions, so more splits cost little traffic)
+    S = std::max(1, std::min((g.nchunks + 1) / 2, std::max(1, kMaxGramCtas / g.npairs)));
+  }
   g.chunks_per_split = (g.nchunks + S - 1) / S;
   g.splits = (g.nchunks + g.chunks_per_split - 1) / g.chunks_per_split;
   return g;
@@ -316,9 +347,20 @@ mm_status coeffs_impl(mm_plan p, const int64_t* off, const double* t, const doub
   r = ensure_tables(p, N, st);
   if (r != MM_OK) return r;
   {
+    StageScope sc(p, MM_STAGE_PREP, st);
+    if (p->fp64)
+      MM_CUDA(launch_prep_f64(off, t, logp, p->bounds, D, p->Mr, p->desc.max_events, p->rec_b0, p->rec_d,
+                              p->rec_v, p->status, st));
+    else
+      MM_CUDA(launch_prep_f32(off, t, logp, p->bounds, D, p->Mr, p->desc.max_events, p->rec_b0, p->rec_d,
+                              p->rec_v, p->status, st));
+  }
+  {
     StageScope sc(p, MM_STAGE_SPREAD, st);
-    if (p->fp64) MM_CUDA(launch_spread_f64(off, t, logp, p->bounds, p->sp, (double*)p->grid, p->status, st));
-    else MM_CUDA(launch_spread_f32(off, t, logp, p->bounds, p->sp, (float*)p->grid, p->status, st));
+    if (p->fp64)
+      MM_CUDA(launch_spread_f64(off, p->rec_b0, p->rec_d, p->rec_v, p->sp, (double*)p->grid, p->status, st));
+    else
+      MM_CUDA(launch_spread_f32(off, p->rec_b0, p->rec_d, p->rec_v, p->sp, (float*)p->grid, p->status, st));
   }
   {
     StageScope sc(p, MM_STAGE_FFT_COLS, st);
@@ -341,23 +383,41 @@ mm_status corr_impl(mm_plan p, const void* coeffs, int N, void* sigma, void* R, 
   if (p->desc.basis == MM_BASIS_FEJER && N < 1) return MM_ERR_CUTOFF;
   p->last = st;
   GramParams g = gram_params(p, N);
-  if ((size_t)g.npairs * g.splits * g.tile * g.tile * p->rs > p->partial_bytes) return MM_ERR_UNSUPPORTED;
+  if (p->fp64 && (size_t)g.npairs * g.splits * g.tile * g.tile * p->rs > p->partial_bytes) return MM_ERR_UNSUPPORTED;
   if (p->w_N != N || p->w_basis != (int)p->desc.basis) {
     StageScope sc(p, MM_STAGE_SETUP, st);
     MM_CUDA(launch_gram_weights(p->desc.basis, N, p->fp64, p->wsq, st));
     p->w_N = N;
     p->w_basis = p->desc.basis;
   }
-  {
-    StageScope sc(p, MM_STAGE_GRAM, st);
-    if (p->fp64) MM_CUDA(launch_gram_f64(coeffs, g, (const double*)p->wsq, (double*)p->partial, st));
-    else
-      MM_CUDA(launch_gram_tc(p->desc.prec == MM_PREC_MIXED_BF16X3 ? 0 : 1, coeffs, g, (const float*)p->wsq,
-                             (float*)p->partial, p->status, st));
-  }
-  {
+  if (p->fp64) {
+    {
+      StageScope sc(p, MM_STAGE_GRAM, st);
+      MM_CUDA(launch_gram_f64(coeffs, g, (const double*)p->wsq, (double*)p->partial, st));
+    }
     StageScope sc(p, MM_STAGE_REDUCE, st);
-    MM_CUDA(launch_reduce_corr(p->fp64, p->partial, g, sigma, R, p->status, st));
+    MM_CUDA(launch_reduce_corr(true, p->partial, g, sigma, R, p->status, st));
+  } else {
+    const size_t acc_bytes = (size_t)g.D * g.Dp * sizeof(float);
+    if (p->acc_dirty) {
+      MM_CUDA(cudaMemsetAsync(p->acc[0], 0, acc_bytes, st));
+      MM_CUDA(cudaMemsetAsync(p->acc[1], 0, acc_bytes, st));
+      p->acc_dirty = false;
+    }
+    float* cur = p->acc[p->acc_sel];
+    float* next = p->acc[p->acc_sel ^ 1];
+    p->acc_dirty = true;  // until both launches below are queued
+    {
+      StageScope sc(p, MM_STAGE_GRAM, st);
+      MM_CUDA(launch_gram_tc(p->desc.prec == MM_PREC_MIXED_BF16X3 ? 0 : 1, coeffs, g, (const float*)p->wsq, cur,
+                             p->status, st));
+    }
+    {
+      StageScope sc(p, MM_STAGE_REDUCE, st);
+      MM_CUDA(launch_corr_acc(cur, g, (float*)sigma, (float*)R, next, p->status, st));
+    }
+    p->acc_sel ^= 1;
+    p->acc_dirty = false;
   }
   p->gram = g;
   return MM_OK;
@@ -398,7 +458,8 @@ mm_status mm_plan_create(const mm_plan_desc* desc, mm_plan* out) {
   if (d.basis < MM_BASIS_DIRICHLET || d.basis > MM_BASIS_FEJER) return MM_ERR_INVALID_ARG;
   if (d.prec < MM_PREC_FP64 || d.prec > MM_PREC_MIXED_3XTF32) return MM_ERR_INVALID_ARG;
   if (d.spread_tile < 0 || d.spread_tile > 50000) return MM_ERR_INVALID_ARG;
-  for (int i = 0; i < 6; ++i)
+  if (d.spread_algo < 0 || d.spread_algo > 2) return MM_ERR_INVALID_ARG;
+  for (int i = 0; i < 5; ++i)
     if (d.reserved[i] != 0) return MM_ERR_INVALID_ARG;
   const int msp = msp_rule(d.kernel, d.tol);
   if (msp < 1 || msp > 30) return MM_ERR_UNSUPPORTED;
@@ -429,20 +490,28 @@ mm_status mm_plan_create(const mm_plan_desc* desc, mm_plan* out) {
     if (r == MM_OK) r = dalloc(p, ptr, bytes);
   };
   A(&p->grid, D * 2 * (size_t)n * p->rs);
+  A((void**)&p->rec_b0, (size_t)std::max<int64_t>(d.max_events, 1) * sizeof(int));
+  A(&p->rec_d, (size_t)std::max<int64_t>(d.max_events, 1) * p->rs);
+  A(&p->rec_v, (size_t)std::max<int64_t>(d.max_events, 1) * p->rs);
   A(&p->W, (size_t)n * p->cs);
   A(&p->U, Np1 * p->cs);
   A(&p->decon, Np1 * p->rs);
   A((void**)&p->glx, kGlNodes * sizeof(double));
   A((void**)&p->glw, kGlNodes * sizeof(double));
-  A((void**)&p->bounds, 2 * sizeof(double));
+  A((void**)&p->bounds, sizeof(Rescale));
   A((void**)&p->status, 4 * sizeof(int));
   A((void**)&p->gapbits, sizeof(unsigned long long));
   A(&p->wsq, Np1 * p->rs);
   {
     GramParams g = gram_params(p, d.N_max);
     size_t ctas = std::max<size_t>((size_t)kMaxGramCtas, (size_t)g.npairs);
-    p->partial_bytes = ctas * g.tile * g.tile * p->rs;
-    A(&p->partial, p->partial_bytes);
+    if (p->fp64) {
+      p->partial_bytes = ctas * g.tile * g.tile * p->rs;
+      A(&p->partial, p->partial_bytes);
+    } else {
+      A((void**)&p->acc[0], D * (size_t)g.Dp * sizeof(float));
+      A((void**)&p->acc[1], D * (size_t)g.Dp * sizeof(float));
+    }
   }
   if (d.max_events > 0) {
     A((void**)&p->s_off, (D + 1) * sizeof(int64_t));
@@ -617,8 +686,8 @@ mm_status mm_profile_read(mm_plan p, double* ms, int64_t* launches, int32_t rese
     float v = 0.f;
     if (cudaEventSynchronize(e.b) == cudaSuccess && cudaEventElapsedTime(&v, e.a, e.b) == cudaSuccess)
       p->ms[e.stage] += v;
-    cudaEventDestroy(e.a);
-    cudaEventDestroy(e.b);
+    p->pool.push_back(e.a);
+    p->pool.push_back(e.b);
   }
   p->pending.clear();
   for (int i = 0; i < MM_NUM_STAGES; ++i) {

@@ -57,6 +57,7 @@ struct SpreadParams {
   int klo, khi;      // stencil offsets k in [klo, khi] around b0
   int kernel;        // mm_kernel
   int single_tile;   // 1: one block covers the whole (small) grid
+  int algo;          // 0: scatter into a shared-memory tile, 1: gather per cell
   // kernel constants
   double es_beta;    // ES: beta
   double es_inv_w;   // ES: 1 / M_sp  (support half-width in cells)
@@ -66,13 +67,27 @@ struct SpreadParams {
   int64_t max_events;
 };
 
+// Rescaling of Algorithm 4 in exact fixed point, written by k_bounds for the
+// current call: t_fix = trunc(t * 2^F) (int64, |t| < 2^(62-F)); the cell
+// coordinate u = (t - t0) M_r / span is u_fix = ((t_fix - t0_fix) * S) >> sh
+// = floor(u * 2^40), so b0 = u_fix >> 40 and d = (u_fix mod 2^40) / 2^40.
+struct Rescale {
+  double t0, t1;             // window used (data minimum / maximum or caller's)
+  long long t0_fix;          // t0 in units of 2^-F
+  unsigned long long S;      // 64-bit multiplier, in [2^63, 2^64)
+  int F;                     // fractional bits of the time fixed point
+  int sh;                    // right shift of the 128-bit product, 0..127
+};
+constexpr int kUFrac = 40;   // fractional bits of u_fix
+
 struct FftParams {
   int64_t n;         // complex length = Mr / 2
   int P, Q;          // n = P * Q
   int nrad_p, nrad_q;
   int rad_p[kMaxRadices], rad_q[kMaxRadices];
-  int cols;          // pass 1: columns (j2 values) per block
+  int lg_cols;       // pass 1: log2 of the columns (j2 values) per block
   int rowblk;        // pass 2: lower rows per block
+  int lg_rowcols;    // pass 2: log2 of the rows held per block (>= 2 rowblk, padded)
   int H;             // pass 2: number of lower rows = P/2 + 1
   int N;             // cutoff
 };
@@ -88,20 +103,25 @@ struct GramParams {
   int chunk;         // complex modes per K-chunk
   int nchunks;       // ceil((N+1) / chunk)
   int chunks_per_split;
+  int Dp;            // row stride of the FP32 accumulator (D rounded up to 4)
 };
 
 // ---------------------------------------------------------------- launchers
 // Each returns cudaGetLastError() of its launch.
 cudaError_t launch_bounds(const int64_t* off, const double* t, int D, int64_t max_events,
-                          double w0, double w1, double* bounds, int* status, cudaStream_t s);
-cudaError_t launch_min_gap(const int64_t* off, const double* t, int D, const double* bounds,
+                          double w0, double w1, Rescale* rs, int* status, cudaStream_t s);
+cudaError_t launch_min_gap(const int64_t* off, const double* t, int D, const Rescale* rs,
                            unsigned long long* gapbits, int* nyq, int* status, cudaStream_t s);
-cudaError_t launch_spread_f32(const int64_t* off, const double* t, const double* logp,
-                              const double* bounds, const SpreadParams& p, float* grid,
-                              int* status, cudaStream_t s);
-cudaError_t launch_spread_f64(const int64_t* off, const double* t, const double* logp,
-                              const double* bounds, const SpreadParams& p, double* grid,
-                              int* status, cudaStream_t s);
+cudaError_t launch_prep_f32(const int64_t* off, const double* t, const double* logp, const Rescale* rs, int D,
+                            int64_t Mr, int64_t max_events, int* rb0, void* rd, void* rv, int* status,
+                            cudaStream_t s);
+cudaError_t launch_prep_f64(const int64_t* off, const double* t, const double* logp, const Rescale* rs, int D,
+                            int64_t Mr, int64_t max_events, int* rb0, void* rd, void* rv, int* status,
+                            cudaStream_t s);
+cudaError_t launch_spread_f32(const int64_t* off, const int* rb0, const void* rd, const void* rv,
+                              const SpreadParams& p, float* grid, const int* status, cudaStream_t s);
+cudaError_t launch_spread_f64(const int64_t* off, const int* rb0, const void* rd, const void* rv,
+                              const SpreadParams& p, double* grid, const int* status, cudaStream_t s);
 
 cudaError_t launch_gl_nodes(int nq, double* x, double* w, cudaStream_t s);
 cudaError_t launch_setup_tables(int kernel, int msp, int64_t Mr, int N, int64_t n,
@@ -114,6 +134,7 @@ cudaError_t launch_fft_rows_f32(const float* grid, const FftParams& f, int D, co
                                 const void* U, const void* decon, void* coeffs, const int* status, cudaStream_t s);
 cudaError_t launch_fft_rows_f64(const double* grid, const FftParams& f, int D, const void* W,
                                 const void* U, const void* decon, void* coeffs, const int* status, cudaStream_t s);
+int spread_max_tile(bool fp64);
 size_t fft_cols_smem(const FftParams& f, bool fp64);
 size_t fft_rows_smem(const FftParams& f, bool fp64);
 
@@ -121,7 +142,9 @@ cudaError_t launch_gram_weights(int basis, int N, bool fp64, void* wsq, cudaStre
 cudaError_t launch_gram_f64(const void* coeffs, const GramParams& g, const double* wsq,
                             double* partial, cudaStream_t s);
 cudaError_t launch_gram_tc(int mode, const void* coeffs, const GramParams& g, const float* wsq,
-                           float* partial, int* status, cudaStream_t s);
+                           float* acc, int* status, cudaStream_t s);
+cudaError_t launch_corr_acc(const float* acc, const GramParams& g, float* sigma, float* R, float* zero_next,
+                            int* status, cudaStream_t s);
 cudaError_t launch_reduce_corr(bool fp64, const void* partial, const GramParams& g,
                                void* sigma, void* R, int* status, cudaStream_t s);
 size_t gram_tc_smem(int mode, bool two_tiles);

@@ -110,46 +110,60 @@ struct Dft<T, 8> {
   }
 };
 
+// j / d for j, d < 2^16 with m = ceil(2^32 / d): floor(j m / 2^32) is exact,
+// because the rounding of m adds less than 2^-16 < 1/d to j / d.
+__device__ __forceinline__ unsigned magic_of(unsigned d) { return d <= 1u ? 0u : 0xFFFFFFFFu / d + 1u; }
+__device__ __forceinline__ int fast_div(int j, int d, unsigned m) { return d == 1 ? j : (int)__umulhi((unsigned)j, m); }
+
+// Shared-memory slot of element j of column c when B = 2^lgB columns are
+// interleaved: row j holds the B columns, permuted by an XOR with the row
+// index so that reading one column down many rows (the transposed loads of
+// pass 2) touches distinct banks while a row stays one contiguous segment.
+__device__ __forceinline__ int swz(int j, int c, int lgB) { return (j << lgB) | (c ^ (j & ((1 << lgB) - 1))); }
+
 // One autosorting Stockham stage of radix R over L-point sequences stored as
-// B interleaved columns (element j of column c at j * B + c). Ns is the
-// product of the radices already applied; tw[j] = e^{-2 pi i j / L}.
+// B = 2^lgB interleaved columns (element j of column c at swz(j, c)).
+// Ns is the product of the radices already applied; tw[j] = e^{-2 pi i j / L}.
 template <typename T, int R>
 __device__ __forceinline__ void stockham_stage(const Cplx<T>* __restrict__ in, Cplx<T>* __restrict__ out,
-                                               const Cplx<T>* __restrict__ tw, int L, int B, int Ns) {
+                                               const Cplx<T>* __restrict__ tw, int L, int lgB, int Ns) {
   const int nb = L / R;
   const int twstep = L / (Ns * R);
-  for (int idx = threadIdx.x; idx < nb * B; idx += blockDim.x) {
-    const int j = idx / B, c = idx - j * B;
-    const int k = j % Ns;
+  const unsigned mNs = magic_of((unsigned)Ns);
+  const int B = 1 << lgB;
+  for (int idx = threadIdx.x; idx < (nb << lgB); idx += blockDim.x) {
+    const int j = idx >> lgB, c = idx & (B - 1);
+    const int q = fast_div(j, Ns, mNs);
+    const int k = j - q * Ns;
     Cplx<T> v[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) v[q] = in[(j + q * nb) * B + c];
+    for (int r = 0; r < R; ++r) v[r] = in[swz(j + r * nb, c, lgB)];
     if (Ns > 1) {
 #pragma unroll
-      for (int q = 1; q < R; ++q) v[q] = cmul(v[q], tw[q * k * twstep]);
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * k * twstep]);
     }
     Dft<T, R>::run(v);
-    const int base = (j / Ns) * Ns * R + k;
+    const int base = q * Ns * R + k;
 #pragma unroll
-    for (int q = 0; q < R; ++q) out[(base + q * Ns) * B + c] = v[q];
+    for (int r = 0; r < R; ++r) out[swz(base + r * Ns, c, lgB)] = v[r];
   }
 }
 
-// Full L-point FFT of B columns; returns the buffer holding the result.
+// Full L-point FFT of 2^lgB columns; returns the buffer holding the result.
 template <typename T>
-__device__ Cplx<T>* stockham_fft(Cplx<T>* a, Cplx<T>* b, const Cplx<T>* tw, int L, int B,
-                                 const int* rad, int nrad) {
+__device__ Cplx<T>* stockham_fft(Cplx<T>* a, Cplx<T>* b, const Cplx<T>* tw, int L, int lgB, const int* rad,
+                                 int nrad) {
   int Ns = 1;
   Cplx<T>* in = a;
   Cplx<T>* out = b;
   for (int s = 0; s < nrad; ++s) {
     const int r = rad[s];
     switch (r) {
-      case 2: stockham_stage<T, 2>(in, out, tw, L, B, Ns); break;
-      case 3: stockham_stage<T, 3>(in, out, tw, L, B, Ns); break;
-      case 4: stockham_stage<T, 4>(in, out, tw, L, B, Ns); break;
-      case 5: stockham_stage<T, 5>(in, out, tw, L, B, Ns); break;
-      default: stockham_stage<T, 8>(in, out, tw, L, B, Ns); break;
+      case 2: stockham_stage<T, 2>(in, out, tw, L, lgB, Ns); break;
+      case 3: stockham_stage<T, 3>(in, out, tw, L, lgB, Ns); break;
+      case 4: stockham_stage<T, 4>(in, out, tw, L, lgB, Ns); break;
+      case 5: stockham_stage<T, 5>(in, out, tw, L, lgB, Ns); break;
+      default: stockham_stage<T, 8>(in, out, tw, L, lgB, Ns); break;
     }
     __syncthreads();
     Cplx<T>* x = in;
@@ -166,25 +180,23 @@ __global__ void __launch_bounds__(256) k_fft_cols(Cplx<T>* __restrict__ z, FftPa
                                                   const Cplx<T>* __restrict__ W, const int* __restrict__ gate) {
   if (*gate) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int P = f.P, Q = f.Q, B = f.cols;
+  const int P = f.P, Q = f.Q, lgB = f.lg_cols, B = 1 << lgB;
   Cplx<T>* buf0 = reinterpret_cast<Cplx<T>*>(smem_raw);
   Cplx<T>* buf1 = buf0 + P * B;
   Cplx<T>* tw = buf1 + P * B;
   const int j20 = blockIdx.x * B;
   Cplx<T>* za = z + (int64_t)blockIdx.y * f.n;
-  for (int j = threadIdx.x; j < P; j += blockDim.x) tw[j] = W[(int64_t)j * Q];
-  for (int idx = threadIdx.x; idx < P * B; idx += blockDim.x) {
-    const int j1 = idx / B, c = idx - j1 * B, j2 = j20 + c;
-    buf0[idx] = (j2 < Q) ? za[(int64_t)Q * j1 + j2] : Cplx<T>{(T)0, (T)0};
+  for (int j = threadIdx.x; j < P; j += blockDim.x) tw[j] = W[j * Q];
+  for (int idx = threadIdx.x; idx < (P << lgB); idx += blockDim.x) {
+    const int j1 = idx >> lgB, c = idx & (B - 1), j2 = j20 + c;
+    buf0[swz(j1, c, lgB)] = (j2 < Q) ? za[Q * j1 + j2] : Cplx<T>{(T)0, (T)0};
   }
   __syncthreads();
-  const Cplx<T>* X = stockham_fft(buf0, buf1, tw, P, B, f.rad_p, f.nrad_p);
-  for (int idx = threadIdx.x; idx < P * B; idx += blockDim.x) {
-    const int k1 = idx / B, c = idx - k1 * B, j2 = j20 + c;
-    if (j2 < Q) {
-      const int64_t e = ((int64_t)j2 * k1) % f.n;
-      za[(int64_t)Q * k1 + j2] = cmul(X[idx], W[e]);
-    }
+  const Cplx<T>* X = stockham_fft(buf0, buf1, tw, P, lgB, f.rad_p, f.nrad_p);
+  for (int idx = threadIdx.x; idx < (P << lgB); idx += blockDim.x) {
+    const int k1 = idx >> lgB, c = idx & (B - 1), j2 = j20 + c;
+    // j2 k1 <= (Q-1)(P-1) < n: the twiddle index needs no reduction
+    if (j2 < Q) za[Q * k1 + j2] = cmul(X[swz(k1, c, lgB)], W[j2 * k1]);
   }
 }
 
@@ -196,9 +208,10 @@ __global__ void __launch_bounds__(256) k_fft_rows(const Cplx<T>* __restrict__ z,
                                                   const int* __restrict__ gate) {
   if (*gate) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_row[2 * 64], s_partner[2 * 64];
+  __shared__ int s_row[64], s_partner[64];
   __shared__ int s_nrows;
   const int P = f.P, Q = f.Q;
+  const int lgB = f.lg_rowcols, B = 1 << lgB;  // padded number of rows held
   const int r0 = blockIdx.x * f.rowblk;
   const int r1 = min(r0 + f.rowblk, f.H);
   if (threadIdx.x == 0) {
@@ -213,45 +226,47 @@ __global__ void __launch_bounds__(256) k_fft_rows(const Cplx<T>* __restrict__ z,
       if (m >= f.H) s_row[nr++] = m;
     }
     for (int i = 0; i < nr; ++i) {
-      const int k1 = s_row[i];
-      const int m = (P - k1) % P;
+      const int m = (P - s_row[i]) % P;
       int pi = i;
       for (int q = 0; q < nr; ++q)
         if (s_row[q] == m) pi = q;
       s_partner[i] = pi;
     }
+    for (int i = nr; i < B; ++i) s_row[i] = -1;
     s_nrows = nr;
   }
   __syncthreads();
   const int nr = s_nrows;
   Cplx<T>* buf0 = reinterpret_cast<Cplx<T>*>(smem_raw);
-  Cplx<T>* buf1 = buf0 + nr * Q;
-  Cplx<T>* tw = buf0 + 2 * 2 * f.rowblk * Q;
+  Cplx<T>* buf1 = buf0 + B * Q;
+  Cplx<T>* tw = buf1 + B * Q;
   const Cplx<T>* za = z + (int64_t)blockIdx.y * f.n;
-  for (int j = threadIdx.x; j < Q; j += blockDim.x) tw[j] = W[(int64_t)j * P];
-  for (int idx = threadIdx.x; idx < nr * Q; idx += blockDim.x) {
-    const int ri = idx / Q, j2 = idx - ri * Q;
-    buf0[j2 * nr + ri] = za[(int64_t)Q * s_row[ri] + j2];
+  for (int j = threadIdx.x; j < Q; j += blockDim.x) tw[j] = W[j * P];
+  const unsigned mQ = magic_of((unsigned)Q);
+  for (int idx = threadIdx.x; idx < B * Q; idx += blockDim.x) {
+    const int ri = fast_div(idx, Q, mQ), j2 = idx - ri * Q;
+    const int row = s_row[ri];
+    buf0[swz(j2, ri, lgB)] = row >= 0 ? za[Q * row + j2] : Cplx<T>{(T)0, (T)0};
   }
   __syncthreads();
-  const Cplx<T>* X = stockham_fft(buf0, buf1, tw, Q, nr, f.rad_q, f.nrad_q);
+  const Cplx<T>* X = stockham_fft(buf0, buf1, tw, Q, lgB, f.rad_q, f.nrad_q);
   Cplx<T>* oa = out + (int64_t)blockIdx.y * (f.N + 1);
-  for (int idx = threadIdx.x; idx < nr * Q; idx += blockDim.x) {
-    const int k2 = idx / nr, ri = idx - k2 * nr;
+  for (int idx = threadIdx.x; idx < (Q << lgB); idx += blockDim.x) {
+    const int k2 = idx >> lgB, ri = idx & (B - 1);
+    if (ri >= nr) continue;
     const int k1 = s_row[ri];
-    const int64_t k = (int64_t)k1 + (int64_t)P * k2;
+    const int k = k1 + P * k2;
     if (k > f.N) continue;
-    int pk2, pri = s_partner[ri];
-    if (k1 == 0) pk2 = (k2 == 0) ? 0 : Q - k2;
-    else pk2 = Q - 1 - k2;
-    const Cplx<T> Zk = X[k2 * nr + ri];
-    const Cplx<T> Zc = cconj(X[pk2 * nr + pri]);
+    const int pri = s_partner[ri];
+    const int pk2 = (k1 == 0) ? ((k2 == 0) ? 0 : Q - k2) : Q - 1 - k2;
+    const Cplx<T> Zk = X[swz(k2, ri, lgB)];
+    const Cplx<T> Zc = cconj(X[swz(pk2, pri, lgB)]);
     const Cplx<T> E = {(T)0.5 * (Zk.x + Zc.x), (T)0.5 * (Zk.y + Zc.y)};
     const Cplx<T> dlt = csub(Zk, Zc);
     const Cplx<T> O = {(T)0.5 * dlt.y, (T)-0.5 * dlt.x};  // (Zk - Zc) / (2i)
     const Cplx<T> G = cadd(E, cmul(U[k], O));
-    const T s = decon[k];
-    oa[k] = Cplx<T>{G.x * s, G.y * s};
+    const T sc = decon[k];
+    oa[k] = Cplx<T>{G.x * sc, G.y * sc};
   }
 }
 
@@ -350,11 +365,11 @@ cudaError_t launch_setup_tables(int kernel, int msp, int64_t Mr, int N, int64_t 
 // ------------------------------------------------------------ launchers
 size_t fft_cols_smem(const FftParams& f, bool fp64) {
   const size_t cs = fp64 ? 16 : 8;
-  return cs * ((size_t)2 * f.P * f.cols + f.P);
+  return cs * ((size_t)2 * f.P * ((size_t)1 << f.lg_cols) + f.P);
 }
 size_t fft_rows_smem(const FftParams& f, bool fp64) {
   const size_t cs = fp64 ? 16 : 8;
-  return cs * ((size_t)2 * 2 * f.rowblk * f.Q + f.Q);
+  return cs * ((size_t)2 * ((size_t)1 << f.lg_rowcols) * f.Q + f.Q);
 }
 
 template <typename T>
@@ -364,7 +379,8 @@ static cudaError_t launch_cols_t(T* grid, const FftParams& f, int D, const void*
   auto fn = k_fft_cols<T>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grd((f.Q + f.cols - 1) / f.cols, D);
+  const int B = 1 << f.lg_cols;
+  dim3 grd((f.Q + B - 1) / B, D);
   fn<<<grd, 256, smem, s>>>(reinterpret_cast<Cplx<T>*>(grid), f, (const Cplx<T>*)W, status + 1);
   return cudaGetLastError();
 }

@@ -17,8 +17,10 @@
 // tracked by mbarriers so the next tile is staged while the tensor core runs.
 // Every wait is bounded: after ~1 s it records MM_ERR_TIMEOUT and the CTA
 // drains and frees its TMEM.
-// FP64: a CUDA-core tiled kernel. Both write per-split partial tiles that
-// k_reduce_corr sums in FP64 before the FP64 correlation normalisation.
+// The split-K partial products meet in an FP32 accumulator through vector
+// reductions in L2 (red.global.add.v4.f32); k_corr_acc then normalises in
+// FP64. FP64 path: a CUDA-core tiled kernel writing per-split partial tiles
+// that k_reduce_corr sums in FP64 before the same normalisation.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -211,47 +213,63 @@ __device__ __forceinline__ uint32_t sw128_off(int r, int cb) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((cb >> 4) ^ (r & 7)) << 4) | (cb & 15)));
 }
 
-// Stage one K-chunk of `rows` coefficient rows (starting at row0) into the
-// hi / lo tiles. MODE 0: 32 complex modes per chunk as bf16 pairs;
-// MODE 1: 16 complex modes per chunk as tf32 pairs.
+// One K-chunk of the operand rows a thread owns, held in registers between
+// the global load and the conversion into shared memory, so that the loads
+// of chunk c+1 are in flight while chunk c is converted and multiplied.
+// MODE 0: 32 complex modes per chunk, one per lane, 32 rows per warp.
+// MODE 1: 16 complex modes per chunk, two rows per warp step, 32 rows per warp.
 template <int MODE>
-__device__ __forceinline__ void stage_tile(const float2* __restrict__ F, const GramParams& g,
-                                           const float* __restrict__ wsq, int row0, int kbase,
-                                           uint8_t* hi, uint8_t* lo) {
+struct Chunk {
+  static constexpr int R = MODE == 0 ? 32 : 16;
+  float2 v[R];
+  float sc;
+};
+
+template <int MODE>
+__device__ __forceinline__ void load_chunk(const float2* __restrict__ F, const GramParams& g,
+                                           const float* __restrict__ wsq, int row0, int kbase, Chunk<MODE>& c) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int l = MODE == 0 ? lane : (lane & 15);
+  const int half = MODE == 0 ? 0 : (lane >> 4);
+  const int k = kbase + l;
+  const bool kin = k <= g.N;
+  c.sc = kin ? __ldg(wsq + k) : 0.0f;
+#pragma unroll
+  for (int rr = 0; rr < Chunk<MODE>::R; ++rr) {
+    const int r = warp * 32 + (MODE == 0 ? rr : rr * 2 + half);
+    const int row = row0 + r;
+    c.v[rr] = (kin && row < g.D) ? __ldg(F + (int64_t)row * g.ld + k) : make_float2(0.f, 0.f);
+  }
+}
+
+// Scale by s_k = 2 pi sqrt(W_k), split into hi + lo (bf16 or tf32) and write
+// both into the 128B-swizzled K-major tiles.
+template <int MODE>
+__device__ __forceinline__ void store_chunk(const Chunk<MODE>& c, uint8_t* hi, uint8_t* lo) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (MODE == 0) {
-    const int k = kbase + lane;
-    const bool kin = k <= g.N;
-    const float sc = kin ? wsq[k] : 0.0f;
-#pragma unroll 4
+#pragma unroll
     for (int rr = 0; rr < 32; ++rr) {
       const int r = warp * 32 + rr;
-      const int row = row0 + r;
-      float2 v = {0.f, 0.f};
-      if (kin && row < g.D) v = F[(int64_t)row * g.ld + k];
-      const float xr = v.x * sc, xi = v.y * sc;
+      const float xr = c.v[rr].x * c.sc, xi = c.v[rr].y * c.sc;
       const __nv_bfloat16 hr = __float2bfloat16_rn(xr), hi_ = __float2bfloat16_rn(xi);
       const __nv_bfloat16 lr = __float2bfloat16_rn(xr - __bfloat162float(hr));
       const __nv_bfloat16 li = __float2bfloat16_rn(xi - __bfloat162float(hi_));
       __nv_bfloat162 H, L;
-      H.x = hr; H.y = hi_;
-      L.x = lr; L.y = li;
+      H.x = hr;
+      H.y = hi_;
+      L.x = lr;
+      L.y = li;
       const uint32_t off = sw128_off(r, lane * 4);
       *reinterpret_cast<__nv_bfloat162*>(hi + off) = H;
       *reinterpret_cast<__nv_bfloat162*>(lo + off) = L;
     }
   } else {
     const int half = lane >> 4, l = lane & 15;
-    const int k = kbase + l;
-    const bool kin = k <= g.N;
-    const float sc = kin ? wsq[k] : 0.0f;
-#pragma unroll 4
+#pragma unroll
     for (int rr = 0; rr < 16; ++rr) {
       const int r = warp * 32 + rr * 2 + half;
-      const int row = row0 + r;
-      float2 v = {0.f, 0.f};
-      if (kin && row < g.D) v = F[(int64_t)row * g.ld + k];
-      const float xr = v.x * sc, xi = v.y * sc;
+      const float xr = c.v[rr].x * c.sc, xi = c.v[rr].y * c.sc;
       const uint32_t hr = f32_to_tf32(xr), hi_ = f32_to_tf32(xi);
       const uint32_t lr = f32_to_tf32(xr - __uint_as_float(hr));
       const uint32_t li = f32_to_tf32(xi - __uint_as_float(hi_));
@@ -262,10 +280,19 @@ __device__ __forceinline__ void stage_tile(const float2* __restrict__ F, const G
   }
 }
 
+__device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
+  asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c),
+               "f"(d)
+               : "memory");
+}
+
+// One CTA per (output tile pair I <= J, K-split): the split's partial
+// 128 x 128 product accumulates in TMEM and is then added into the FP32
+// accumulator acc (row stride Dp) with vector reductions in L2.
 template <int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restrict__ F, GramParams g,
-                                                           const float* __restrict__ wsq,
-                                                           float* __restrict__ partial, int* status) {
+                                                           const float* __restrict__ wsq, float* __restrict__ acc,
+                                                           int* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ uint32_t s_tmem;
@@ -284,8 +311,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restr
   uint8_t* base = smem_raw + (((base_s + 1023u) & ~1023u) - base_s);
   const int tiles_per_stage = two ? 4 : 2;
 
+  const int rowsI = min(kTile, g.D - I * kTile);
   const int rowsJ = min(kTile, g.D - J * kTile);
-  const int Nmma = two ? ((rowsJ + 15) / 16) * 16 : ((min(kTile, g.D - I * kTile) + 15) / 16) * 16;
+  const int Nmma = ((rowsJ + 15) / 16) * 16;
   const uint32_t fmt = (MODE == 0) ? 1u : 2u;  // bf16 / tf32 operands
   const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(Nmma >> 3) << 17) |
                          ((uint32_t)(kTile >> 4) << 24);
@@ -308,17 +336,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restr
   const uint32_t tmem = s_tmem;
 
   const int chunk = g.chunk;
+  Chunk<MODE> ca, cb;
+  if (nit > 0) {
+    load_chunk<MODE>(F, g, wsq, I * kTile, c0 * chunk, ca);
+    if (two) load_chunk<MODE>(F, g, wsq, J * kTile, c0 * chunk, cb);
+  }
   bool ok = true;
   for (int it = 0; it < nit; ++it) {
     const int st = it & 1;
     if (it >= 2) {
       if (!mbar_wait(&bars[st], (uint32_t)(((it >> 1) - 1) & 1), kWaitLimitNs)) ok = false;
     }
-    if (__syncthreads_or(!ok)) { ok = false; break; }
+    if (__syncthreads_or(!ok)) {
+      ok = false;
+      break;
+    }
     uint8_t* stg = base + (size_t)st * tiles_per_stage * kTileBytes;
-    const int kbase = (c0 + it) * chunk;
-    stage_tile<MODE>(F, g, wsq, I * kTile, kbase, stg, stg + kTileBytes);
-    if (two) stage_tile<MODE>(F, g, wsq, J * kTile, kbase, stg + 2 * kTileBytes, stg + 3 * kTileBytes);
+    store_chunk<MODE>(ca, stg, stg + kTileBytes);
+    if (two) store_chunk<MODE>(cb, stg + 2 * kTileBytes, stg + 3 * kTileBytes);
+    if (it + 1 < nit) {
+      const int kb = (c0 + it + 1) * chunk;
+      load_chunk<MODE>(F, g, wsq, I * kTile, kb, ca);
+      if (two) load_chunk<MODE>(F, g, wsq, J * kTile, kb, cb);
+    }
     fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -345,22 +385,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restr
   tc_fence_after();
   __syncthreads();
 
-  float* out = partial + ((int64_t)blockIdx.y * g.splits + s) * kTile * kTile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = warp * 32 + lane;
   if (!s_fail && nit > 0) {
+    float* out = acc + (int64_t)(I * kTile + r) * g.Dp + J * kTile;
     for (int c = 0; c < Nmma; c += 16) {
       uint32_t v[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-      float4* o4 = reinterpret_cast<float4*>(out + (int64_t)r * kTile + c);
+      if (r < rowsI) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        o4[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
-                            __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+        for (int q = 0; q < 4; ++q)
+          if (c + 4 * q < rowsJ)
+            red_add_v4(out + c + 4 * q, __uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                       __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+      }
     }
-  } else {
-    for (int c = 0; c < Nmma; ++c) out[(int64_t)r * kTile + c] = (nit > 0) ? __int_as_float(0x7fc00000) : 0.f;
-    if (threadIdx.x == 0 && nit > 0) atomicOr(status, ST_TIMEOUT);
+  } else if (threadIdx.x == 0 && nit > 0) {
+    atomicOr(status, ST_TIMEOUT);
   }
   tc_fence_before();
   __syncthreads();
@@ -369,7 +410,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restr
   }
 }
 
-cudaError_t launch_gram_tc(int mode, const void* coeffs, const GramParams& g, const float* wsq, float* partial,
+cudaError_t launch_gram_tc(int mode, const void* coeffs, const GramParams& g, const float* wsq, float* acc,
                            int* status, cudaStream_t s) {
   const bool two = g.ntiles > 1;
   const size_t smem = gram_tc_smem(mode, two);
@@ -378,12 +419,60 @@ cudaError_t launch_gram_tc(int mode, const void* coeffs, const GramParams& g, co
   if (mode == 0) {
     e = cudaFuncSetAttribute(k_gram_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_gram_tc<0><<<grd, kTcThreads, smem, s>>>((const float2*)coeffs, g, wsq, partial, status);
+    k_gram_tc<0><<<grd, kTcThreads, smem, s>>>((const float2*)coeffs, g, wsq, acc, status);
   } else {
     e = cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_gram_tc<1><<<grd, kTcThreads, smem, s>>>((const float2*)coeffs, g, wsq, partial, status);
+    k_gram_tc<1><<<grd, kTcThreads, smem, s>>>((const float2*)coeffs, g, wsq, acc, status);
   }
+  return cudaGetLastError();
+}
+
+// Sigma and R from the FP32 accumulator of k_gram_tc (upper tile pairs only:
+// entry (i, j) lives at acc[i][j] when tile(i) <= tile(j), else acc[j][i]).
+// The normalisation R_ij = Sigma_ij / (sqrt(Sigma_ii) sqrt(Sigma_jj)) is in
+// FP64; R_ii = 1 exactly; zero variance gives NaN and a status. The block
+// also clears the matching entries of zero_next, the accumulator the next
+// call will use.
+__global__ void __launch_bounds__(256) k_corr_acc(const float* __restrict__ acc, GramParams g, float* __restrict__ sigma,
+                                                  float* __restrict__ R, float* __restrict__ zero_next, int* status) {
+  __shared__ double s_inv_i[16], s_inv_j[16];
+  const int li = threadIdx.x >> 4, lj = threadIdx.x & 15;
+  const int j = blockIdx.x * 16 + lj;
+  const int i = blockIdx.y * 16 + li;
+  // 1 / sqrt(Sigma_dd) in FP64 once per row and column of the block
+  if (threadIdx.x < 32) {
+    const int q = threadIdx.x & 15;
+    const int d = (threadIdx.x < 16 ? blockIdx.y : blockIdx.x) * 16 + q;
+    double inv = 0.0;
+    if (d < g.D) {
+      const double v = acc[(int64_t)d * g.Dp + d];
+      inv = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
+    }
+    if (threadIdx.x < 16) s_inv_i[q] = inv;
+    else s_inv_j[q] = inv;
+  }
+  __syncthreads();
+  if (i >= g.D || j >= g.Dp) return;
+  if (zero_next) zero_next[(int64_t)i * g.Dp + j] = 0.0f;
+  if (j >= g.D) return;
+  const bool up = (i / kTile) <= (j / kTile);
+  const double v = up ? (double)acc[(int64_t)i * g.Dp + j] : (double)acc[(int64_t)j * g.Dp + i];
+  const double a = s_inv_i[li], b = s_inv_j[lj];
+  double r;
+  if (a > 0.0 && b > 0.0) r = (i == j) ? 1.0 : v * a * b;
+  else {
+    r = __longlong_as_double(0x7ff8000000000000ll);
+    if (i == j) atomicOr(status, ST_ZERO_VAR);
+  }
+  if (sigma) sigma[(int64_t)i * g.D + j] = (float)v;
+  if (R) R[(int64_t)i * g.D + j] = (float)r;
+}
+
+cudaError_t launch_corr_acc(const float* acc, const GramParams& g, float* sigma, float* R, float* zero_next,
+                            int* status, cudaStream_t s) {
+  dim3 grd((g.Dp + 15) / 16, (g.D + 15) / 16);
+  k_corr_acc<<<grd, 256, 0, s>>>(acc, g, sigma, R, zero_next, status);
   return cudaGetLastError();
 }
 

@@ -8,7 +8,9 @@
 // as mm_corr without a plan, taking its scratch (the basis weights, the
 // split-K partial tiles and a status word) from one file-scope device array.
 //
-// Limits: 1 <= D <= 128, 0 <= N <= 65535, at most 16 K-splits. The array is
+// Limits: 1 <= D <= 128, 0 <= N <= 65535, at most 16 K-splits (the FP64
+// path's partial tiles; the mixed path uses the same bytes as its 128 x 128
+// float accumulator). The array is
 // about 2 MB and every GPU that loads the library holds it until the process
 // exits. Every call shares it, so calls that overlap on the GPU (different
 // streams, or host threads without ordering) race and give wrong results.
@@ -25,7 +27,7 @@ constexpr int kNaMaxN = 65535;
 constexpr int kNaMaxSplits = 16;
 // partial tiles: FP32 path 1 pair of 128 x 128 floats; FP64 path up to
 // 3 pairs of 64 x 64 doubles (D <= 128 gives at most 2 x 2 tiles of 64)
-constexpr size_t kNaPartialBytes = (size_t)kNaMaxSplits * 3 * 64 * 64 * 8;
+constexpr size_t kNaPartialBytes = (size_t)kNaMaxSplits * 3 * 64 * 64 * 8;  // >= the FP32 accumulator
 constexpr size_t kNaWeightBytes = (size_t)(kNaMaxN + 1) * 8;
 constexpr size_t kNaStatusBytes = 256;
 constexpr size_t kNaBytes = kNaPartialBytes + kNaWeightBytes + kNaStatusBytes;
@@ -83,6 +85,7 @@ extern "C" mm_status mm_corr_noalloc(int32_t D, int32_t N, mm_basis basis, mm_pr
   g.D = D;
   g.N = N;
   g.ld = N + 1;
+  g.Dp = (D + 3) / 4 * 4;
   g.tile = fp64 ? 64 : 128;
   g.ntiles = (D + g.tile - 1) / g.tile;
   g.npairs = g.ntiles * (g.ntiles + 1) / 2;
@@ -93,16 +96,22 @@ extern "C" mm_status mm_corr_noalloc(int32_t D, int32_t N, mm_basis basis, mm_pr
   g.splits = (g.nchunks + g.chunks_per_split - 1) / g.chunks_per_split;
 
   cudaStream_t st = (cudaStream_t)stream;
-  // the status word must start at zero; the partial tiles and weights are
-  // fully rewritten by the kernels below
+  // the status word and the mixed path's accumulator must start at zero; the
+  // FP64 partial tiles and the weights are fully rewritten by the kernels
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return MM_ERR_CUDA;
   if (launch_gram_weights(basis, N, fp64, wsq, st) != cudaSuccess) return MM_ERR_CUDA;
-  cudaError_t e;
-  if (fp64) e = launch_gram_f64(d_coeffs, g, (const double*)wsq, (double*)partial, st);
-  else e = launch_gram_tc(prec == MM_PREC_MIXED_BF16X3 ? 0 : 1, d_coeffs, g, (const float*)wsq, (float*)partial,
-                          status, st);
-  if (e != cudaSuccess) return MM_ERR_CUDA;
-  if (launch_reduce_corr(fp64, partial, g, d_sigma_or_null, d_R, status, st) != cudaSuccess) return MM_ERR_CUDA;
+  if (fp64) {
+    if (launch_gram_f64(d_coeffs, g, (const double*)wsq, (double*)partial, st) != cudaSuccess) return MM_ERR_CUDA;
+    if (launch_reduce_corr(true, partial, g, d_sigma_or_null, d_R, status, st) != cudaSuccess) return MM_ERR_CUDA;
+  } else {
+    float* acc = (float*)partial;
+    if (cudaMemsetAsync(acc, 0, (size_t)D * g.Dp * sizeof(float), st) != cudaSuccess) return MM_ERR_CUDA;
+    if (launch_gram_tc(prec == MM_PREC_MIXED_BF16X3 ? 0 : 1, d_coeffs, g, (const float*)wsq, acc, status, st) !=
+        cudaSuccess)
+      return MM_ERR_CUDA;
+    if (launch_corr_acc(acc, g, (float*)d_sigma_or_null, (float*)d_R, nullptr, status, st) != cudaSuccess)
+      return MM_ERR_CUDA;
+  }
   int f = 0;
   if (cudaMemcpyAsync(&f, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return MM_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return MM_ERR_CUDA;

@@ -83,27 +83,30 @@ def test_covariance_and_correlation(prec, basis, wl):
     assert np.array_equal(S, S.T) and np.array_equal(R, R.T, equal_nan=True)
 
 
-@pytest.mark.parametrize("tile", [64, 257, 1000])
+@pytest.mark.parametrize("algo", ["scatter", "gather"])
+@pytest.mark.parametrize("tile", [64, 257, 1000, 0])
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
-def test_many_tiles_and_periodic_halos(tile, prec):
+def test_many_tiles_and_periodic_halos(tile, prec, algo):
     # small spreading tiles: most events feed two tiles and the first and last
-    # tiles exchange halos across the periodic wrap
+    # tiles exchange halos across the periodic wrap; both spreading variants
     ev = synth.c2_async(1)
     N = 333
     tl = TOL[prec]
     for kernel in ("gauss", "kb", "es"):
-        out = run(dict(tol=tl["tol"], kernel=kernel, basis="dirichlet", prec=prec, spread_tile=tile), ev, N)
+        out = run(dict(tol=tl["tol"], kernel=kernel, basis="dirichlet", prec=prec, spread_tile=tile,
+                       spread_algo=algo), ev, N)
         assert out["status"] == 0
         ref = oracle.coeffs_F(ev.offsets, ev.t, ev.logp, N)
         assert np.all(rel_l2_rows(out["F"], ref) <= tl["coef"])
 
 
+@pytest.mark.parametrize("algo", ["scatter", "gather"])
 @pytest.mark.parametrize("N", [1, 2, 7, 15, 64, 121, 1000])
-def test_cutoffs_small_and_non_smooth(N):
+def test_cutoffs_small_and_non_smooth(N, algo):
     ev = synth.random_events(11, D=3, n_range=(50, 400), T=2000.0)
     for prec in ("fp64", "bf16x3"):
         tl = TOL[prec]
-        out = run(dict(tol=tl["tol"], kernel="es", basis="fejer", prec=prec), ev, N)
+        out = run(dict(tol=tl["tol"], kernel="es", basis="fejer", prec=prec, spread_algo=algo), ev, N)
         ref = oracle.estimate(ev.offsets, ev.t, ev.logp, N=N, basis="fejer")
         assert np.all(rel_l2_rows(out["F"], ref["F"]) <= tl["coef"])
         assert np.max(np.abs(out["R"].astype(np.float64) - ref["R"])) <= tl["R"]
@@ -139,6 +142,21 @@ def test_window_rescaling():
         out = run(dict(tol=tl["tol"], kernel="es", basis="dirichlet", prec=prec), ev, 40, window=win)
         ref = oracle.estimate(ev.offsets, ev.t, ev.logp, N=40, window=win)
         assert np.all(rel_l2_rows(out["F"], ref["F"]) <= tl["coef"])
+
+
+@pytest.mark.parametrize("origin", [0.0, 1.7e9, -3.0e5])
+def test_large_time_origin_keeps_phase(origin):
+    # epoch-scale timestamps: the fixed-point phase reduction keeps the cell
+    # offsets exact where a float32 rescaling would lose every digit
+    ev = synth.c2_async(3)
+    ev2 = synth.Events(ev.offsets.copy(), ev.t + origin, ev.logp.copy())
+    N = ev.meta["N"]
+    ref = oracle.coeffs_F(ev2.offsets, ev2.t, ev2.logp, N)
+    for prec in ("fp64", "bf16x3"):
+        tl = TOL[prec]
+        out = run(dict(tol=tl["tol"], kernel="es", basis="dirichlet", prec=prec), ev2, N)
+        assert out["status"] == 0
+        assert np.all(rel_l2_rows(out["F"], ref) <= tl["coef"])
 
 
 def test_nyquist_cutoff_matches_oracle():
@@ -226,7 +244,8 @@ def test_profiling_counts_launches():
     for _ in range(3):
         mm.mm_estimate(plan, off, t, p, 500)
     prof = mm.mm_profile_read(plan)
-    for stage in ("prep", "spread", "fft_cols", "fft_rows", "gram", "reduce"):
+    assert prof["prep"][1] == 6 and prof["prep"][0] > 0  # bounds + per-event prep
+    for stage in ("spread", "fft_cols", "fft_rows", "gram", "reduce"):
         assert prof[stage][1] == 3 and prof[stage][0] > 0
     assert prof["setup"][1] == 0  # tables are cached per cutoff
     mm.mm_destroy(plan)
