@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--kernel", default="es", choices=["gauss", "kb", "es"])
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison path")
-    ap.add_argument("--spread-algo", default="default", choices=["default", "scatter", "gather"])
+    ap.add_argument("--spread-algo", default="default", choices=["default", "scatter", "gather", "fused"])
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default configuration")
     return ap.parse_args()
 
 
@@ -233,7 +234,11 @@ def main():
     def step():
         mm.mm_estimate(plan, off, tt, lp, N, coeffs=coef, sigma=S, R=R)
 
+    # autotune stages (a)-(c) on this workload (kept in the plan), then the
     # first call builds the per-cutoff tables; then check the status
+    tuned = None
+    if not args.no_autotune and args.spread_algo == "default":
+        tuned = mm.mm_autotune(plan, off, tt, lp, N, coeffs=coef, reps=3)
     step()
     st = mm.mm_plan_sync(plan)
     if st != 0:
@@ -375,7 +380,9 @@ def main():
                        "events": ev.n_events, "kernel": args.kernel, "tol": tol, "basis": "dirichlet",
                        "contraction": args.prec, "l2": "flushed between steps (256 MB write)",
                        "grid_Mr": Mr, "fft": [info["fft_P"], info["fft_Q"]], "gram_splits": info["gram_splits"],
-                       "spread_algo": args.spread_algo,
+                       "spread_algo": {1: "scatter", 2: "gather", 3: "fused"}.get(info["spread_algo"]),
+                       "spread_tile": info["spread_tile"], "fft_blocking": [info["fft_lg_cols"], info["fft_rowblk"]],
+                       "autotuned": tuned is not None,
                        "replicas": world},
             "matrices_per_s": world * args.steps / (total_ms * 1e-3),
             "stage_ms": stage_ms,

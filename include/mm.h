@@ -99,8 +99,11 @@ typedef struct {
   mm_basis basis;
   mm_precision prec;
   int32_t spread_tile;  /* grid cells per spreading block; 0 = library default */
-  int32_t spread_algo;  /* 0 library default, 1 scatter into a shared-memory tile,
-                           2 gather per grid cell (both compute Eq. (12) exactly) */
+  int32_t spread_algo;  /* 0 library default (= 1 unless mm_autotune chose otherwise);
+                           1 separate prep / scatter-into-tile / FFT kernels; 2 as 1
+                           with a gather per grid cell; 3 stages (a)-(c) fused in one
+                           CTA per asset when the grid fits in shared memory, else 1.
+                           All compute Eq. (12) exactly. */
   int32_t reserved[5];  /* must be zero */
 } mm_plan_desc;
 
@@ -109,7 +112,7 @@ typedef struct mm_plan_s* mm_plan;
 /* Per-stage timing and launch counters (device time from CUDA events on the
  * launching stream, summed since the last reset). */
 enum { MM_STAGE_PREP = 0, MM_STAGE_SPREAD = 1, MM_STAGE_FFT_COLS = 2, MM_STAGE_FFT_ROWS = 3,
-       MM_STAGE_GRAM = 4, MM_STAGE_REDUCE = 5, MM_STAGE_SETUP = 6, MM_NUM_STAGES = 7 };
+       MM_STAGE_GRAM = 4, MM_STAGE_REDUCE = 5, MM_STAGE_SETUP = 6, MM_STAGE_FUSED = 7, MM_NUM_STAGES = 8 };
 
 typedef struct {
   int32_t msp;           /* spreading half-width M_sp */
@@ -119,7 +122,11 @@ typedef struct {
   int64_t workspace_bytes;
   int64_t launches;      /* kernels launched by this plan since creation */
   int32_t gram_splits;   /* split-K factor of the last contraction */
-  int32_t reserved[5];
+  int32_t spread_algo;   /* stage (a)-(c) variant in use: 1 scatter, 2 gather, 3 fused */
+  int32_t spread_tile;   /* grid cells per spreading block in use */
+  int32_t fft_lg_cols;   /* FFT pass 1: log2 of the columns per block */
+  int32_t fft_rowblk;    /* FFT pass 2: lower rows per block */
+  float tuned_ms;        /* mm_coeffs time of the configuration mm_autotune chose (0 if untuned) */
 } mm_plan_info;
 
 /* Create a plan: validates desc, allocates the workspace on the current
@@ -192,6 +199,15 @@ mm_status mm_estimate_host(mm_plan plan, const int64_t* h_offsets, const double*
                            const double* h_logp, int32_t N, double t0, double t1,
                            void* h_coeffs_or_null, void* h_sigma_or_null, void* h_R,
                            int32_t* N_used, void* stream);
+
+/* Autotuner: times mm_coeffs on the caller's data for every candidate
+ * configuration of stages (a)-(c) (spreading variant scatter / gather /
+ * fused, cells per spreading block, FFT column and row blocking), reps calls
+ * each after one warm-up call, and keeps the fastest in the plan for all
+ * later calls (mm_plan_get_info reports it). d_coeffs is scratch of
+ * D * (N+1) complex elements. Synchronises the stream; allocates nothing. */
+mm_status mm_autotune(mm_plan plan, const int64_t* d_offsets, const double* d_t, const double* d_logp,
+                      int32_t N, double t0, double t1, void* d_coeffs, int32_t reps, void* stream);
 
 /* Nyquist cutoff of Algorithm 2 on device data (synchronises the stream).
  * Window as for mm_coeffs. Returns MM_ERR_CUTOFF when no asset has two

@@ -22,7 +22,7 @@ from ._lib import BASES, KERNELS, PRECISIONS, STAGES, STATUS_NAMES
 __all__ = [
     "MMError", "Plan", "mm_plan_create", "mm_destroy", "mm_coeffs", "mm_cov", "mm_corr", "mm_estimate",
     "mm_estimate_host", "mm_nyquist", "mm_plan_sync", "mm_plan_get_info", "mm_profile_enable",
-    "mm_profile_read", "mm_status_string", "mm_version", "mm_corr_noalloc", "KERNELS", "BASES", "PRECISIONS", "STAGES",
+    "mm_profile_read", "mm_status_string", "mm_version", "mm_corr_noalloc", "mm_autotune", "KERNELS", "BASES", "PRECISIONS", "STAGES",
 ]
 
 
@@ -259,6 +259,19 @@ def mm_estimate_host(plan, offsets, t, logp, N, window=None, coeffs=None, sigma=
     if st != 0 and st not in allow_status:
         raise MMError(st, "mm_estimate_host")
     return st, int(Nu.value)
+
+
+def mm_autotune(plan, offsets, t, logp, N, window=None, coeffs=None, reps=5, stream=None) -> dict:
+    """Time every candidate configuration of stages (a)-(c) on this data and
+    keep the fastest in the plan; returns mm_plan_get_info afterwards."""
+    if coeffs is None:
+        coeffs = _alloc_coeffs(plan, N, t.device)
+    t0, t1 = window if window is not None else (0.0, 0.0)
+    po, pt, pp = _events(offsets, t, logp)
+    _check(_lib.load().mm_autotune(plan.handle, po, pt, pp, int(N), float(t0), float(t1),
+                                   _dptr(coeffs, _coef_dtype(plan), "coeffs"), int(reps), _stream(stream)),
+           "mm_autotune")
+    return mm_plan_get_info(plan)
 
 
 def mm_plan_sync(plan) -> int:

@@ -21,8 +21,8 @@ STATUS_NAMES = {
 KERNELS = {"gauss": 0, "kb": 1, "es": 2}
 BASES = {"dirichlet": 0, "fejer": 1}
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "3xtf32": 2}
-SPREAD_ALGOS = {"default": 0, "scatter": 1, "gather": 2}
-STAGES = ["prep", "spread", "fft_cols", "fft_rows", "gram", "reduce", "setup"]
+SPREAD_ALGOS = {"default": 0, "scatter": 1, "gather": 2, "fused": 3}
+STAGES = ["prep", "spread", "fft_cols", "fft_rows", "gram", "reduce", "setup", "fused"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -50,7 +50,11 @@ class PlanInfo(ctypes.Structure):
         ("workspace_bytes", ctypes.c_int64),
         ("launches", ctypes.c_int64),
         ("gram_splits", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("spread_algo", ctypes.c_int32),
+        ("spread_tile", ctypes.c_int32),
+        ("fft_lg_cols", ctypes.c_int32),
+        ("fft_rowblk", ctypes.c_int32),
+        ("tuned_ms", ctypes.c_float),
     ]
 
 
@@ -79,6 +83,7 @@ def load():
         "mm_corr_noalloc": ([i32, i32, st, st, p, p, p, p], st),
         "mm_estimate_host": ([p, p, p, p, i32, d, d, p, p, p, ctypes.POINTER(i32), p], st),
         "mm_nyquist": ([p, p, p, d, d, ctypes.POINTER(i32), p], st),
+        "mm_autotune": ([p, p, p, p, i32, d, d, p, i32, p], st),
         "mm_plan_sync": ([p], st),
         "mm_plan_get_info": ([p, ctypes.POINTER(PlanInfo)], st),
         "mm_profile_enable": ([p, i32], st),

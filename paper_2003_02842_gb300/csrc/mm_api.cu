@@ -93,6 +93,7 @@ mm_status flags_to_status(int f) {
 struct mm_plan_s {
   mm_plan_desc desc{};
   int dev = 0;
+  int smem_optin = 0;  // largest dynamic shared memory per block on this device
   bool fp64 = false;
   size_t cs = 8;   // bytes per complex coefficient
   size_t rs = 4;   // bytes per real grid cell / output element
@@ -127,6 +128,12 @@ struct mm_plan_s {
   // per-cutoff configuration
   int cfg_N = -1;
   int tab_N = -1;
+  // autotuned choices (-1 = library default); applied by configure()
+  int tune_algo = -1;     // 0 scatter, 1 gather, 2 fused
+  int tune_tile = -1;     // spreading cells per block
+  int tune_lgcols = -1;   // FFT pass 1: log2 columns per block
+  int tune_rowblk = -1;   // FFT pass 2: lower rows per block
+  float tune_ms = 0.f;    // time of the chosen configuration
   int64_t Mr = 0;
   FftParams fft{};
   SpreadParams sp{};
@@ -231,16 +238,28 @@ mm_status configure(mm_plan p, int N) {
   f.nrad_q = radix_plan(Q, f.rad_q);
   const size_t cs = p->cs;
   const size_t budget = 48 * 1024;  // about four blocks per SM
+  const int max_elems = 256 * 16;   // the FFT kernels batch at most 16 elements per thread
   int lg = 4;                       // pass 1: up to 16 adjacent columns (128 B per row in FP32)
-  while (lg > 0 && ((size_t)2 * P * ((size_t)1 << lg) + P) * cs > budget) --lg;
+  while (lg > 0 && (((size_t)2 * P * ((size_t)1 << lg) + P) * cs > budget || (P << lg) > max_elems)) --lg;
   while (lg > 0 && (1 << (lg - 1)) >= Q) --lg;
   f.lg_cols = lg;
   f.H = P / 2 + 1;
   f.rowblk = 8;
   auto rows_lg = [](int rb) { int l = 0; while ((1 << l) < 2 * rb) ++l; return l; };
-  while (f.rowblk > 1 && ((size_t)2 * ((size_t)1 << rows_lg(f.rowblk)) * Q + Q) * cs > budget) f.rowblk >>= 1;
+  while (f.rowblk > 1 && (((size_t)2 * ((size_t)1 << rows_lg(f.rowblk)) * Q + Q) * cs > budget ||
+                          ((1 << rows_lg(f.rowblk)) * Q) > max_elems))
+    f.rowblk >>= 1;
   while (f.rowblk > 1 && f.rowblk / 2 >= f.H) f.rowblk >>= 1;
   f.lg_rowcols = rows_lg(f.rowblk);
+  if (p->tune_lgcols >= 0 && p->tune_lgcols <= 5 && (1 << p->tune_lgcols) <= 2 * Q &&
+      (P << p->tune_lgcols) <= max_elems && ((size_t)2 * P * ((size_t)1 << p->tune_lgcols) + P) * cs <= 100 * 1024)
+    f.lg_cols = p->tune_lgcols;
+  if (p->tune_rowblk >= 1 && p->tune_rowblk <= 32 && p->tune_rowblk / 2 < f.H &&
+      ((1 << rows_lg(p->tune_rowblk)) * Q) <= max_elems &&
+      ((size_t)2 * ((size_t)1 << rows_lg(p->tune_rowblk)) * Q + Q) * cs <= 100 * 1024) {
+    f.rowblk = p->tune_rowblk;
+    f.lg_rowcols = rows_lg(f.rowblk);
+  }
   f.N = N;
 
   SpreadParams s{};
@@ -253,11 +272,17 @@ mm_status configure(mm_plan p, int N) {
   s.max_events = p->desc.max_events;
   const int tmax = spread_max_tile(p->fp64);
   int tile = p->desc.spread_tile > 0 ? std::min(p->desc.spread_tile, tmax) : tmax;
+  if (p->tune_tile > 0) tile = std::min(p->tune_tile, tmax);
   if (Mr <= (int64_t)tile) {
     tile = (int)Mr;
     s.single_tile = 1;
   }
-  s.algo = p->desc.spread_algo == 2 ? 1 : 0;
+  const bool fits = fused_smem(f, Mr, p->fp64) + 2048 <= (size_t)p->smem_optin;
+  int algo = p->desc.spread_algo == 2 ? 1 : (p->desc.spread_algo == 3 ? 2 : 0);
+  if (p->tune_algo >= 0) algo = p->tune_algo;
+  if (algo == 2 && !fits) algo = 0;
+  s.algo = algo == 1 ? 1 : 0;
+  s.fused = algo == 2 ? 1 : 0;
   s.tile = tile;
   s.ntiles = (int)((Mr + tile - 1) / tile);
   s.es_beta = 2.3 * 2.0 * p->msp;
@@ -346,33 +371,39 @@ mm_status coeffs_impl(mm_plan p, const int64_t* off, const double* t, const doub
   if (r != MM_OK) return r;
   r = ensure_tables(p, N, st);
   if (r != MM_OK) return r;
-  {
-    StageScope sc(p, MM_STAGE_PREP, st);
-    if (p->fp64)
-      MM_CUDA(launch_prep_f64(off, t, logp, p->bounds, D, p->Mr, p->desc.max_events, p->rec_b0, p->rec_d,
-                              p->rec_v, p->status, st));
-    else
-      MM_CUDA(launch_prep_f32(off, t, logp, p->bounds, D, p->Mr, p->desc.max_events, p->rec_b0, p->rec_d,
-                              p->rec_v, p->status, st));
-  }
-  {
-    StageScope sc(p, MM_STAGE_SPREAD, st);
-    if (p->fp64)
-      MM_CUDA(launch_spread_f64(off, p->rec_b0, p->rec_d, p->rec_v, p->sp, (double*)p->grid, p->status, st));
-    else
-      MM_CUDA(launch_spread_f32(off, p->rec_b0, p->rec_d, p->rec_v, p->sp, (float*)p->grid, p->status, st));
-  }
-  {
-    StageScope sc(p, MM_STAGE_FFT_COLS, st);
-    if (p->fp64) MM_CUDA(launch_fft_cols_f64((double*)p->grid, p->fft, D, p->W, p->status, st));
-    else MM_CUDA(launch_fft_cols_f32((float*)p->grid, p->fft, D, p->W, p->status, st));
-  }
-  {
-    StageScope sc(p, MM_STAGE_FFT_ROWS, st);
-    if (p->fp64)
-      MM_CUDA(launch_fft_rows_f64((const double*)p->grid, p->fft, D, p->W, p->U, p->decon, coeffs, p->status, st));
-    else
-      MM_CUDA(launch_fft_rows_f32((const float*)p->grid, p->fft, D, p->W, p->U, p->decon, coeffs, p->status, st));
+  if (p->sp.fused) {
+    StageScope sc(p, MM_STAGE_FUSED, st);
+    MM_CUDA(launch_coeff_fused(p->fp64, off, t, logp, p->bounds, p->sp, p->fft, p->W, p->U, p->decon, coeffs,
+                               p->status, st));
+  } else {
+    {
+      StageScope sc(p, MM_STAGE_PREP, st);
+      if (p->fp64)
+        MM_CUDA(launch_prep_f64(off, t, logp, p->bounds, D, p->Mr, p->desc.max_events, p->rec_b0, p->rec_d,
+                                p->rec_v, p->status, st));
+      else
+        MM_CUDA(launch_prep_f32(off, t, logp, p->bounds, D, p->Mr, p->desc.max_events, p->rec_b0, p->rec_d,
+                                p->rec_v, p->status, st));
+    }
+    {
+      StageScope sc(p, MM_STAGE_SPREAD, st);
+      if (p->fp64)
+        MM_CUDA(launch_spread_f64(off, p->rec_b0, p->rec_d, p->rec_v, p->sp, (double*)p->grid, p->status, st));
+      else
+        MM_CUDA(launch_spread_f32(off, p->rec_b0, p->rec_d, p->rec_v, p->sp, (float*)p->grid, p->status, st));
+    }
+    {
+      StageScope sc(p, MM_STAGE_FFT_COLS, st);
+      if (p->fp64) MM_CUDA(launch_fft_cols_f64((double*)p->grid, p->fft, D, p->W, p->status, st));
+      else MM_CUDA(launch_fft_cols_f32((float*)p->grid, p->fft, D, p->W, p->status, st));
+    }
+    {
+      StageScope sc(p, MM_STAGE_FFT_ROWS, st);
+      if (p->fp64)
+        MM_CUDA(launch_fft_rows_f64((const double*)p->grid, p->fft, D, p->W, p->U, p->decon, coeffs, p->status, st));
+      else
+        MM_CUDA(launch_fft_rows_f32((const float*)p->grid, p->fft, D, p->W, p->U, p->decon, coeffs, p->status, st));
+    }
   }
   if (N_used) *N_used = N;
   return MM_OK;
@@ -458,7 +489,7 @@ mm_status mm_plan_create(const mm_plan_desc* desc, mm_plan* out) {
   if (d.basis < MM_BASIS_DIRICHLET || d.basis > MM_BASIS_FEJER) return MM_ERR_INVALID_ARG;
   if (d.prec < MM_PREC_FP64 || d.prec > MM_PREC_MIXED_3XTF32) return MM_ERR_INVALID_ARG;
   if (d.spread_tile < 0 || d.spread_tile > 50000) return MM_ERR_INVALID_ARG;
-  if (d.spread_algo < 0 || d.spread_algo > 2) return MM_ERR_INVALID_ARG;
+  if (d.spread_algo < 0 || d.spread_algo > 3) return MM_ERR_INVALID_ARG;
   for (int i = 0; i < 5; ++i)
     if (d.reserved[i] != 0) return MM_ERR_INVALID_ARG;
   const int msp = msp_rule(d.kernel, d.tol);
@@ -479,7 +510,8 @@ mm_status mm_plan_create(const mm_plan_desc* desc, mm_plan* out) {
     return MM_ERR_UNSUPPORTED;
   }
   p->n_max = n;
-  if (cudaGetDevice(&p->dev) != cudaSuccess) {
+  if (cudaGetDevice(&p->dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&p->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->dev) != cudaSuccess) {
     delete p;
     return MM_ERR_CUDA;
   }
@@ -620,6 +652,75 @@ mm_status mm_estimate_host(mm_plan p, const int64_t* h_offsets, const double* h_
   return mm_plan_sync(p);
 }
 
+mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, const double* d_logp, int32_t N,
+                      double t0, double t1, void* d_coeffs, int32_t reps, void* stream) {
+  mm_status r = check_plan(p);
+  if (r != MM_OK) return r;
+  if (!d_offsets || !d_t || !d_logp || !d_coeffs || N < 1 || N > p->desc.N_max) return MM_ERR_INVALID_ARG;
+  if (reps < 1) reps = 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool prof = p->prof;
+  p->prof = false;
+  struct Cand { int algo, tile, lgc, rb; };
+  std::vector<Cand> cands;
+  const int tmax = spread_max_tile(p->fp64);
+  for (int tile : {tmax / 4, tmax / 2, tmax})
+    for (int lgc : {3, 4, 5})
+      for (int rb : {4, 8, 16}) cands.push_back({0, tile, lgc, rb});
+  for (int tile : {tmax / 2, tmax}) cands.push_back({1, tile, 4, 8});
+  for (int lgc : {3, 4})
+    for (int rb : {4, 8}) cands.push_back({2, tmax, lgc, rb});
+  cudaEvent_t e0, e1;
+  MM_CUDA(cudaEventCreate(&e0));
+  MM_CUDA(cudaEventCreate(&e1));
+  float best = 3.0e38f;
+  Cand bestc{-1, -1, -1, -1};
+  const Cand saved{p->tune_algo, p->tune_tile, p->tune_lgcols, p->tune_rowblk};
+  for (const Cand& c : cands) {
+    p->tune_algo = c.algo;
+    p->tune_tile = c.tile;
+    p->tune_lgcols = c.lgc;
+    p->tune_rowblk = c.rb;
+    p->cfg_N = -1;  // force reconfiguration
+    if (configure(p, N) != MM_OK) continue;
+    if (c.algo == 2 && !p->sp.fused) continue;  // fused variant does not fit
+    // warm-up (also builds the tables for N)
+    if (coeffs_impl(p, d_offsets, d_t, d_logp, N, t0, t1, d_coeffs, nullptr, st) != MM_OK) continue;
+    cudaEventRecord(e0, st);
+    bool ok = true;
+    for (int i = 0; i < reps && ok; ++i)
+      ok = coeffs_impl(p, d_offsets, d_t, d_logp, N, t0, t1, d_coeffs, nullptr, st) == MM_OK;
+    cudaEventRecord(e1, st);
+    if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (ms < best) {
+      best = ms;
+      bestc = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->prof = prof;
+  if (bestc.algo < 0) {
+    p->tune_algo = saved.algo;
+    p->tune_tile = saved.tile;
+    p->tune_lgcols = saved.lgc;
+    p->tune_rowblk = saved.rb;
+    p->cfg_N = -1;
+    cudaGetLastError();
+    return MM_ERR_CUDA;
+  }
+  p->tune_algo = bestc.algo;
+  p->tune_tile = bestc.tile;
+  p->tune_lgcols = bestc.lgc;
+  p->tune_rowblk = bestc.rb;
+  p->tune_ms = best;
+  p->cfg_N = -1;
+  return configure(p, N);
+}
+
 mm_status mm_nyquist(mm_plan p, const int64_t* d_offsets, const double* d_t, double t0, double t1, int32_t* N_out,
                      void* stream) {
   mm_status r = check_plan(p);
@@ -671,6 +772,11 @@ mm_status mm_plan_get_info(mm_plan p, mm_plan_info* info) {
   info->workspace_bytes = p->workspace;
   info->launches = p->launches;
   info->gram_splits = p->gram.splits;
+  info->spread_algo = p->sp.fused ? 3 : (p->sp.algo == 1 ? 2 : 1);
+  info->spread_tile = p->sp.tile;
+  info->fft_lg_cols = p->fft.lg_cols;
+  info->fft_rowblk = p->fft.rowblk;
+  info->tuned_ms = p->tune_ms;
   return MM_OK;
 }
 

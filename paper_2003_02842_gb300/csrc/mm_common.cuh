@@ -58,6 +58,7 @@ struct SpreadParams {
   int kernel;        // mm_kernel
   int single_tile;   // 1: one block covers the whole (small) grid
   int algo;          // 0: scatter into a shared-memory tile, 1: gather per cell
+  int fused;         // 1: stages (a)-(c) in one CTA per asset (grid in shared memory)
   // kernel constants
   double es_beta;    // ES: beta
   double es_inv_w;   // ES: 1 / M_sp  (support half-width in cells)
@@ -135,6 +136,10 @@ cudaError_t launch_fft_rows_f32(const float* grid, const FftParams& f, int D, co
 cudaError_t launch_fft_rows_f64(const double* grid, const FftParams& f, int D, const void* W,
                                 const void* U, const void* decon, void* coeffs, const int* status, cudaStream_t s);
 int spread_max_tile(bool fp64);
+size_t fused_smem(const FftParams& f, int64_t Mr, bool fp64);
+cudaError_t launch_coeff_fused(bool fp64, const int64_t* off, const double* t, const double* logp, const Rescale* rs,
+                               const SpreadParams& sp, const FftParams& f, const void* W, const void* U,
+                               const void* decon, void* coeffs, int* status, cudaStream_t s);
 size_t fft_cols_smem(const FftParams& f, bool fp64);
 size_t fft_rows_smem(const FftParams& f, bool fp64);
 

@@ -17,167 +17,23 @@
 #include <math.h>
 
 #include "mm_common.cuh"
+#include "mm_fft_dev.cuh"
 
 namespace mmgpu {
 
-// ------------------------------------------------------------ small DFTs
-// Forward DFTs (exponent -2 pi i j k / R) of R = 2, 3, 4, 5, 8 points.
-template <typename T>
-__device__ __forceinline__ void dft2(Cplx<T>& a, Cplx<T>& b) {
-  Cplx<T> s = cadd(a, b), d = csub(a, b);
-  a = s;
-  b = d;
-}
-
-template <typename T, int R>
-struct Dft;
-
-template <typename T>
-struct Dft<T, 2> {
-  static __device__ __forceinline__ void run(Cplx<T>* v) { dft2(v[0], v[1]); }
-};
-
-template <typename T>
-struct Dft<T, 3> {
-  static __device__ __forceinline__ void run(Cplx<T>* v) {
-    const T c = (T)-0.5, s = (T)0.866025403784438646763723170752936183;  // cos, sin of 2 pi / 3
-    Cplx<T> p = cadd(v[1], v[2]), m = csub(v[1], v[2]);
-    Cplx<T> y0 = cadd(v[0], p);
-    Cplx<T> a = {v[0].x + c * p.x, v[0].y + c * p.y};
-    Cplx<T> b = {s * m.x, s * m.y};
-    Cplx<T> jb = cmul_mi(b);  // -i s (x1 - x2)
-    v[0] = y0;
-    v[1] = cadd(a, jb);
-    v[2] = csub(a, jb);
-  }
-};
-
-template <typename T>
-struct Dft<T, 4> {
-  static __device__ __forceinline__ void run(Cplx<T>* v) {
-    Cplx<T> s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-    Cplx<T> s13 = cadd(v[1], v[3]), d13 = cmul_mi(csub(v[1], v[3]));
-    v[0] = cadd(s02, s13);
-    v[2] = csub(s02, s13);
-    v[1] = cadd(d02, d13);
-    v[3] = csub(d02, d13);
-  }
-};
-
-template <typename T>
-struct Dft<T, 5> {
-  static __device__ __forceinline__ void run(Cplx<T>* v) {
-    const T c1 = (T)0.309016994374947424102293417182819059;   // cos(2 pi/5)
-    const T c2 = (T)-0.809016994374947424102293417182819059;  // cos(4 pi/5)
-    const T s1 = (T)0.951056516295153572116439333379382143;   // sin(2 pi/5)
-    const T s2 = (T)0.587785252292473129168705954639072769;   // sin(4 pi/5)
-    Cplx<T> p14 = cadd(v[1], v[4]), m14 = csub(v[1], v[4]);
-    Cplx<T> p23 = cadd(v[2], v[3]), m23 = csub(v[2], v[3]);
-    Cplx<T> y0 = cadd(v[0], cadd(p14, p23));
-    Cplx<T> a1 = {v[0].x + c1 * p14.x + c2 * p23.x, v[0].y + c1 * p14.y + c2 * p23.y};
-    Cplx<T> a2 = {v[0].x + c2 * p14.x + c1 * p23.x, v[0].y + c2 * p14.y + c1 * p23.y};
-    Cplx<T> b1 = {s1 * m14.x + s2 * m23.x, s1 * m14.y + s2 * m23.y};
-    Cplx<T> b2 = {s2 * m14.x - s1 * m23.x, s2 * m14.y - s1 * m23.y};
-    Cplx<T> jb1 = cmul_mi(b1), jb2 = cmul_mi(b2);
-    v[0] = y0;
-    v[1] = cadd(a1, jb1);
-    v[4] = csub(a1, jb1);
-    v[2] = cadd(a2, jb2);
-    v[3] = csub(a2, jb2);
-  }
-};
-
-template <typename T>
-struct Dft<T, 8> {
-  static __device__ __forceinline__ void run(Cplx<T>* v) {
-    const T r = (T)0.707106781186547524400844362104849039;  // sqrt(1/2)
-    Cplx<T> e[4] = {v[0], v[2], v[4], v[6]};
-    Cplx<T> o[4] = {v[1], v[3], v[5], v[7]};
-    Dft<T, 4>::run(e);
-    Dft<T, 4>::run(o);
-    // o_k *= w8^k, w8 = e^{-i pi/4}
-    Cplx<T> o1 = {r * (o[1].x + o[1].y), r * (o[1].y - o[1].x)};
-    Cplx<T> o2 = cmul_mi(o[2]);
-    Cplx<T> o3 = {r * (o[3].y - o[3].x), -r * (o[3].x + o[3].y)};
-    v[0] = cadd(e[0], o[0]);
-    v[4] = csub(e[0], o[0]);
-    v[1] = cadd(e[1], o1);
-    v[5] = csub(e[1], o1);
-    v[2] = cadd(e[2], o2);
-    v[6] = csub(e[2], o2);
-    v[3] = cadd(e[3], o3);
-    v[7] = csub(e[3], o3);
-  }
-};
-
-// j / d for j, d < 2^16 with m = ceil(2^32 / d): floor(j m / 2^32) is exact,
-// because the rounding of m adds less than 2^-16 < 1/d to j / d.
-__device__ __forceinline__ unsigned magic_of(unsigned d) { return d <= 1u ? 0u : 0xFFFFFFFFu / d + 1u; }
-__device__ __forceinline__ int fast_div(int j, int d, unsigned m) { return d == 1 ? j : (int)__umulhi((unsigned)j, m); }
-
-// Shared-memory slot of element j of column c when B = 2^lgB columns are
-// interleaved: row j holds the B columns, permuted by an XOR with the row
-// index so that reading one column down many rows (the transposed loads of
-// pass 2) touches distinct banks while a row stays one contiguous segment.
-__device__ __forceinline__ int swz(int j, int c, int lgB) { return (j << lgB) | (c ^ (j & ((1 << lgB) - 1))); }
-
-// One autosorting Stockham stage of radix R over L-point sequences stored as
-// B = 2^lgB interleaved columns (element j of column c at swz(j, c)).
-// Ns is the product of the radices already applied; tw[j] = e^{-2 pi i j / L}.
-template <typename T, int R>
-__device__ __forceinline__ void stockham_stage(const Cplx<T>* __restrict__ in, Cplx<T>* __restrict__ out,
-                                               const Cplx<T>* __restrict__ tw, int L, int lgB, int Ns) {
-  const int nb = L / R;
-  const int twstep = L / (Ns * R);
-  const unsigned mNs = magic_of((unsigned)Ns);
-  const int B = 1 << lgB;
-  for (int idx = threadIdx.x; idx < (nb << lgB); idx += blockDim.x) {
-    const int j = idx >> lgB, c = idx & (B - 1);
-    const int q = fast_div(j, Ns, mNs);
-    const int k = j - q * Ns;
-    Cplx<T> v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = in[swz(j + r * nb, c, lgB)];
-    if (Ns > 1) {
-#pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * k * twstep]);
-    }
-    Dft<T, R>::run(v);
-    const int base = q * Ns * R + k;
-#pragma unroll
-    for (int r = 0; r < R; ++r) out[swz(base + r * Ns, c, lgB)] = v[r];
-  }
-}
-
-// Full L-point FFT of 2^lgB columns; returns the buffer holding the result.
-template <typename T>
-__device__ Cplx<T>* stockham_fft(Cplx<T>* a, Cplx<T>* b, const Cplx<T>* tw, int L, int lgB, const int* rad,
-                                 int nrad) {
-  int Ns = 1;
-  Cplx<T>* in = a;
-  Cplx<T>* out = b;
-  for (int s = 0; s < nrad; ++s) {
-    const int r = rad[s];
-    switch (r) {
-      case 2: stockham_stage<T, 2>(in, out, tw, L, lgB, Ns); break;
-      case 3: stockham_stage<T, 3>(in, out, tw, L, lgB, Ns); break;
-      case 4: stockham_stage<T, 4>(in, out, tw, L, lgB, Ns); break;
-      case 5: stockham_stage<T, 5>(in, out, tw, L, lgB, Ns); break;
-      default: stockham_stage<T, 8>(in, out, tw, L, lgB, Ns); break;
-    }
-    __syncthreads();
-    Cplx<T>* x = in;
-    in = out;
-    out = x;
-    Ns *= r;
-  }
-  return in;
-}
+// Elements per thread held in registers between the batched global loads
+// and the shared-memory stages (the host keeps P 2^lg_cols and 2^lg_rowcols Q
+// at most kFftThreads * kFftPer).
+constexpr int kFftThreads = 256;
+constexpr int kFftPer = 16;
 
 // ------------------------------------------------------------ pass 1
+// Every global load of a block (its column values and the write-back
+// twiddles) is issued in one batch into registers before the first barrier,
+// so the block waits for memory once.
 template <typename T>
-__global__ void __launch_bounds__(256) k_fft_cols(Cplx<T>* __restrict__ z, FftParams f,
-                                                  const Cplx<T>* __restrict__ W, const int* __restrict__ gate) {
+__global__ void __launch_bounds__(kFftThreads) k_fft_cols(Cplx<T>* __restrict__ z, FftParams f,
+                                                          const Cplx<T>* __restrict__ W, const int* __restrict__ gate) {
   if (*gate) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int P = f.P, Q = f.Q, lgB = f.lg_cols, B = 1 << lgB;
@@ -186,87 +42,139 @@ __global__ void __launch_bounds__(256) k_fft_cols(Cplx<T>* __restrict__ z, FftPa
   Cplx<T>* tw = buf1 + P * B;
   const int j20 = blockIdx.x * B;
   Cplx<T>* za = z + (int64_t)blockIdx.y * f.n;
-  for (int j = threadIdx.x; j < P; j += blockDim.x) tw[j] = W[j * Q];
-  for (int idx = threadIdx.x; idx < (P << lgB); idx += blockDim.x) {
-    const int j1 = idx >> lgB, c = idx & (B - 1), j2 = j20 + c;
-    buf0[swz(j1, c, lgB)] = (j2 < Q) ? za[Q * j1 + j2] : Cplx<T>{(T)0, (T)0};
+  const int total = P << lgB;
+  Cplx<T> v[kFftPer], wt[kFftPer];
+#pragma unroll
+  for (int i = 0; i < kFftPer; ++i) {
+    const int idx = threadIdx.x + i * kFftThreads;
+    v[i] = Cplx<T>{(T)0, (T)0};
+    wt[i] = Cplx<T>{(T)1, (T)0};
+    if (idx < total) {
+      const int j1 = idx >> lgB, j2 = j20 + (idx & (B - 1));
+      if (j2 < Q) {
+        v[i] = za[Q * j1 + j2];
+        wt[i] = W[j2 * j1];  // j2 k1 <= (Q-1)(P-1) < n: no reduction
+      }
+    }
+  }
+  for (int j = threadIdx.x; j < P; j += kFftThreads) tw[j] = W[j * Q];
+#pragma unroll
+  for (int i = 0; i < kFftPer; ++i) {
+    const int idx = threadIdx.x + i * kFftThreads;
+    if (idx < total) buf0[swz(idx >> lgB, idx & (B - 1), lgB)] = v[i];
   }
   __syncthreads();
   const Cplx<T>* X = stockham_fft(buf0, buf1, tw, P, lgB, f.rad_p, f.nrad_p);
-  for (int idx = threadIdx.x; idx < (P << lgB); idx += blockDim.x) {
-    const int k1 = idx >> lgB, c = idx & (B - 1), j2 = j20 + c;
-    // j2 k1 <= (Q-1)(P-1) < n: the twiddle index needs no reduction
-    if (j2 < Q) za[Q * k1 + j2] = cmul(X[swz(k1, c, lgB)], W[j2 * k1]);
+#pragma unroll
+  for (int i = 0; i < kFftPer; ++i) {
+    const int idx = threadIdx.x + i * kFftThreads;
+    if (idx < total) {
+      const int k1 = idx >> lgB, c = idx & (B - 1), j2 = j20 + c;
+      if (j2 < Q) za[Q * k1 + j2] = cmul(X[swz(k1, c, lgB)], wt[i]);
+    }
   }
+}
+
+// Rows held by a pass-2 block: lower rows k1 = r0 .. r1-1, then the mirrors
+// P - k1 that are not lower rows (k1 in [max(r0,1), min(r1, P-H+1))), so the
+// block's output segments are contiguous. Closed forms, no search.
+struct RowSet {
+  int r0, nlow, mlo, nr;
+};
+__device__ __forceinline__ RowSet row_set(int r0, int rowblk, int P, int H) {
+  RowSet r;
+  const int r1 = min(r0 + rowblk, H);
+  r.r0 = r0;
+  r.nlow = r1 - r0;
+  r.mlo = max(r0, 1);
+  const int mhi = min(r1, P - H + 1);
+  r.nr = r.nlow + max(0, mhi - r.mlo);
+  return r;
+}
+__device__ __forceinline__ int row_of(const RowSet& r, int ri, int P) {
+  if (ri < r.nlow) return r.r0 + ri;
+  if (ri < r.nr) return P - (r.mlo + (ri - r.nlow));
+  return -1;
+}
+// index of the row holding Z_{n-k} for the rows of the block
+__device__ __forceinline__ int partner_of(const RowSet& r, int ri, int P, int H) {
+  if (ri < r.nlow) {
+    const int k1 = r.r0 + ri;
+    if (k1 >= 1 && P - k1 >= H) return r.nlow + (k1 - r.mlo);
+    return ri;  // row 0 and the self-mirrored row P/2
+  }
+  return (r.mlo + (ri - r.nlow)) - r.r0;
 }
 
 // ------------------------------------------------------------ pass 2
 template <typename T>
-__global__ void __launch_bounds__(256) k_fft_rows(const Cplx<T>* __restrict__ z, FftParams f,
-                                                  const Cplx<T>* __restrict__ W, const Cplx<T>* __restrict__ U,
-                                                  const T* __restrict__ decon, Cplx<T>* __restrict__ out,
-                                                  const int* __restrict__ gate) {
+__global__ void __launch_bounds__(kFftThreads) k_fft_rows(const Cplx<T>* __restrict__ z, FftParams f,
+                                                          const Cplx<T>* __restrict__ W, const Cplx<T>* __restrict__ U,
+                                                          const T* __restrict__ decon, Cplx<T>* __restrict__ out,
+                                                          const int* __restrict__ gate) {
   if (*gate) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_row[64], s_partner[64];
-  __shared__ int s_nrows;
   const int P = f.P, Q = f.Q;
   const int lgB = f.lg_rowcols, B = 1 << lgB;  // padded number of rows held
-  const int r0 = blockIdx.x * f.rowblk;
-  const int r1 = min(r0 + f.rowblk, f.H);
-  if (threadIdx.x == 0) {
-    // lower rows first (ascending k1), then the mirrors P - k1 that are not
-    // lower rows themselves (descending), so output segments stay contiguous
-    int nr = 0;
-    for (int k1 = r0; k1 < r1; ++k1) s_row[nr++] = k1;
-    const int nlow = nr;
-    for (int i = 0; i < nlow; ++i) {
-      const int k1 = s_row[i];
-      const int m = (P - k1) % P;
-      if (m >= f.H) s_row[nr++] = m;
-    }
-    for (int i = 0; i < nr; ++i) {
-      const int m = (P - s_row[i]) % P;
-      int pi = i;
-      for (int q = 0; q < nr; ++q)
-        if (s_row[q] == m) pi = q;
-      s_partner[i] = pi;
-    }
-    for (int i = nr; i < B; ++i) s_row[i] = -1;
-    s_nrows = nr;
-  }
-  __syncthreads();
-  const int nr = s_nrows;
+  const RowSet rs = row_set(blockIdx.x * f.rowblk, f.rowblk, P, f.H);
   Cplx<T>* buf0 = reinterpret_cast<Cplx<T>*>(smem_raw);
   Cplx<T>* buf1 = buf0 + B * Q;
   Cplx<T>* tw = buf1 + B * Q;
   const Cplx<T>* za = z + (int64_t)blockIdx.y * f.n;
-  for (int j = threadIdx.x; j < Q; j += blockDim.x) tw[j] = W[j * P];
+  const int total = B * Q;
   const unsigned mQ = magic_of((unsigned)Q);
-  for (int idx = threadIdx.x; idx < B * Q; idx += blockDim.x) {
-    const int ri = fast_div(idx, Q, mQ), j2 = idx - ri * Q;
-    const int row = s_row[ri];
-    buf0[swz(j2, ri, lgB)] = row >= 0 ? za[Q * row + j2] : Cplx<T>{(T)0, (T)0};
+  // batched loads: row values (load order: row-major, coalesced), and for
+  // the unpack (order: k2-major) the U and deconvolution factors
+  Cplx<T> v[kFftPer], uk[kFftPer];
+  T dk[kFftPer];
+#pragma unroll
+  for (int i = 0; i < kFftPer; ++i) {
+    const int idx = threadIdx.x + i * kFftThreads;
+    v[i] = Cplx<T>{(T)0, (T)0};
+    uk[i] = Cplx<T>{(T)0, (T)0};
+    dk[i] = (T)0;
+    if (idx < total) {
+      const int ri = fast_div(idx, Q, mQ), j2 = idx - ri * Q;
+      const int row = row_of(rs, ri, P);
+      if (row >= 0) v[i] = za[Q * row + j2];
+      const int k2 = idx >> lgB, ro = idx & (B - 1);
+      const int k1 = row_of(rs, ro, P);
+      const int k = k1 + P * k2;
+      if (k1 >= 0 && k <= f.N) {
+        uk[i] = U[k];
+        dk[i] = decon[k];
+      }
+    }
+  }
+  for (int j = threadIdx.x; j < Q; j += kFftThreads) tw[j] = W[j * P];
+#pragma unroll
+  for (int i = 0; i < kFftPer; ++i) {
+    const int idx = threadIdx.x + i * kFftThreads;
+    if (idx < total) {
+      const int ri = fast_div(idx, Q, mQ), j2 = idx - ri * Q;
+      buf0[swz(j2, ri, lgB)] = v[i];
+    }
   }
   __syncthreads();
   const Cplx<T>* X = stockham_fft(buf0, buf1, tw, Q, lgB, f.rad_q, f.nrad_q);
   Cplx<T>* oa = out + (int64_t)blockIdx.y * (f.N + 1);
-  for (int idx = threadIdx.x; idx < (Q << lgB); idx += blockDim.x) {
+#pragma unroll
+  for (int i = 0; i < kFftPer; ++i) {
+    const int idx = threadIdx.x + i * kFftThreads;
+    if (idx >= total) continue;
     const int k2 = idx >> lgB, ri = idx & (B - 1);
-    if (ri >= nr) continue;
-    const int k1 = s_row[ri];
+    const int k1 = row_of(rs, ri, P);
     const int k = k1 + P * k2;
-    if (k > f.N) continue;
-    const int pri = s_partner[ri];
+    if (k1 < 0 || k > f.N) continue;
+    const int pri = partner_of(rs, ri, P, f.H);
     const int pk2 = (k1 == 0) ? ((k2 == 0) ? 0 : Q - k2) : Q - 1 - k2;
     const Cplx<T> Zk = X[swz(k2, ri, lgB)];
     const Cplx<T> Zc = cconj(X[swz(pk2, pri, lgB)]);
     const Cplx<T> E = {(T)0.5 * (Zk.x + Zc.x), (T)0.5 * (Zk.y + Zc.y)};
     const Cplx<T> dlt = csub(Zk, Zc);
     const Cplx<T> O = {(T)0.5 * dlt.y, (T)-0.5 * dlt.x};  // (Zk - Zc) / (2i)
-    const Cplx<T> G = cadd(E, cmul(U[k], O));
-    const T sc = decon[k];
-    oa[k] = Cplx<T>{G.x * sc, G.y * sc};
+    const Cplx<T> G = cadd(E, cmul(uk[i], O));
+    oa[k] = Cplx<T>{G.x * dk[i], G.y * dk[i]};
   }
 }
 
@@ -381,7 +289,8 @@ static cudaError_t launch_cols_t(T* grid, const FftParams& f, int D, const void*
   if (e != cudaSuccess) return e;
   const int B = 1 << f.lg_cols;
   dim3 grd((f.Q + B - 1) / B, D);
-  fn<<<grd, 256, smem, s>>>(reinterpret_cast<Cplx<T>*>(grid), f, (const Cplx<T>*)W, status + 1);
+  if ((f.P << f.lg_cols) > kFftThreads * kFftPer) return cudaErrorInvalidValue;
+  fn<<<grd, kFftThreads, smem, s>>>(reinterpret_cast<Cplx<T>*>(grid), f, (const Cplx<T>*)W, status + 1);
   return cudaGetLastError();
 }
 
@@ -393,7 +302,8 @@ static cudaError_t launch_rows_t(const T* grid, const FftParams& f, int D, const
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grd((f.H + f.rowblk - 1) / f.rowblk, D);
-  fn<<<grd, 256, smem, s>>>(reinterpret_cast<const Cplx<T>*>(grid), f, (const Cplx<T>*)W, (const Cplx<T>*)U,
+  if (((1 << f.lg_rowcols) * f.Q) > kFftThreads * kFftPer) return cudaErrorInvalidValue;
+  fn<<<grd, kFftThreads, smem, s>>>(reinterpret_cast<const Cplx<T>*>(grid), f, (const Cplx<T>*)W, (const Cplx<T>*)U,
                             (const T*)decon, (Cplx<T>*)coeffs, status + 1);
   return cudaGetLastError();
 }

@@ -233,10 +233,32 @@ def test_host_buffer_entry_point_matches_device_path():
     mm.mm_destroy(plan)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_fused_variant_and_autotuner(prec):
+    # the fused one-CTA-per-asset variant and every configuration the
+    # autotuner may pick give the same coefficients as the direct sum
+    import paper_2003_02842_gb300 as mm
+    ev = synth.c2_async(4)
+    N = ev.meta["N"]
+    tl = TOL[prec]
+    ref = oracle.coeffs_F(ev.offsets, ev.t, ev.logp, N)
+    out = run(dict(tol=tl["tol"], kernel="es", basis="dirichlet", prec=prec, spread_algo="fused"), ev, N)
+    assert out["info"]["spread_algo"] == 3
+    assert np.all(rel_l2_rows(out["F"], ref) <= tl["coef"])
+    plan = mm.mm_plan_create(D=ev.D, N_max=N, max_events=ev.n_events, tol=tl["tol"], kernel="es", prec=prec)
+    off, t, p = to_dev(ev)
+    info = mm.mm_autotune(plan, off, t, p, N, reps=2)
+    assert info["tuned_ms"] > 0 and info["spread_algo"] in (1, 2, 3)
+    F, _ = mm.mm_coeffs(plan, off, t, p, N)
+    assert mm.mm_plan_sync(plan) == 0
+    assert np.all(rel_l2_rows(F.cpu().numpy(), ref) <= tl["coef"])
+    mm.mm_destroy(plan)
+
+
 def test_profiling_counts_launches():
     import paper_2003_02842_gb300 as mm
     ev = synth.c1_sync(0)
-    plan = mm.mm_plan_create(D=2, N_max=500, max_events=ev.n_events, tol=1e-6)
+    plan = mm.mm_plan_create(D=2, N_max=500, max_events=ev.n_events, tol=1e-6, spread_algo="scatter")
     off, t, p = to_dev(ev)
     mm.mm_estimate(plan, off, t, p, 500)
     mm.mm_profile_enable(plan, True)
@@ -247,5 +269,6 @@ def test_profiling_counts_launches():
     assert prof["prep"][1] == 6 and prof["prep"][0] > 0  # bounds + per-event prep
     for stage in ("spread", "fft_cols", "fft_rows", "gram", "reduce"):
         assert prof[stage][1] == 3 and prof[stage][0] > 0
+    assert prof["fused"][1] == 0
     assert prof["setup"][1] == 0  # tables are cached per cutoff
     mm.mm_destroy(plan)
