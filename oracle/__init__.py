@@ -34,11 +34,17 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
     tmp = _LIB + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
-           "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    compile_c(_SRC, tmp)
     os.replace(tmp, _LIB)
     return _LIB
+
+
+def compile_c(src: str, out: str) -> None:
+    """The oracle's compiler line, also used by the tests that build copies of
+    the oracle with planted mistakes."""
+    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-shared", "-fPIC", "-o", out, src, "-lm"]
+    subprocess.run(cmd, check=True)
 
 
 _lib = None

@@ -89,6 +89,15 @@ def test_phase_exact_at_large_k(orc):
     c = orc.coeffs_at(t, d, 0.0, span, ks)
     want = 0.5 * np.exp(-1j * np.pi / 4 * (ks % 8))
     assert np.max(np.abs(c - want)) < 1e-15
+    # A time whose rescaled value is not a binary fraction (t / span =
+    # 1/28800): for k = 28800 m + r the exact phase is 2 pi r / 28800, which
+    # needs the low-order part of k * t / span at m ~ 1e3.
+    t = np.array([1.0])
+    r = np.array([1, 7, 12345, 28799])
+    ks = 28800 * 1000 + r
+    c = orc.coeffs_at(t, d, 0.0, span, ks)
+    want = 0.5 * np.exp(-2j * np.pi * r / 28800.0)
+    assert np.max(np.abs(c - want)) < 1e-15
 
 
 # --------------------------------------------------------------------------
