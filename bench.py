@@ -356,6 +356,7 @@ def main():
             "spread": rbytes * ev.n_events + gbytes * Mr * D,  # records in; grid out
             "fft_cols": 2.0 * gbytes * Mr * D,                 # grid in and out
             "fft_rows": gbytes * Mr * D + cbytes * (N + 1) * D,
+            "fft": gbytes * Mr * D + cbytes * (N + 1) * D,     # grid in, coefficients out
             "gram": cbytes * (N + 1) * D,                      # coefficients in
             "reduce": 0.0,
         }
@@ -382,6 +383,8 @@ def main():
                        "grid_Mr": Mr, "fft": [info["fft_P"], info["fft_Q"]], "gram_splits": info["gram_splits"],
                        "spread_algo": {1: "scatter", 2: "gather", 3: "fused"}.get(info["spread_algo"]),
                        "spread_tile": info["spread_tile"], "fft_blocking": [info["fft_lg_cols"], info["fft_rowblk"]],
+                       "fft_algo": "per-asset shared-memory" if info["fft_algo"] == 0 else "two-pass",
+                       "fft_radix": info["fft_radix"], "fft_split": info["fft_split"],
                        "autotuned": tuned is not None,
                        "replicas": world},
             "matrices_per_s": world * args.steps / (total_ms * 1e-3),

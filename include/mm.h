@@ -104,7 +104,11 @@ typedef struct {
                            with a gather per grid cell; 3 stages (a)-(c) fused in one
                            CTA per asset when the grid fits in shared memory, else 1.
                            All compute Eq. (12) exactly. */
-  int32_t reserved[5];  /* must be zero */
+  int32_t fft_algo;     /* stages (b)-(c) in the mixed precisions: 0 library default
+                           (one CTA per asset with the grid in shared memory when it
+                           fits, else 1); 1 two-pass FFT through global memory. The
+                           FP64 path always uses 1. Both compute Eqs. (13)-(14). */
+  int32_t reserved[4];  /* must be zero */
 } mm_plan_desc;
 
 typedef struct mm_plan_s* mm_plan;
@@ -112,7 +116,8 @@ typedef struct mm_plan_s* mm_plan;
 /* Per-stage timing and launch counters (device time from CUDA events on the
  * launching stream, summed since the last reset). */
 enum { MM_STAGE_PREP = 0, MM_STAGE_SPREAD = 1, MM_STAGE_FFT_COLS = 2, MM_STAGE_FFT_ROWS = 3,
-       MM_STAGE_GRAM = 4, MM_STAGE_REDUCE = 5, MM_STAGE_SETUP = 6, MM_STAGE_FUSED = 7, MM_NUM_STAGES = 8 };
+       MM_STAGE_GRAM = 4, MM_STAGE_REDUCE = 5, MM_STAGE_SETUP = 6, MM_STAGE_FUSED = 7, MM_STAGE_FFT = 8,
+       MM_NUM_STAGES = 9 };
 
 typedef struct {
   int32_t msp;           /* spreading half-width M_sp */
@@ -127,6 +132,10 @@ typedef struct {
   int32_t fft_lg_cols;   /* FFT pass 1: log2 of the columns per block */
   int32_t fft_rowblk;    /* FFT pass 2: lower rows per block */
   float tuned_ms;        /* mm_coeffs time of the configuration mm_autotune chose (0 if untuned) */
+  int32_t fft_algo;      /* stages (b)-(c) in use: 0 per-asset shared-memory FFT, 1 two-pass */
+  int32_t fft_passes;    /* per-asset FFT: number of radix passes (0 when not in use) */
+  int32_t fft_radix[4];  /* per-asset FFT: radix of each pass */
+  int32_t fft_split;     /* per-asset FFT: CTAs per asset (1 or 2; 0 when not in use) */
 } mm_plan_info;
 
 /* Create a plan: validates desc, allocates the workspace on the current

@@ -22,7 +22,8 @@ KERNELS = {"gauss": 0, "kb": 1, "es": 2}
 BASES = {"dirichlet": 0, "fejer": 1}
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "3xtf32": 2}
 SPREAD_ALGOS = {"default": 0, "scatter": 1, "gather": 2, "fused": 3}
-STAGES = ["prep", "spread", "fft_cols", "fft_rows", "gram", "reduce", "setup", "fused"]
+FFT_ALGOS = {"default": 0, "two_pass": 1}
+STAGES = ["prep", "spread", "fft_cols", "fft_rows", "gram", "reduce", "setup", "fused", "fft"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -36,7 +37,8 @@ class PlanDesc(ctypes.Structure):
         ("prec", ctypes.c_int),
         ("spread_tile", ctypes.c_int32),
         ("spread_algo", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("fft_algo", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 
@@ -55,6 +57,10 @@ class PlanInfo(ctypes.Structure):
         ("fft_lg_cols", ctypes.c_int32),
         ("fft_rowblk", ctypes.c_int32),
         ("tuned_ms", ctypes.c_float),
+        ("fft_algo", ctypes.c_int32),
+        ("fft_passes", ctypes.c_int32),
+        ("fft_radix", ctypes.c_int32 * 4),
+        ("fft_split", ctypes.c_int32),
     ]
 
 

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <vector>
 
 #include "mm_common.cuh"
@@ -42,12 +43,12 @@ int radix_plan(int L, int* rad) {
   return n;
 }
 
-// Smallest 5-smooth n >= nmin that splits as P * Q with P, Q <= kMaxFftLen;
+// Smallest even 5-smooth n >= nmin that splits as P * Q with P, Q <= kMaxFftLen;
 // P is the divisor closest to sqrt(n). Returns false when none exists.
 bool choose_fft(int64_t nmin, int64_t* n_out, int* P_out, int* Q_out) {
   const int64_t cap = (int64_t)kMaxFftLen * kMaxFftLen;
-  for (int64_t n = std::max<int64_t>(nmin, 1); n <= cap; ++n) {
-    if (!smooth235(n)) continue;
+  for (int64_t n = std::max<int64_t>(nmin, 2); n <= cap; ++n) {
+    if ((n & 1) || !smooth235(n)) continue;  // even n: rows of M_r = 2n floats stay 16-byte aligned
     int bestP = -1;
     double best = 1e300;
     for (int64_t P = 1; P <= kMaxFftLen && P <= n; ++P) {
@@ -66,6 +67,71 @@ bool choose_fft(int64_t nmin, int64_t* n_out, int* P_out, int* Q_out) {
   }
   return false;
 }
+
+// Plan of the per-asset FFT of n points split over `split` CTAs: the local
+// length nl = n / split factored into the fewest radices from the compiled
+// set (largest smallest factor on ties), even radices first in the list so
+// that the last entry, the first decimation-in-time pass, whose butterflies
+// are contiguous in shared memory, has an odd radix where one exists (fewer
+// bank conflicts). Returns false when nl needs more than kMaxAssetPasses
+// factors.
+bool plan_asset_fft(int64_t n, int split, int N, int maxr, AssetFft* out) {
+  static const int kRad[] = {32, 30, 27, 25, 24, 20, 18, 16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+  if (split < 1 || n % split) return false;
+  const int64_t nl = n / split;
+  std::vector<int> best, cur;
+  std::function<void(int64_t, int)> rec = [&](int64_t rest, int maxr) {
+    if (rest == 1) {
+      auto key = [](const std::vector<int>& v) {
+        return std::make_pair((int)v.size(), -*std::min_element(v.begin(), v.end()));
+      };
+      if (best.empty() || key(cur) < key(best)) best = cur;
+      return;
+    }
+    if ((int)cur.size() >= kMaxAssetPasses) return;
+    if (!best.empty() && (int)cur.size() + 1 > (int)best.size()) return;
+    for (int r : kRad) {
+      if (r > maxr || rest % r) continue;
+      cur.push_back(r);
+      rec(rest / r, r);
+      cur.pop_back();
+    }
+  };
+  if (nl < 2 || nl > (1 << 15)) return false;
+  rec(nl, maxr);
+  if (best.empty()) return false;
+  // the last entry is the first DIT pass (unit stride): keep an odd radix there
+  std::stable_sort(best.begin(), best.end(), [](int a, int b) {
+    if ((a & 1) != (b & 1)) return (a & 1) == 0;
+    return a > b;
+  });
+  AssetFft f{};
+  f.n = (int)n;
+  f.nl = (int)nl;
+  f.split = split;
+  f.N = N;
+  f.npass = (int)best.size();
+  int64_t L = nl;
+  int off = 0;
+  for (int q = 0; q < f.npass; ++q) {
+    f.rad[q] = best[q];
+    f.stride[q] = (int)(L / best[q]);
+    f.tw_off[q] = off;
+    if (f.stride[q] > 1) off += f.stride[q];
+    L /= best[q];
+  }
+  for (int q = f.npass; q < kMaxAssetPasses; ++q) {
+    f.rad[q] = 1;
+    f.stride[q] = 1;
+    f.tw_off[q] = off;
+  }
+  f.tw_rows = off;
+  *out = f;
+  return true;
+}
+
+// Twiddle entries (complex) of an asset FFT plan: four anchors per row.
+int64_t asset_twiddle_count(const AssetFft& f) { return 4 * (int64_t)f.tw_rows; }
 
 // M_sp rules of Sec. 2.2.5 (sigma = 2).
 int msp_rule(mm_kernel k, double eps) {
@@ -105,6 +171,8 @@ struct mm_plan_s {
   void* rec_d = nullptr;
   void* rec_v = nullptr;
   void* W = nullptr;
+  void* atw = nullptr;            // per-asset FFT pass twiddles (mixed path)
+  int64_t atw_cap = 0;            // entries allocated
   void* U = nullptr;
   void* decon = nullptr;
   double* glx = nullptr;
@@ -134,8 +202,13 @@ struct mm_plan_s {
   int tune_lgcols = -1;   // FFT pass 1: log2 columns per block
   int tune_rowblk = -1;   // FFT pass 2: lower rows per block
   float tune_ms = 0.f;    // time of the chosen configuration
+  int tune_fft = -1;      // 0 per-asset shared-memory FFT, 1 two-pass FFT
+  int tune_split = -1;    // per-asset FFT: CTAs per asset (1 or 2)
+  int tune_maxr = -1;     // per-asset FFT: largest radix (16 or 32)
   int64_t Mr = 0;
   FftParams fft{};
+  AssetFft afft{};
+  bool use_afft = false;  // stages (b)-(c) by the per-asset FFT kernel
   SpreadParams sp{};
   double tau = 0;
   int w_N = -1, w_basis = -1;
@@ -170,7 +243,7 @@ mm_status dalloc(mm_plan p, void** ptr, size_t bytes) {
 }
 
 void free_all(mm_plan p) {
-  void* ptrs[] = {p->grid, p->rec_b0, p->rec_d, p->rec_v, p->W, p->U, p->decon, p->glx, p->glw, p->bounds, p->status, p->gapbits, p->wsq,
+  void* ptrs[] = {p->grid, p->rec_b0, p->rec_d, p->rec_v, p->W, p->atw, p->U, p->decon, p->glx, p->glw, p->bounds, p->status, p->gapbits, p->wsq,
                   p->partial, p->acc[0], p->acc[1], p->s_off, p->s_t, p->s_p, p->s_coef, p->s_sigma, p->s_R};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -292,6 +365,20 @@ mm_status configure(mm_plan p, int N) {
   s.kb_b = kPi * (2.0 - 1.0 / sigma);
   s.kb_inv_phi0 = kPi * p->msp / sinh(s.kb_b * p->msp);
   p->tau = kPi * lam / ((double)Mr * (double)Mr);
+  // per-asset FFT: mixed path, the complex grid fits in shared memory and n
+  // factors into at most kMaxAssetPasses compiled radices
+  AssetFft af{};
+  int split = p->desc.D < kSMs ? 2 : 1;  // fewer assets than SMs: two CTAs per asset
+  if (p->tune_split == 1 || p->tune_split == 2) split = p->tune_split;
+  const int maxr = p->tune_maxr == 16 ? 16 : 32;
+  if (!plan_asset_fft(n, split, N, maxr, &af) && split == 2) split = 1;
+  bool afft = !p->fp64 && plan_asset_fft(n, split, N, maxr, &af) &&
+              asset_fft_smem(af) + 2048 <= (size_t)p->smem_optin && asset_twiddle_count(af) <= p->atw_cap;
+  int fft_algo = p->desc.fft_algo;
+  if (p->tune_fft >= 0) fft_algo = p->tune_fft == 0 ? 0 : 1;
+  if (fft_algo == 1) afft = false;
+  p->afft = af;
+  p->use_afft = afft && !s.fused;
   p->fft = f;
   p->sp = s;
   p->Mr = Mr;
@@ -304,6 +391,11 @@ mm_status ensure_tables(mm_plan p, int N, cudaStream_t st) {
   StageScope sc(p, MM_STAGE_SETUP, st);
   MM_CUDA(launch_setup_tables(p->desc.kernel, p->msp, p->Mr, N, p->fft.n, p->sp, p->tau, p->glx, p->glw, kGlNodes,
                               p->W, p->U, p->decon, p->fp64, st));
+  if (!p->fp64 && p->afft.npass > 0 && asset_twiddle_count(p->afft) <= p->atw_cap) {
+    p->launches += 1;
+    p->nl[MM_STAGE_SETUP] += 1;
+    MM_CUDA(launch_asset_twiddles(p->afft, p->atw, st));
+  }
   p->tab_N = N;
   return MM_OK;
 }
@@ -392,6 +484,11 @@ mm_status coeffs_impl(mm_plan p, const int64_t* off, const double* t, const doub
       else
         MM_CUDA(launch_spread_f32(off, p->rec_b0, p->rec_d, p->rec_v, p->sp, (float*)p->grid, p->status, st));
     }
+    if (p->use_afft) {
+      StageScope sc(p, MM_STAGE_FFT, st);
+      MM_CUDA(launch_fft_asset((const float*)p->grid, p->afft, D, p->W, p->atw, p->U, p->decon, coeffs, p->status,
+                               st));
+    } else {
     {
       StageScope sc(p, MM_STAGE_FFT_COLS, st);
       if (p->fp64) MM_CUDA(launch_fft_cols_f64((double*)p->grid, p->fft, D, p->W, p->status, st));
@@ -403,6 +500,7 @@ mm_status coeffs_impl(mm_plan p, const int64_t* off, const double* t, const doub
         MM_CUDA(launch_fft_rows_f64((const double*)p->grid, p->fft, D, p->W, p->U, p->decon, coeffs, p->status, st));
       else
         MM_CUDA(launch_fft_rows_f32((const float*)p->grid, p->fft, D, p->W, p->U, p->decon, coeffs, p->status, st));
+    }
     }
   }
   if (N_used) *N_used = N;
@@ -490,7 +588,8 @@ mm_status mm_plan_create(const mm_plan_desc* desc, mm_plan* out) {
   if (d.prec < MM_PREC_FP64 || d.prec > MM_PREC_MIXED_3XTF32) return MM_ERR_INVALID_ARG;
   if (d.spread_tile < 0 || d.spread_tile > 50000) return MM_ERR_INVALID_ARG;
   if (d.spread_algo < 0 || d.spread_algo > 3) return MM_ERR_INVALID_ARG;
-  for (int i = 0; i < 5; ++i)
+  if (d.fft_algo < 0 || d.fft_algo > 1) return MM_ERR_INVALID_ARG;
+  for (int i = 0; i < 4; ++i)
     if (d.reserved[i] != 0) return MM_ERR_INVALID_ARG;
   const int msp = msp_rule(d.kernel, d.tol);
   if (msp < 1 || msp > 30) return MM_ERR_UNSUPPORTED;
@@ -526,6 +625,10 @@ mm_status mm_plan_create(const mm_plan_desc* desc, mm_plan* out) {
   A(&p->rec_d, (size_t)std::max<int64_t>(d.max_events, 1) * p->rs);
   A(&p->rec_v, (size_t)std::max<int64_t>(d.max_events, 1) * p->rs);
   A(&p->W, (size_t)n * p->cs);
+  if (!p->fp64) {
+    p->atw_cap = 2 * n;  // sum_p m_p (R_p - 1) < n (1 + 1/R_1 + ...) < 2n
+    A(&p->atw, (size_t)p->atw_cap * p->cs);
+  }
   A(&p->U, Np1 * p->cs);
   A(&p->decon, Np1 * p->rs);
   A((void**)&p->glx, kGlNodes * sizeof(double));
@@ -661,29 +764,42 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
   cudaStream_t st = (cudaStream_t)stream;
   const bool prof = p->prof;
   p->prof = false;
-  struct Cand { int algo, tile, lgc, rb; };
+  struct Cand { int algo, tile, lgc, rb, fft, split, maxr; };
   std::vector<Cand> cands;
   const int tmax = spread_max_tile(p->fp64);
+  if (!p->fp64) {
+    for (int split : {1, 2})
+      for (int maxr : {16, 32}) {
+        for (int tile : {tmax / 4, tmax / 2, tmax}) cands.push_back({0, tile, -1, -1, 0, split, maxr});
+        for (int tile : {tmax / 2, tmax}) cands.push_back({1, tile, -1, -1, 0, split, maxr});
+      }
+  }
   for (int tile : {tmax / 4, tmax / 2, tmax})
     for (int lgc : {3, 4, 5})
-      for (int rb : {4, 8, 16}) cands.push_back({0, tile, lgc, rb});
-  for (int tile : {tmax / 2, tmax}) cands.push_back({1, tile, 4, 8});
+      for (int rb : {4, 8, 16}) cands.push_back({0, tile, lgc, rb, 1, -1, -1});
+  for (int tile : {tmax / 2, tmax}) cands.push_back({1, tile, 4, 8, 1, -1, -1});
   for (int lgc : {3, 4})
-    for (int rb : {4, 8}) cands.push_back({2, tmax, lgc, rb});
+    for (int rb : {4, 8}) cands.push_back({2, tmax, lgc, rb, 1, -1, -1});
   cudaEvent_t e0, e1;
   MM_CUDA(cudaEventCreate(&e0));
   MM_CUDA(cudaEventCreate(&e1));
   float best = 3.0e38f;
-  Cand bestc{-1, -1, -1, -1};
-  const Cand saved{p->tune_algo, p->tune_tile, p->tune_lgcols, p->tune_rowblk};
+  Cand bestc{-1, -1, -1, -1, -1, -1, -1};
+  const Cand saved{p->tune_algo, p->tune_tile, p->tune_lgcols, p->tune_rowblk, p->tune_fft, p->tune_split,
+                   p->tune_maxr};
   for (const Cand& c : cands) {
     p->tune_algo = c.algo;
     p->tune_tile = c.tile;
     p->tune_lgcols = c.lgc;
     p->tune_rowblk = c.rb;
+    p->tune_fft = c.fft;
+    p->tune_split = c.split;
+    p->tune_maxr = c.maxr;
     p->cfg_N = -1;  // force reconfiguration
+    p->tab_N = -1;
     if (configure(p, N) != MM_OK) continue;
     if (c.algo == 2 && !p->sp.fused) continue;  // fused variant does not fit
+    if (c.fft == 0 && (!p->use_afft || p->afft.split != c.split)) continue;  // not available
     // warm-up (also builds the tables for N)
     if (coeffs_impl(p, d_offsets, d_t, d_logp, N, t0, t1, d_coeffs, nullptr, st) != MM_OK) continue;
     cudaEventRecord(e0, st);
@@ -708,7 +824,11 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
     p->tune_tile = saved.tile;
     p->tune_lgcols = saved.lgc;
     p->tune_rowblk = saved.rb;
+    p->tune_fft = saved.fft;
+    p->tune_split = saved.split;
+    p->tune_maxr = saved.maxr;
     p->cfg_N = -1;
+    p->tab_N = -1;
     cudaGetLastError();
     return MM_ERR_CUDA;
   }
@@ -716,8 +836,12 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
   p->tune_tile = bestc.tile;
   p->tune_lgcols = bestc.lgc;
   p->tune_rowblk = bestc.rb;
+  p->tune_fft = bestc.fft;
+  p->tune_split = bestc.split;
+  p->tune_maxr = bestc.maxr;
   p->tune_ms = best;
   p->cfg_N = -1;
+  p->tab_N = -1;
   return configure(p, N);
 }
 
@@ -777,6 +901,10 @@ mm_status mm_plan_get_info(mm_plan p, mm_plan_info* info) {
   info->fft_lg_cols = p->fft.lg_cols;
   info->fft_rowblk = p->fft.rowblk;
   info->tuned_ms = p->tune_ms;
+  info->fft_algo = p->use_afft ? 0 : 1;
+  info->fft_passes = p->use_afft ? p->afft.npass : 0;
+  info->fft_split = p->use_afft ? p->afft.split : 0;
+  for (int q = 0; q < 4; ++q) info->fft_radix[q] = p->use_afft && q < p->afft.npass ? p->afft.rad[q] : 0;
   return MM_OK;
 }
 

@@ -24,7 +24,7 @@ enum : int {
 };
 
 template <typename T>
-struct Cplx {
+struct __align__(2 * sizeof(T)) Cplx {
   T x, y;
 };
 
@@ -93,6 +93,24 @@ struct FftParams {
   int N;             // cutoff
 };
 
+// Per-asset shared-memory FFT (mm_fft_asset.cu): an asset's n-point complex
+// transform is split over `split` CTAs (1 or 2), each transforming nl =
+// n / split points as nl = rad[0] * ... * rad[npass-1]; pass p works on
+// blocks of length rad[p] * stride[p]; its twiddle anchor rows (w^1..w^4 of
+// w = w_{L_p}^j, one row per j < stride[p]) start at row tw_off[p].
+constexpr int kMaxAssetPasses = 4;
+struct AssetFft {
+  int n;
+  int nl;
+  int split;
+  int N;
+  int npass;
+  int tw_rows;  // anchor rows over all passes
+  int rad[kMaxAssetPasses];
+  int stride[kMaxAssetPasses];
+  int tw_off[kMaxAssetPasses];
+};
+
 struct GramParams {
   int D;
   int N;             // modes k = 0..N
@@ -141,6 +159,12 @@ cudaError_t launch_coeff_fused(bool fp64, const int64_t* off, const double* t, c
                                const SpreadParams& sp, const FftParams& f, const void* W, const void* U,
                                const void* decon, void* coeffs, int* status, cudaStream_t s);
 size_t fft_cols_smem(const FftParams& f, bool fp64);
+bool asset_fft_radix_ok(int R);
+size_t asset_fft_smem(const AssetFft& f);
+int asset_fft_threads(int split);
+cudaError_t launch_asset_twiddles(const AssetFft& f, void* tw, cudaStream_t s);
+cudaError_t launch_fft_asset(const float* grid, const AssetFft& f, int D, const void* W, const void* tw,
+                             const void* U, const void* decon, void* coeffs, const int* status, cudaStream_t s);
 size_t fft_rows_smem(const FftParams& f, bool fp64);
 
 cudaError_t launch_gram_weights(int basis, int N, bool fp64, void* wsq, cudaStream_t s);

@@ -1,0 +1,388 @@
+// mm_fft_asset.cu -- stages (b) and (c) of the hot path for grids that fit in
+// shared memory: each asset's spread grid (Eq. (12)) is read once from global
+// memory (L2) into shared memory, transformed there by the length-M_r real FFT
+// of Eq. (13) taken as an n = M_r/2-point complex FFT, and its deconvolved,
+// truncated coefficients of Eq. (14) are written for k = 0..N.
+//
+// An asset is handled by S = 1 or 2 CTAs. With S = 2 the first radix-2 step of
+// the transform is done while loading: CTA c keeps the half-length sequence
+//   y_c[j] = (z[j] + (-1)^c z[j + n/2]) w_n^{c j},   j < n/2,
+// whose n/2-point DFT gives the even (c = 0) or odd (c = 1) outputs
+// Z_{2k'+c}. Both partners Z_k and Z_{n-k} of the real-input unpacking have
+// the parity of k, so each CTA finishes its half of the modes on its own, and
+// a workload of fewer assets than SMs still fills the GPU.
+//
+// The local transform of L = R_1 R_2 ... R_s points (every R_p <= 32) is an
+// in-place decimation-in-time FFT: the input is stored in mixed-radix
+// digit-reversed order, then pass p = s..1 (blocks of length L_p =
+// R_p m_p, stride m_p) multiplies each butterfly's points by the twiddles
+// w_{L_p}^{j r} as they are loaded, transforms them in registers with a fully
+// unrolled R_p-point DFT (a compile-time Cooley-Tukey split into 2-, 3-, 4-,
+// 5- and 8-point DFTs with its twiddles folded into immediates) and stores
+// them back in place; the output comes out in natural order. With
+// k = q_1 + R_1 (q_2 + R_2 (q_3 + ...)), input k goes to position
+// sum_p q_p m_p.
+#include <algorithm>
+#include <utility>
+
+#include "mm_common.cuh"
+#include "mm_fft_dev.cuh"
+
+namespace mmgpu {
+
+namespace {
+
+// ------------------------------------------------------------------------
+// cos and sin of 2 pi p / q for integers, evaluated at compile time in double
+// precision: the angle is reduced exactly to an eighth of a turn plus
+// x = pi s / (4 q) in [0, pi/4], then Taylor series (error < 1e-17).
+__host__ __device__ constexpr double ct_sin_series(double x) {
+  double x2 = x * x, term = x, sum = x;
+  for (int k = 1; k < 14; ++k) {
+    term *= -x2 / (double)((2 * k) * (2 * k + 1));
+    sum += term;
+  }
+  return sum;
+}
+__host__ __device__ constexpr double ct_cos_series(double x) {
+  double x2 = x * x, term = 1.0, sum = 1.0;
+  for (int k = 1; k < 14; ++k) {
+    term *= -x2 / (double)((2 * k - 1) * (2 * k));
+    sum += term;
+  }
+  return sum;
+}
+// which = 0: cos, 1: sin
+__host__ __device__ constexpr double ct_trig(long p, long q, int which) {
+  long r = p % q;
+  if (r < 0) r += q;
+  const long o = (8 * r) / q;       // octant
+  const long s = 8 * r - o * q;     // remainder, angle = o pi/4 + pi s/(4q)
+  const double x = kPi * (double)s / (4.0 * (double)q);
+  const double y = kPi * (double)(q - s) / (4.0 * (double)q);  // pi/4 - x
+  double c = 0, sn = 0;
+  switch (o) {
+    case 0: c = ct_cos_series(x); sn = ct_sin_series(x); break;
+    case 1: c = ct_sin_series(y); sn = ct_cos_series(y); break;
+    case 2: c = -ct_sin_series(x); sn = ct_cos_series(x); break;
+    case 3: c = -ct_cos_series(y); sn = ct_sin_series(y); break;
+    case 4: c = -ct_cos_series(x); sn = -ct_sin_series(x); break;
+    case 5: c = -ct_sin_series(y); sn = -ct_cos_series(y); break;
+    case 6: c = ct_sin_series(x); sn = -ct_cos_series(x); break;
+    default: c = ct_cos_series(y); sn = -ct_sin_series(y); break;
+  }
+  return which == 0 ? c : sn;
+}
+constexpr double ct_abs(double x) { return x < 0 ? -x : x; }
+static_assert(ct_abs(ct_trig(1, 6, 0) - 0.5) < 1e-15, "cos(pi/3)");
+static_assert(ct_abs(ct_trig(1, 4, 1) - 1.0) < 1e-15, "sin(pi/2)");
+static_assert(ct_abs(ct_trig(3, 8, 0) + 0.70710678118654752) < 1e-15, "cos(3pi/4)");
+static_assert(ct_abs(ct_trig(2, 5, 1) - 0.58778525229247313) < 1e-15, "sin(4pi/5)");
+
+template <int... I, typename F>
+__device__ __forceinline__ void static_for_impl(std::integer_sequence<int, I...>, F&& f) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(std::make_integer_sequence<int, N>{}, f);
+}
+
+// u * w_R^E with w_R = e^{-2 pi i / R}; trivial angles cost no multiply.
+template <int E, int R>
+__device__ __forceinline__ Cplx<float> twmul(Cplx<float> u) {
+  constexpr int e = ((E % R) + R) % R;
+  if constexpr (e == 0) {
+    return u;
+  } else if constexpr (4 * e == R) {
+    return Cplx<float>{u.y, -u.x};  // -i
+  } else if constexpr (2 * e == R) {
+    return Cplx<float>{-u.x, -u.y};
+  } else if constexpr (4 * e == 3 * R) {
+    return Cplx<float>{-u.y, u.x};  // +i
+  } else {
+    constexpr float c = (float)ct_trig(e, R, 0);
+    constexpr float s = (float)ct_trig(e, R, 1);
+    // (u.x + i u.y)(c - i s)
+    return Cplx<float>{fmaf(u.x, c, u.y * s), fmaf(u.y, c, -u.x * s)};
+  }
+}
+
+// Outer radix of the compile-time split R = A * (R / A).
+__host__ __device__ constexpr int outer_radix(int R) {
+  return (R % 8 == 0 && R > 8) ? 8 : (R % 5 == 0 && R > 5) ? 5 : (R % 4 == 0 && R > 4) ? 4 : (R % 3 == 0 && R > 3) ? 3 : 2;
+}
+
+// Forward R-point DFT in registers, natural order in and out.
+template <int R>
+struct Codelet {
+  static __device__ __forceinline__ void run(Cplx<float>* v) {
+    constexpr int A = outer_radix(R);
+    constexpr int B = R / A;
+    Cplx<float> t[R];
+    static_for<A>([&](auto ia) {
+      constexpr int a = decltype(ia)::value;
+      Cplx<float> u[B];
+#pragma unroll
+      for (int m = 0; m < B; ++m) u[m] = v[A * m + a];
+      Codelet<B>::run(u);
+      static_for<B>([&](auto ib) {
+        constexpr int b = decltype(ib)::value;
+        t[a * B + b] = twmul<a * b, R>(u[b]);
+      });
+    });
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      Cplx<float> w[A];
+#pragma unroll
+      for (int a = 0; a < A; ++a) w[a] = t[a * B + b];
+      Dft<float, A>::run(w);
+#pragma unroll
+      for (int c = 0; c < A; ++c) v[b + B * c] = w[c];
+    }
+  }
+};
+template <> struct Codelet<2> { static __device__ __forceinline__ void run(Cplx<float>* v) { Dft<float, 2>::run(v); } };
+template <> struct Codelet<3> { static __device__ __forceinline__ void run(Cplx<float>* v) { Dft<float, 3>::run(v); } };
+template <> struct Codelet<4> { static __device__ __forceinline__ void run(Cplx<float>* v) { Dft<float, 4>::run(v); } };
+template <> struct Codelet<5> { static __device__ __forceinline__ void run(Cplx<float>* v) { Dft<float, 5>::run(v); } };
+template <> struct Codelet<8> { static __device__ __forceinline__ void run(Cplx<float>* v) { Dft<float, 8>::run(v); } };
+
+// One decimation-in-time pass of radix R over L points in place. The
+// twiddles w^r (w = w_{L_p}^j), r = 1..R-1, are built from the four anchors
+// w, w^2, w^3, w^4 of row j (shared memory) as (w^4)^(r/4) w^(r mod 4): at
+// most R/4 + 1 rounded complex products per twiddle.
+template <int R>
+__device__ __forceinline__ void dit_pass(Cplx<float>* __restrict__ s, int L, int m, const float4* __restrict__ anc,
+                                         int nth) {
+  const int nbf = L / R;
+  const unsigned mm = magic_of((unsigned)m);
+  for (int i = threadIdx.x; i < nbf; i += nth) {
+    const int b = fast_div(i, m, mm);
+    const int j = i - b * m;
+    const int base = b * (R * m) + j;
+    Cplx<float> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = s[base + r * m];
+    if (m > 1) {
+      const float4 a01 = anc[2 * j], a23 = anc[2 * j + 1];
+      const Cplx<float> w1{a01.x, a01.y}, w2{a01.z, a01.w}, w3{a23.x, a23.y}, w4{a23.z, a23.w};
+      Cplx<float> pw = w4;  // (w^4)^(q4) for q4 >= 1
+#pragma unroll
+      for (int q4 = 0; 4 * q4 < R; ++q4) {
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+          const int r = 4 * q4 + rr;
+          if (r == 0 || r >= R) continue;
+          Cplx<float> t;
+          if (q4 == 0) t = rr == 1 ? w1 : (rr == 2 ? w2 : w3);
+          else if (rr == 0) t = pw;
+          else t = cmul(pw, rr == 1 ? w1 : (rr == 2 ? w2 : w3));
+          v[r] = cmul(v[r], t);
+        }
+        if (q4 >= 1) pw = cmul(pw, w4);
+      }
+    }
+    Codelet<R>::run(v);
+#pragma unroll
+    for (int q = 0; q < R; ++q) s[base + q * m] = v[q];
+  }
+}
+
+__device__ __forceinline__ void run_pass(int R, Cplx<float>* s, int L, int m, const float4* anc, int nth) {
+  switch (R) {
+    case 2: dit_pass<2>(s, L, m, anc, nth); break;
+    case 3: dit_pass<3>(s, L, m, anc, nth); break;
+    case 4: dit_pass<4>(s, L, m, anc, nth); break;
+    case 5: dit_pass<5>(s, L, m, anc, nth); break;
+    case 6: dit_pass<6>(s, L, m, anc, nth); break;
+    case 8: dit_pass<8>(s, L, m, anc, nth); break;
+    case 9: dit_pass<9>(s, L, m, anc, nth); break;
+    case 10: dit_pass<10>(s, L, m, anc, nth); break;
+    case 12: dit_pass<12>(s, L, m, anc, nth); break;
+    case 15: dit_pass<15>(s, L, m, anc, nth); break;
+    case 16: dit_pass<16>(s, L, m, anc, nth); break;
+    case 18: dit_pass<18>(s, L, m, anc, nth); break;
+    case 20: dit_pass<20>(s, L, m, anc, nth); break;
+    case 24: dit_pass<24>(s, L, m, anc, nth); break;
+    case 25: dit_pass<25>(s, L, m, anc, nth); break;
+    case 27: dit_pass<27>(s, L, m, anc, nth); break;
+    case 30: dit_pass<30>(s, L, m, anc, nth); break;
+    case 32: dit_pass<32>(s, L, m, anc, nth); break;
+    default: break;  // the host plans only the radices above
+  }
+}
+
+// Position of local input j in digit-reversed order.
+__device__ __forceinline__ int digit_rev(int j, const AssetFft& f, const unsigned* mr) {
+  int pos = 0;
+#pragma unroll
+  for (int p = 0; p < kMaxAssetPasses; ++p) {
+    if (p < f.npass) {
+      const int R = f.rad[p];
+      const int q = fast_div(j, R, mr[p]);
+      pos += (j - q * R) * f.stride[p];
+      j = q;
+    }
+  }
+  return pos;
+}
+
+// Byte offset of the anchor rows in shared memory: after the nl complex
+// points, rounded up to 16 bytes (nl may be odd) for the float4 accesses.
+__host__ __device__ __forceinline__ size_t anchor_offset(int nl) { return ((size_t)nl * 8 + 15) & ~(size_t)15; }
+
+constexpr int kLoadBatch = 8;     // global loads in flight per thread (split load)
+constexpr int kUnpackBatch = 8;   // table reads in flight per thread in the unpacking step
+
+template <int NTH>
+__global__ void __launch_bounds__(NTH, 512 / NTH)
+    k_fft_asset(const float* __restrict__ grid, AssetFft f, const Cplx<float>* __restrict__ W,
+                const Cplx<float>* __restrict__ tw, const Cplx<float>* __restrict__ U,
+                const float* __restrict__ decon, Cplx<float>* __restrict__ out, const int* __restrict__ gate) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (*gate) return;  // uniform: the whole block leaves
+  Cplx<float>* s = reinterpret_cast<Cplx<float>*>(smem_raw);
+  float4* anc = reinterpret_cast<float4*>(smem_raw + anchor_offset(f.nl));  // twiddle anchors, 32 B per row
+  {
+    // anchor rows: 16-byte asynchronous copies, waited for with the grid
+    const float4* src = reinterpret_cast<const float4*>(tw);
+    for (int i = threadIdx.x; i < 2 * f.tw_rows; i += NTH) {
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(anc + i);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src + i) : "memory");
+    }
+  }
+  const int c = blockIdx.x;  // which half of the modes (S = 2), else 0
+  const int a = blockIdx.y;
+  const int L = f.nl;
+  unsigned mr[kMaxAssetPasses];
+#pragma unroll
+  for (int p = 0; p < kMaxAssetPasses; ++p) mr[p] = magic_of((unsigned)f.rad[p]);
+
+  // load into digit-reversed order (with the first radix-2 step when S = 2)
+  const Cplx<float>* z = reinterpret_cast<const Cplx<float>*>(grid) + (size_t)a * f.n;
+  if (f.split == 1) {
+    // asynchronous 8-byte copies straight into their shared-memory slots:
+    // the whole grid row is in flight at once, no registers held
+    for (int j = threadIdx.x; j < L; j += NTH) {
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s + digit_rev(j, f, mr));
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(z + j) : "memory");
+    }
+  } else {
+    for (int j0 = threadIdx.x; j0 < L; j0 += NTH * kLoadBatch) {
+      Cplx<float> y[kLoadBatch], z1[kLoadBatch], w[kLoadBatch];
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int j = j0 + u * NTH;
+        if (j < L) {
+          y[u] = z[j];
+          z1[u] = z[j + L];
+          if (c) w[u] = W[j];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int j = j0 + u * NTH;
+        if (j < L) s[digit_rev(j, f, mr)] = c == 0 ? cadd(y[u], z1[u]) : cmul(csub(y[u], z1[u]), w[u]);
+      }
+    }
+  }
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+
+  for (int p = f.npass - 1; p >= 0; --p) {
+    run_pass(f.rad[p], s, L, f.stride[p], anc + 2 * f.tw_off[p], NTH);
+    __syncthreads();
+  }
+
+  // unpack the real-input transform and deconvolve (Eq. (14)):
+  // G(k) = (Z_k + conj Z_{n-k}) / 2 + w_{2n}^k (Z_k - conj Z_{n-k}) / (2i)
+  // U[k] = w_{2n}^k and the deconvolution factors are read kUnpackBatch at a
+  // time per thread
+  Cplx<float>* oa = out + (size_t)a * (f.N + 1);
+  const int S = f.split;
+  for (int k0 = c + S * (int)threadIdx.x; k0 <= f.N; k0 += S * NTH * kUnpackBatch) {
+    float dk[kUnpackBatch];
+    Cplx<float> Uk[kUnpackBatch];
+#pragma unroll
+    for (int u = 0; u < kUnpackBatch; ++u) {
+      const int k = k0 + u * S * NTH;
+      if (k <= f.N) {
+        dk[u] = __ldg(decon + k);
+        Uk[u] = U[k];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnpackBatch; ++u) {
+      const int k = k0 + u * S * NTH;
+      if (k <= f.N) {
+        const int mk = k == 0 ? 0 : f.n - k;  // n - k, same parity as k
+        const Cplx<float> Zk = s[(k - c) / S];
+        const Cplx<float> Zc = cconj(s[(mk - c) / S]);
+        const Cplx<float> E = {0.5f * (Zk.x + Zc.x), 0.5f * (Zk.y + Zc.y)};
+        const Cplx<float> dlt = csub(Zk, Zc);
+        const Cplx<float> O = {0.5f * dlt.y, -0.5f * dlt.x};  // (Z_k - conj Z_{n-k}) / (2i)
+        const Cplx<float> G = cadd(E, cmul(Uk[u], O));
+        oa[k] = Cplx<float>{G.x * dk[u], G.y * dk[u]};
+      }
+    }
+  }
+}
+
+// Twiddle anchors of each pass: row j < m_p holds w^1..w^4 of w = w_{L_p}^j,
+// from float64 angles.
+__global__ void k_asset_twiddles(AssetFft f, Cplx<float>* tw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int p = 0; p < f.npass; ++p) {
+    const int R = f.rad[p], m = f.stride[p];
+    if (m <= 1) continue;
+    if (i < 4 * m) {
+      const int j = i >> 2, e = (i & 3) + 1;
+      const long Lp = (long)R * m;
+      const long x = ((long)j * e) % Lp;
+      double sn, cs;
+      sincospi(-2.0 * (double)x / (double)Lp, &sn, &cs);
+      tw[4 * f.tw_off[p] + i] = Cplx<float>{(float)cs, (float)sn};
+    }
+  }
+}
+
+}  // namespace
+
+bool asset_fft_radix_ok(int R) {
+  switch (R) {
+    case 2: case 3: case 4: case 5: case 6: case 8: case 9: case 10: case 12: case 15:
+    case 16: case 18: case 20: case 24: case 25: case 27: case 30: case 32:
+      return true;
+    default:
+      return false;
+  }
+}
+
+size_t asset_fft_smem(const AssetFft& f) { return anchor_offset(f.nl) + (size_t)f.tw_rows * 32; }
+
+int asset_fft_threads(int split) { return split == 2 ? 256 : 512; }
+
+cudaError_t launch_asset_twiddles(const AssetFft& f, void* tw, cudaStream_t s) {
+  int cnt = 1;
+  for (int p = 0; p < f.npass; ++p) cnt = std::max(cnt, 4 * f.stride[p]);
+  k_asset_twiddles<<<(cnt + 255) / 256, 256, 0, s>>>(f, (Cplx<float>*)tw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fft_asset(const float* grid, const AssetFft& f, int D, const void* W, const void* tw,
+                             const void* U, const void* decon, void* coeffs, const int* status, cudaStream_t s) {
+  const size_t smem = asset_fft_smem(f);
+  dim3 grd(f.split, D);
+  auto go = [&](auto fn, int nth) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fn<<<grd, nth, smem, s>>>(grid, f, (const Cplx<float>*)W, (const Cplx<float>*)tw, (const Cplx<float>*)U,
+                              (const float*)decon, (Cplx<float>*)coeffs, status + 1);
+    return cudaGetLastError();
+  };
+  if (asset_fft_threads(f.split) == 256) return go(k_fft_asset<256>, 256);
+  return go(k_fft_asset<512>, 512);
+}
+
+}  // namespace mmgpu

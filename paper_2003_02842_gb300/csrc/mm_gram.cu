@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include "mm_async.cuh"
 #include "mm_common.cuh"
 
 namespace mmgpu {
@@ -115,41 +116,6 @@ cudaError_t launch_gram_f64(const void* coeffs, const GramParams& g, const doubl
 }
 
 // ------------------------------------------------------------ tcgen05 path
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint64_t globaltimer_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred P;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, P;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Wait for the phase with the given parity to complete; gives up after
-// limit_ns and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer_ns();
-  while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (globaltimer_ns() - t0 > limit_ns) return false;
-  }
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -201,7 +167,6 @@ constexpr int kTcThreads = 128;
 constexpr int kTile = 128;                 // rows per operand tile
 constexpr int kTileBytes = kTile * 128;    // 128-byte rows
 constexpr uint32_t kTmemCols = 128;
-constexpr uint64_t kWaitLimitNs = 1000000000ull;
 
 size_t gram_tc_smem(int, bool two_tiles) {
   return (size_t)2 /*stages*/ * (two_tiles ? 4 : 2) * kTileBytes + 1024 /*alignment slack*/;

@@ -191,18 +191,30 @@ __global__ void __launch_bounds__(256) k_prep(const int64_t* __restrict__ off, c
   __syncthreads();
   const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t ntot = off[D];
-  // asset of the block's first event (binary search once per block), then
-  // each thread walks forward to its own asset
+  // asset of the block's first event (a 32-ary search by warp 0, a couple of
+  // dependent loads), then each thread walks forward to its own asset
   __shared__ int s_a0;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
     const int64_t hb = min((int64_t)blockIdx.x * blockDim.x, ntot > 0 ? ntot - 1 : 0);
-    int lo = 0, hi = D;  // off[lo] <= hb < off[hi]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (off[mid] <= hb) lo = mid;
-      else hi = mid;
+    // first index in [1, D] with off[idx] > hb (D when none): the asset is idx - 1
+    const int lane = threadIdx.x;
+    int64_t lo = 1, hi = D;
+    for (int it = 0; it < 16 && hi > lo; ++it) {
+      const int64_t len = hi - lo;
+      const int64_t stride = (len + 31) / 32;
+      const int64_t o = (int64_t)lane * stride;
+      const bool below = o < len && off[lo + o] <= hb;
+      const int cnt = __popc(__ballot_sync(0xffffffffu, below));
+      if (cnt == 0) {
+        hi = lo;
+      } else {
+        const int64_t nlo = lo + (int64_t)(cnt - 1) * stride + 1;
+        const int64_t nhi = min(lo + (int64_t)cnt * stride, hi);
+        lo = min(nlo, nhi);
+        hi = nhi;
+      }
     }
-    s_a0 = lo;
+    if (lane == 0) s_a0 = (int)lo - 1;
   }
   __syncthreads();
   int flags = 0;

@@ -100,16 +100,34 @@ def test_many_tiles_and_periodic_halos(tile, prec, algo):
         assert np.all(rel_l2_rows(out["F"], ref) <= tl["coef"])
 
 
+@pytest.mark.parametrize("fft", ["default", "two_pass"])
 @pytest.mark.parametrize("algo", ["scatter", "gather"])
 @pytest.mark.parametrize("N", [1, 2, 7, 15, 64, 121, 1000])
-def test_cutoffs_small_and_non_smooth(N, algo):
+def test_cutoffs_small_and_non_smooth(N, algo, fft):
     ev = synth.random_events(11, D=3, n_range=(50, 400), T=2000.0)
+    ref = oracle.estimate(ev.offsets, ev.t, ev.logp, N=N, basis="fejer")
     for prec in ("fp64", "bf16x3"):
         tl = TOL[prec]
-        out = run(dict(tol=tl["tol"], kernel="es", basis="fejer", prec=prec, spread_algo=algo), ev, N)
-        ref = oracle.estimate(ev.offsets, ev.t, ev.logp, N=N, basis="fejer")
+        out = run(dict(tol=tl["tol"], kernel="es", basis="fejer", prec=prec, spread_algo=algo, fft_algo=fft), ev, N)
+        assert out["info"]["fft_algo"] == (0 if (prec != "fp64" and fft == "default") else 1)
         assert np.all(rel_l2_rows(out["F"], ref["F"]) <= tl["coef"])
         assert np.max(np.abs(out["R"].astype(np.float64) - ref["R"])) <= tl["R"]
+
+
+# cutoffs whose grids need different radix plans of the per-asset FFT: one
+# to four passes, odd and even last radices, the largest grid that fits in
+# shared memory (n = 28800, N = 14399)
+@pytest.mark.parametrize("N", [3, 14, 100, 365, 729, 2047, 5000, 10000, 14399])
+def test_per_asset_fft_radix_plans(N):
+    ev = synth.random_events(12, D=3, n_range=(200, 1500), T=28800.0, grid=28800)
+    tl = TOL["bf16x3"]
+    ref = oracle.coeffs_F(ev.offsets, ev.t, ev.logp, N)
+    for kernel in ("gauss", "kb", "es"):
+        out = run(dict(tol=tl["tol"], kernel=kernel, basis="dirichlet", prec="bf16x3"), ev, N)
+        info = out["info"]
+        assert info["fft_algo"] == 0 and info["fft_split"] == 2, info  # D = 3: two CTAs per asset
+        assert int(np.prod(info["fft_radix"])) * 2 * info["fft_split"] == info["Mr"]
+        assert np.all(rel_l2_rows(out["F"], ref) <= tl["coef"]), (kernel, info["fft_radix"])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3", "3xtf32"])
@@ -267,8 +285,68 @@ def test_profiling_counts_launches():
         mm.mm_estimate(plan, off, t, p, 500)
     prof = mm.mm_profile_read(plan)
     assert prof["prep"][1] == 6 and prof["prep"][0] > 0  # bounds + per-event prep
-    for stage in ("spread", "fft_cols", "fft_rows", "gram", "reduce"):
+    for stage in ("spread", "fft", "gram", "reduce"):
         assert prof[stage][1] == 3 and prof[stage][0] > 0
-    assert prof["fused"][1] == 0
+    assert prof["fused"][1] == 0 and prof["fft_cols"][1] == 0 and prof["fft_rows"][1] == 0
     assert prof["setup"][1] == 0  # tables are cached per cutoff
     mm.mm_destroy(plan)
+    # the two-pass FFT (and the FP64 path, which always uses it)
+    for kw in (dict(fft_algo="two_pass"), dict(prec="fp64", tol=1e-12)):
+        args = dict(D=2, N_max=500, max_events=ev.n_events, tol=1e-6, spread_algo="scatter")
+        args.update(kw)
+        plan = mm.mm_plan_create(**args)
+        mm.mm_estimate(plan, off, t, p, 500)
+        mm.mm_profile_enable(plan, True)
+        mm.mm_profile_read(plan, reset=True)
+        mm.mm_estimate(plan, off, t, p, 500)
+        prof = mm.mm_profile_read(plan)
+        assert prof["fft"][1] == 0 and prof["fft_cols"][1] == 1 and prof["fft_rows"][1] == 1
+        mm.mm_destroy(plan)
+
+
+def test_per_asset_fft_one_cta_per_asset():
+    # 160 assets (more than the SMs): one CTA transforms each whole grid
+    ev = synth.random_events(13, D=160, n_range=(2, 120), T=5000.0)
+    tl = TOL["bf16x3"]
+    for N in (50, 777):
+        out = run(dict(tol=tl["tol"], kernel="es", basis="dirichlet", prec="bf16x3"), ev, N)
+        assert out["info"]["fft_algo"] == 0 and out["info"]["fft_split"] == 1, out["info"]
+        ref = oracle.estimate(ev.offsets, ev.t, ev.logp, N=N)
+        assert np.all(rel_l2_rows(out["F"], ref["F"]) <= tl["coef"])
+        ok = np.diag(ref["Sigma"]) > 0
+        sub = np.ix_(ok, ok)
+        assert np.max(np.abs(out["R"].astype(np.float64)[sub] - ref["R"][sub])) <= tl["R"]
+
+
+def test_full_size_block_workload_sampled():
+    # the benchmarked workload at full size (D = 100, 766,162 events,
+    # N = 10^4, ES at 1e-6, BF16x3) in the autotuned launch configuration:
+    # coefficients of sampled assets and modes against the direct sum,
+    # Sigma of two assets against the oracle's, and R against the FP64 GPU
+    # path (itself checked against the oracle at smaller sizes above)
+    import paper_2003_02842_gb300 as mm
+    ev = synth.c3_block(0)
+    N = ev.meta["N"]
+    plan = mm.mm_plan_create(D=ev.D, N_max=N, max_events=ev.n_events, tol=1e-6, kernel="es", prec="bf16x3")
+    off, t, p = to_dev(ev)
+    mm.mm_autotune(plan, off, t, p, N, reps=2)
+    F, S, R, _ = mm.mm_estimate(plan, off, t, p, N)
+    assert mm.mm_plan_sync(plan) == 0
+    F = F.cpu().numpy()
+    rng = np.random.default_rng(5)
+    ks = np.unique(np.concatenate([[0, 1, N // 2, N], rng.integers(0, N + 1, 60)]))
+    for a in (0, 37, 99):
+        ref = oracle.coeffs_F(ev.offsets, ev.t, ev.logp, N, assets=[a], ks=ks)[0]
+        assert np.linalg.norm(F[a, ks] - ref) <= TOL["bf16x3"]["coef"] * np.linalg.norm(ref)
+    pair = [4, 57]
+    Fo = oracle.coeffs_F(ev.offsets, ev.t, ev.logp, N, assets=pair)
+    c = np.concatenate([np.conj(Fo[:, :0:-1]), Fo], axis=1) * (2 * np.pi)
+    So, _ = oracle.cov_from_coeffs(c, N, "dirichlet")
+    Sg = S.cpu().numpy().astype(np.float64)[np.ix_(pair, pair)]
+    assert sigma_err(Sg, So) <= TOL["bf16x3"]["sig"]
+    mm.mm_destroy(plan)
+    p64 = mm.mm_plan_create(D=ev.D, N_max=N, max_events=ev.n_events, tol=1e-12, kernel="es", prec="fp64")
+    _, _, R64, _ = mm.mm_estimate(p64, off, t, p, N)
+    assert mm.mm_plan_sync(p64) == 0
+    assert float((R.double() - R64).abs().max()) <= TOL["bf16x3"]["R"]
+    mm.mm_destroy(p64)
