@@ -244,6 +244,86 @@ const char* mm_status_string(mm_status s);
 /* Library version as major*10000 + minor*100 + patch. */
 int32_t mm_version(void);
 
+/* ------------------------------------------------------------------------
+ * Batched form: many independent problems of one shape (Monte Carlo
+ * replications of D assets), each with its own events and its own rescaling
+ * (Algorithm 4 per problem), and for each problem the covariance and
+ * correlation at every cutoff of an ascending list N_1 < ... < N_J (an
+ * Epps-effect sweep, Sec. 3.3), all from one set of coefficients at N_J:
+ * the sweep is a prefix-weighted contraction (segment sums of the per-mode
+ * products over (N_{j-1}, N_j], then prefix sums and the weights of
+ * Eq. (2) or (3) per cutoff), not J separate contractions.
+ *
+ * Events are CSR over all reps * D assets in problem-major order (asset i
+ * of problem r is entry r * D + i). Outputs are float32, layout
+ * [reps][J][D][D], row-major per matrix. The first call with a given set of
+ * inputs runs eagerly and captures the whole launch sequence (stages (a)-(c)
+ * for every problem and the sweep) into a CUDA graph; later calls with the
+ * same pointers and cutoffs replay it with a single graph launch.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t reps;          /* problems in the batch, >= 1 */
+  int32_t D;             /* assets per problem, 1 .. 12 */
+  int32_t N_max;         /* largest cutoff of any sweep, >= 1 */
+  int32_t reserved0;     /* must be zero */
+  int64_t max_events;    /* upper bound on the batch's total event count */
+  double tol;            /* NUFFT tolerance (Sec. 2.2.5) */
+  mm_kernel kernel;
+  mm_basis basis;
+  mm_precision prec;     /* MM_PREC_MIXED_*: stages (a)-(c) in float32; the sweep
+                            contraction accumulates in float32 on the CUDA cores
+                            (D <= 12 makes it memory-bound), normalised in float64 */
+  int32_t reserved[5];   /* must be zero */
+} mm_batch_desc;
+
+typedef struct mm_batch_s* mm_batch;
+
+typedef struct {
+  int64_t graph_launches;  /* calls served by one CUDA graph launch */
+  int64_t launches;        /* kernels launched by the batch (graph replays included) */
+  int64_t Mr;              /* oversampled grid size of the last call */
+  int32_t graph_captures;  /* graphs captured so far */
+  int32_t graph_kernels;   /* kernels in the captured graph */
+  int32_t spread_tile;
+  int32_t fft_algo;
+  int32_t fft_split;
+  int32_t fft_passes;
+  float tuned_ms;
+} mm_batch_info;
+
+/* Create a batch: validates desc and allocates the workspace of reps * D
+ * assets (grids, coefficients at N_max, tables) on the current device.
+ * MM_ERR_UNSUPPORTED for FP64 or D > 12. */
+mm_status mm_batch_create(const mm_batch_desc* desc, mm_batch* out);
+mm_status mm_batch_destroy(mm_batch batch);
+
+/* Sweep: h_cutoffs (host, n_cutoffs <= 128, strictly increasing, each in
+ * [0 or 1 (Fejer), N_max]); d_R and d_sigma_or_null receive
+ * reps * n_cutoffs * D * D floats. Asynchronous on stream (a change of
+ * cutoffs synchronises it once); device-side errors are reported by
+ * mm_batch_sync. */
+mm_status mm_batch_epps(mm_batch batch, const int64_t* d_offsets, const double* d_t, const double* d_logp,
+                        const int32_t* h_cutoffs, int32_t n_cutoffs, void* d_sigma_or_null, void* d_R,
+                        void* stream);
+
+/* mm_autotune for stages (a)-(c) on this batch's data at cutoff N; later
+ * sweeps re-capture their graph with the chosen configuration. */
+mm_status mm_batch_autotune(mm_batch batch, const int64_t* d_offsets, const double* d_t, const double* d_logp,
+                            int32_t N, int32_t reps, void* stream);
+
+/* Device pointer to the coefficients of the last sweep (complex64,
+ * [reps * D][*ld], F-convention, k = 0..N_J) and their row stride. Valid
+ * until the next call; owned by the batch. */
+mm_status mm_batch_coeffs(mm_batch batch, const void** d_coeffs, int32_t* ld);
+
+/* Copy those coefficients (reps * D * ld complex64) into d_dst on stream. */
+mm_status mm_batch_copy_coeffs(mm_batch batch, void* d_dst, void* stream);
+
+/* Synchronise the last call's stream and return its device status as
+ * mm_plan_sync does. */
+mm_status mm_batch_sync(mm_batch batch);
+mm_status mm_batch_get_info(mm_batch batch, mm_batch_info* info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,6 +23,8 @@ __all__ = [
     "MMError", "Plan", "mm_plan_create", "mm_destroy", "mm_coeffs", "mm_cov", "mm_corr", "mm_estimate",
     "mm_estimate_host", "mm_nyquist", "mm_plan_sync", "mm_plan_get_info", "mm_profile_enable",
     "mm_profile_read", "mm_status_string", "mm_version", "mm_corr_noalloc", "mm_autotune", "KERNELS", "BASES", "PRECISIONS", "STAGES",
+    "Batch", "mm_batch_create", "mm_batch_destroy", "mm_batch_epps", "mm_batch_autotune", "mm_batch_coeffs",
+    "mm_batch_sync", "mm_batch_get_info",
 ]
 
 
@@ -298,3 +300,91 @@ def mm_profile_read(plan, reset=False) -> dict:
     nl = (ctypes.c_int64 * len(STAGES))()
     _check(_lib.load().mm_profile_read(plan.handle, ms, nl, 1 if reset else 0), "mm_profile_read")
     return {s: (ms[i], nl[i]) for i, s in enumerate(STAGES)}
+
+
+# --------------------------------------------------------------------------
+# Batched form: replications x cutoff sweep (see include/mm.h)
+# --------------------------------------------------------------------------
+class Batch:
+    """Owns an mm_batch handle plus the description it was created from."""
+
+    def __init__(self, handle, desc: dict):
+        self.handle = handle
+        self.desc = desc
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                _lib.load().mm_batch_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def mm_batch_create(reps, D, N_max, max_events, tol=1e-6, kernel="es", basis="dirichlet", prec="bf16x3") -> Batch:
+    d = _lib.BatchDesc()
+    d.reps, d.D, d.N_max, d.max_events, d.tol = int(reps), int(D), int(N_max), int(max_events), float(tol)
+    d.kernel, d.basis, d.prec = KERNELS[kernel], BASES[basis], PRECISIONS[prec]
+    h = ctypes.c_void_p()
+    _check(_lib.load().mm_batch_create(ctypes.byref(d), ctypes.byref(h)), "mm_batch_create")
+    return Batch(h, dict(reps=int(reps), D=int(D), N_max=int(N_max), max_events=int(max_events), tol=float(tol),
+                         kernel=kernel, basis=basis, prec=prec))
+
+
+def mm_batch_destroy(batch: Batch):
+    if batch.handle:
+        _check(_lib.load().mm_batch_destroy(batch.handle), "mm_batch_destroy")
+        batch.handle = None
+
+
+def mm_batch_epps(batch, offsets, t, logp, cutoffs, sigma=True, R=None, stream=None):
+    """Covariance / correlation of every problem at every cutoff (ascending).
+    Returns (Sigma or None, R), each [reps, len(cutoffs), D, D] float32."""
+    torch = _torch()
+    reps, D = batch.desc["reps"], batch.desc["D"]
+    J = len(cutoffs)
+    cut = (ctypes.c_int32 * J)(*[int(x) for x in cutoffs])
+    dev = t.device
+    if R is None:
+        R = torch.empty((reps, J, D, D), dtype=torch.float32, device=dev)
+    if sigma is True:
+        S = torch.empty((reps, J, D, D), dtype=torch.float32, device=dev)
+    elif sigma is None or sigma is False:
+        S = None
+    else:
+        S = sigma
+    ps = _dptr(S, torch.float32, "sigma") if S is not None else ctypes.c_void_p(0)
+    po, pt, pp = _events(offsets, t, logp)
+    _check(_lib.load().mm_batch_epps(batch.handle, po, pt, pp, cut, J, ps, _dptr(R, torch.float32, "R"),
+                                     _stream(stream)), "mm_batch_epps")
+    return S, R
+
+
+def mm_batch_autotune(batch, offsets, t, logp, N, reps=3, stream=None) -> dict:
+    po, pt, pp = _events(offsets, t, logp)
+    _check(_lib.load().mm_batch_autotune(batch.handle, po, pt, pp, int(N), int(reps), _stream(stream)),
+           "mm_batch_autotune")
+    return mm_batch_get_info(batch)
+
+
+def mm_batch_coeffs(batch, stream=None):
+    """Copy of the last sweep's coefficients: complex64 [reps * D, N_J + 1]."""
+    torch = _torch()
+    ptr, ld = ctypes.c_void_p(), ctypes.c_int32()
+    _check(_lib.load().mm_batch_coeffs(batch.handle, ctypes.byref(ptr), ctypes.byref(ld)), "mm_batch_coeffs")
+    out = torch.empty((batch.desc["reps"] * batch.desc["D"], ld.value), dtype=torch.complex64, device="cuda")
+    _check(_lib.load().mm_batch_copy_coeffs(batch.handle, ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+           "mm_batch_copy_coeffs")
+    return out
+
+
+def mm_batch_sync(batch) -> int:
+    return int(_lib.load().mm_batch_sync(batch.handle))
+
+
+def mm_batch_get_info(batch) -> dict:
+    info = _lib.BatchInfo()
+    _check(_lib.load().mm_batch_get_info(batch.handle, ctypes.byref(info)), "mm_batch_get_info")
+    return {k: getattr(info, k) for k, _ in _lib.BatchInfo._fields_}
+

@@ -64,6 +64,36 @@ class PlanInfo(ctypes.Structure):
     ]
 
 
+class BatchDesc(ctypes.Structure):
+    _fields_ = [
+        ("reps", ctypes.c_int32),
+        ("D", ctypes.c_int32),
+        ("N_max", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("max_events", ctypes.c_int64),
+        ("tol", ctypes.c_double),
+        ("kernel", ctypes.c_int),
+        ("basis", ctypes.c_int),
+        ("prec", ctypes.c_int),
+        ("reserved", ctypes.c_int32 * 5),
+    ]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [
+        ("graph_launches", ctypes.c_int64),
+        ("launches", ctypes.c_int64),
+        ("Mr", ctypes.c_int64),
+        ("graph_captures", ctypes.c_int32),
+        ("graph_kernels", ctypes.c_int32),
+        ("spread_tile", ctypes.c_int32),
+        ("fft_algo", ctypes.c_int32),
+        ("fft_split", ctypes.c_int32),
+        ("fft_passes", ctypes.c_int32),
+        ("tuned_ms", ctypes.c_float),
+    ]
+
+
 _lib = None
 
 
@@ -96,6 +126,14 @@ def load():
         "mm_profile_read": ([p, p, p, i32], st),
         "mm_status_string": ([st], ctypes.c_char_p),
         "mm_version": ([], i32),
+        "mm_batch_create": ([ctypes.POINTER(BatchDesc), ctypes.POINTER(p)], st),
+        "mm_batch_destroy": ([p], st),
+        "mm_batch_epps": ([p, p, p, p, ctypes.POINTER(i32), i32, p, p, p], st),
+        "mm_batch_autotune": ([p, p, p, p, i32, i32, p], st),
+        "mm_batch_coeffs": ([p, ctypes.POINTER(p), ctypes.POINTER(i32)], st),
+        "mm_batch_copy_coeffs": ([p, p, p], st),
+        "mm_batch_sync": ([p], st),
+        "mm_batch_get_info": ([p, ctypes.POINTER(BatchInfo)], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)

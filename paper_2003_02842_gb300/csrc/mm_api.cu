@@ -165,6 +165,9 @@ struct mm_plan_s {
   size_t rs = 4;   // bytes per real grid cell / output element
   int msp = 0, klo = 0, khi = 0;
   int64_t n_max = 0;
+  int gsize = 0;                  // assets per problem (D for a single problem)
+  int G = 1;                      // problems (a batch has G > 1)
+  bool batch = false;             // created for a batch: no contraction or host-staging workspace
   // workspace
   void* grid = nullptr;
   int* rec_b0 = nullptr;          // per-event records of the prep kernel
@@ -177,7 +180,8 @@ struct mm_plan_s {
   void* decon = nullptr;
   double* glx = nullptr;
   double* glw = nullptr;
-  Rescale* bounds = nullptr;
+  Rescale* bounds = nullptr;       // one per problem
+  void* gscale = nullptr;          // per-problem cell scales (batched form)
   int* status = nullptr;  // [0] sticky flags, [1] gate, [2] Nyquist N
   unsigned long long* gapbits = nullptr;
   void* wsq = nullptr;
@@ -243,7 +247,7 @@ mm_status dalloc(mm_plan p, void** ptr, size_t bytes) {
 }
 
 void free_all(mm_plan p) {
-  void* ptrs[] = {p->grid, p->rec_b0, p->rec_d, p->rec_v, p->W, p->atw, p->U, p->decon, p->glx, p->glw, p->bounds, p->status, p->gapbits, p->wsq,
+  void* ptrs[] = {p->grid, p->rec_b0, p->rec_d, p->rec_v, p->W, p->atw, p->U, p->decon, p->glx, p->glw, p->bounds, p->gscale, p->status, p->gapbits, p->wsq,
                   p->partial, p->acc[0], p->acc[1], p->s_off, p->s_t, p->s_p, p->s_coef, p->s_sigma, p->s_R};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -353,7 +357,7 @@ mm_status configure(mm_plan p, int N) {
   const bool fits = fused_smem(f, Mr, p->fp64) + 2048 <= (size_t)p->smem_optin;
   int algo = p->desc.spread_algo == 2 ? 1 : (p->desc.spread_algo == 3 ? 2 : 0);
   if (p->tune_algo >= 0) algo = p->tune_algo;
-  if (algo == 2 && !fits) algo = 0;
+  if (algo == 2 && (!fits || p->G > 1)) algo = 0;
   s.algo = algo == 1 ? 1 : 0;
   s.fused = algo == 2 ? 1 : 0;
   s.tile = tile;
@@ -371,9 +375,15 @@ mm_status configure(mm_plan p, int N) {
   int split = p->desc.D < kSMs ? 2 : 1;  // fewer assets than SMs: two CTAs per asset
   if (p->tune_split == 1 || p->tune_split == 2) split = p->tune_split;
   const int maxr = p->tune_maxr == 16 ? 16 : 32;
-  if (!plan_asset_fft(n, split, N, maxr, &af) && split == 2) split = 1;
-  bool afft = !p->fp64 && plan_asset_fft(n, split, N, maxr, &af) &&
-              asset_fft_smem(af) + 2048 <= (size_t)p->smem_optin && asset_twiddle_count(af) <= p->atw_cap;
+  auto fits_split = [&](int sp_) {
+    return plan_asset_fft(n, sp_, N, maxr, &af) && asset_fft_smem(af) + 2048 <= (size_t)p->smem_optin &&
+           asset_twiddle_count(af) <= p->atw_cap;
+  };
+  bool afft = !p->fp64 && fits_split(split);
+  if (!p->fp64 && !afft && p->tune_split != 1 && p->tune_split != 2) {
+    split = 3 - split;  // the other split (a large grid fits in shared memory only as two halves)
+    afft = fits_split(split);
+  }
   int fft_algo = p->desc.fft_algo;
   if (p->tune_fft >= 0) fft_algo = p->tune_fft == 0 ? 0 : 1;
   if (fft_algo == 1) afft = false;
@@ -443,8 +453,9 @@ mm_status coeffs_impl(mm_plan p, const int64_t* off, const double* t, const doub
   p->last = st;
   {
     StageScope sc(p, MM_STAGE_PREP, st);
-    MM_CUDA(launch_bounds(off, t, D, p->desc.max_events, t0, t1, p->bounds, p->status, st));
+    MM_CUDA(launch_bounds(off, t, D, p->gsize, p->desc.max_events, t0, t1, p->bounds, p->status, st));
   }
+  if (N <= 0 && p->G > 1) return MM_ERR_CUTOFF;  // a batch sweeps given cutoffs
   if (N <= 0) {
     {
       StageScope sc(p, MM_STAGE_PREP, st, 2);
@@ -468,14 +479,19 @@ mm_status coeffs_impl(mm_plan p, const int64_t* off, const double* t, const doub
     MM_CUDA(launch_coeff_fused(p->fp64, off, t, logp, p->bounds, p->sp, p->fft, p->W, p->U, p->decon, coeffs,
                                p->status, st));
   } else {
+    const GroupScale* gsc = p->G > 1 ? (const GroupScale*)p->gscale : nullptr;
+    if (gsc) {
+      StageScope sc(p, MM_STAGE_PREP, st);
+      MM_CUDA(launch_group_scales(p->bounds, p->G, p->Mr, (GroupScale*)p->gscale, p->status, st));
+    }
     {
       StageScope sc(p, MM_STAGE_PREP, st);
       if (p->fp64)
-        MM_CUDA(launch_prep_f64(off, t, logp, p->bounds, D, p->Mr, p->desc.max_events, p->rec_b0, p->rec_d,
-                                p->rec_v, p->status, st));
+        MM_CUDA(launch_prep_f64(off, t, logp, p->bounds, gsc, p->gsize, D, p->Mr, p->desc.max_events, p->rec_b0,
+                                p->rec_d, p->rec_v, p->status, st));
       else
-        MM_CUDA(launch_prep_f32(off, t, logp, p->bounds, D, p->Mr, p->desc.max_events, p->rec_b0, p->rec_d,
-                                p->rec_v, p->status, st));
+        MM_CUDA(launch_prep_f32(off, t, logp, p->bounds, gsc, p->gsize, D, p->Mr, p->desc.max_events, p->rec_b0,
+                                p->rec_d, p->rec_v, p->status, st));
     }
     {
       StageScope sc(p, MM_STAGE_SPREAD, st);
@@ -508,6 +524,7 @@ mm_status coeffs_impl(mm_plan p, const int64_t* off, const double* t, const doub
 }
 
 mm_status corr_impl(mm_plan p, const void* coeffs, int N, void* sigma, void* R, cudaStream_t st) {
+  if (p->batch) return MM_ERR_UNSUPPORTED;
   if (N < 0 || N > p->desc.N_max) return MM_ERR_CUTOFF;
   if (p->desc.basis == MM_BASIS_FEJER && N < 1) return MM_ERR_CUTOFF;
   p->last = st;
@@ -576,11 +593,19 @@ const char* mm_status_string(mm_status s) {
   return "unknown status";
 }
 
-mm_status mm_plan_create(const mm_plan_desc* desc, mm_plan* out) {
+}  // extern "C"
+
+namespace {
+
+// Plan for D = G * gsize assets in G independent problems of gsize assets
+// each (G = 1: the single-problem plan of mm_plan_create). A batch plan
+// allocates no contraction or host-staging workspace.
+mm_status plan_create_impl(const mm_plan_desc* desc, int gsize, bool batch, mm_plan* out) {
   if (!out) return MM_ERR_INVALID_ARG;
   *out = nullptr;
   if (!desc) return MM_ERR_INVALID_ARG;
   const mm_plan_desc& d = *desc;
+  if (gsize < 1 || d.D % gsize) return MM_ERR_INVALID_ARG;
   if (d.D < 1 || d.N_max < 0 || d.max_events < 0) return MM_ERR_INVALID_ARG;
   if (!(d.tol > 0.0 && d.tol < 0.5)) return MM_ERR_INVALID_ARG;
   if (d.kernel < MM_KERNEL_GAUSS || d.kernel > MM_KERNEL_ES) return MM_ERR_INVALID_ARG;
@@ -596,6 +621,9 @@ mm_status mm_plan_create(const mm_plan_desc* desc, mm_plan* out) {
 
   mm_plan p = new mm_plan_s();
   p->desc = d;
+  p->gsize = gsize;
+  p->G = d.D / gsize;
+  p->batch = batch;
   p->fp64 = d.prec == MM_PREC_FP64;
   p->cs = p->fp64 ? 16 : 8;
   p->rs = p->fp64 ? 8 : 4;
@@ -633,11 +661,12 @@ mm_status mm_plan_create(const mm_plan_desc* desc, mm_plan* out) {
   A(&p->decon, Np1 * p->rs);
   A((void**)&p->glx, kGlNodes * sizeof(double));
   A((void**)&p->glw, kGlNodes * sizeof(double));
-  A((void**)&p->bounds, sizeof(Rescale));
+  A((void**)&p->bounds, (size_t)p->G * sizeof(Rescale));
+  if (p->G > 1) A(&p->gscale, (size_t)p->G * group_scale_bytes());
   A((void**)&p->status, 4 * sizeof(int));
   A((void**)&p->gapbits, sizeof(unsigned long long));
   A(&p->wsq, Np1 * p->rs);
-  {
+  if (!batch) {
     GramParams g = gram_params(p, d.N_max);
     size_t ctas = std::max<size_t>((size_t)kMaxGramCtas, (size_t)g.npairs);
     if (p->fp64) {
@@ -648,7 +677,7 @@ mm_status mm_plan_create(const mm_plan_desc* desc, mm_plan* out) {
       A((void**)&p->acc[1], D * (size_t)g.Dp * sizeof(float));
     }
   }
-  if (d.max_events > 0) {
+  if (d.max_events > 0 && !batch) {
     A((void**)&p->s_off, (D + 1) * sizeof(int64_t));
     A((void**)&p->s_t, (size_t)d.max_events * sizeof(double));
     A((void**)&p->s_p, (size_t)d.max_events * sizeof(double));
@@ -673,6 +702,18 @@ mm_status mm_plan_create(const mm_plan_desc* desc, mm_plan* out) {
   }
   *out = p;
   return MM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mm_status mm_plan_create(const mm_plan_desc* desc, mm_plan* out) {
+  if (!desc) {
+    if (out) *out = nullptr;
+    return MM_ERR_INVALID_ARG;
+  }
+  return plan_create_impl(desc, desc->D > 0 ? desc->D : 1, false, out);
 }
 
 mm_status mm_destroy(mm_plan p) {
@@ -854,7 +895,7 @@ mm_status mm_nyquist(mm_plan p, const int64_t* d_offsets, const double* d_t, dou
   p->last = st;
   {
     StageScope sc(p, MM_STAGE_PREP, st);
-    MM_CUDA(launch_bounds(d_offsets, d_t, p->desc.D, p->desc.max_events, t0, t1, p->bounds, p->status, st));
+    MM_CUDA(launch_bounds(d_offsets, d_t, p->desc.D, p->gsize, p->desc.max_events, t0, t1, p->bounds, p->status, st));
   }
   {
     StageScope sc(p, MM_STAGE_PREP, st, 2);
@@ -939,3 +980,222 @@ mm_status mm_profile_read(mm_plan p, double* ms, int64_t* launches, int32_t rese
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ batch
+struct mm_batch_s {
+  mm_batch_desc desc{};
+  mm_plan p = nullptr;
+  void* coef = nullptr;           // [reps * D][N + 1] complex64 of the last call
+  int ld = 0;
+  int* d_cut = nullptr;           // cutoffs of the captured sweep (device)
+  std::vector<int> cut;
+  cudaStream_t cap = nullptr;     // capture stream
+  cudaStream_t last = nullptr;    // caller's stream of the last call
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const void* key[5] = {};        // inputs and outputs the graph was captured with
+  int key_cfg = -1;               // plan configuration generation of the graph
+  int cfg_gen = 0;
+  int64_t graph_launches = 0;
+  int captures = 0;
+  int kernels = 0;
+};
+
+namespace {
+
+void batch_drop_graph(mm_batch b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+// Coefficients of every problem at the sweep's largest cutoff, then the
+// prefix-weighted sweep contraction, enqueued on st.
+mm_status batch_enqueue(mm_batch b, const int64_t* off, const double* t, const double* logp, int N, void* sigma,
+                        void* R, cudaStream_t st) {
+  mm_plan p = b->p;
+  mm_status r = coeffs_impl(p, off, t, logp, N, 0.0, 0.0, b->coef, nullptr, st);
+  if (r != MM_OK) return r;
+  StageScope sc(p, MM_STAGE_GRAM, st);
+  const int grid = std::max(1, std::min(p->G, 2 * kSMs));
+  MM_CUDA(launch_epps(b->desc.D, b->desc.basis == MM_BASIS_FEJER, b->coef, N + 1, b->d_cut, (int)b->cut.size(), p->G,
+                      (float*)sigma, (float*)R, p->status, grid, st));
+  return MM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mm_status mm_batch_create(const mm_batch_desc* desc, mm_batch* out) {
+  if (!out) return MM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!desc) return MM_ERR_INVALID_ARG;
+  const mm_batch_desc& d = *desc;
+  if (d.reps < 1 || d.D < 1 || d.N_max < 1 || d.max_events < 0 || d.reserved0 != 0) return MM_ERR_INVALID_ARG;
+  for (int i = 0; i < 5; ++i)
+    if (d.reserved[i] != 0) return MM_ERR_INVALID_ARG;
+  if (d.prec != MM_PREC_MIXED_BF16X3 && d.prec != MM_PREC_MIXED_3XTF32) return MM_ERR_UNSUPPORTED;
+  if (d.D > epps_max_assets()) return MM_ERR_UNSUPPORTED;
+  if ((int64_t)d.reps * d.D > (int64_t)1 << 30) return MM_ERR_UNSUPPORTED;
+  mm_plan_desc pd{};
+  pd.D = d.reps * d.D;
+  pd.N_max = d.N_max;
+  pd.max_events = d.max_events;
+  pd.tol = d.tol;
+  pd.kernel = d.kernel;
+  pd.basis = d.basis;
+  pd.prec = d.prec;
+  mm_batch b = new mm_batch_s();
+  b->desc = d;
+  mm_status r = plan_create_impl(&pd, d.D, true, &b->p);
+  if (r != MM_OK) {
+    delete b;
+    return r;
+  }
+  const size_t coef_bytes = (size_t)pd.D * ((size_t)d.N_max + 1) * 8;
+  if (dalloc(b->p, &b->coef, coef_bytes) != MM_OK || dalloc(b->p, (void**)&b->d_cut, kMaxCutoffs * sizeof(int)) != MM_OK ||
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    if (b->coef) cudaFree(b->coef);
+    if (b->d_cut) cudaFree(b->d_cut);
+    mm_destroy(b->p);
+    delete b;
+    cudaGetLastError();
+    return MM_ERR_OOM;
+  }
+  *out = b;
+  return MM_OK;
+}
+
+mm_status mm_batch_destroy(mm_batch b) {
+  if (!b) return MM_ERR_INVALID_ARG;
+  if (check_plan(b->p) == MM_OK) cudaDeviceSynchronize();
+  batch_drop_graph(b);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->coef) cudaFree(b->coef);
+  if (b->d_cut) cudaFree(b->d_cut);
+  mm_destroy(b->p);
+  delete b;
+  return MM_OK;
+}
+
+mm_status mm_batch_epps(mm_batch b, const int64_t* d_offsets, const double* d_t, const double* d_logp,
+                        const int32_t* h_cutoffs, int32_t n_cutoffs, void* d_sigma_or_null, void* d_R, void* stream) {
+  if (!b) return MM_ERR_INVALID_ARG;
+  mm_plan p = b->p;
+  mm_status r = check_plan(p);
+  if (r != MM_OK) return r;
+  if (!d_offsets || !d_t || !d_logp || !h_cutoffs || !d_R) return MM_ERR_INVALID_ARG;
+  if (n_cutoffs < 1 || n_cutoffs > kMaxCutoffs) return MM_ERR_INVALID_ARG;
+  const int lo = b->desc.basis == MM_BASIS_FEJER ? 1 : 0;
+  for (int j = 0; j < n_cutoffs; ++j) {
+    if (h_cutoffs[j] < lo || h_cutoffs[j] > b->desc.N_max) return MM_ERR_CUTOFF;
+    if (j > 0 && h_cutoffs[j] <= h_cutoffs[j - 1]) return MM_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = h_cutoffs[n_cutoffs - 1];
+  std::vector<int> cut(h_cutoffs, h_cutoffs + n_cutoffs);
+  const bool new_cut = cut != b->cut;
+  if (new_cut) {
+    MM_CUDA(cudaStreamSynchronize(st));  // the previous sweep may still read the old cutoffs
+    MM_CUDA(cudaMemcpy(b->d_cut, cut.data(), cut.size() * sizeof(int), cudaMemcpyHostToDevice));
+    b->cut = cut;
+  }
+  const void* key[5] = {d_offsets, d_t, d_logp, d_sigma_or_null, d_R};
+  bool same = b->exec && !new_cut && b->key_cfg == b->cfg_gen && b->ld == N + 1;
+  for (int i = 0; i < 5 && same; ++i) same = key[i] == b->key[i];
+  b->last = st;
+  if (same) {
+    MM_CUDA(cudaGraphLaunch(b->exec, st));
+    b->graph_launches += 1;
+    p->launches += b->kernels;
+    return MM_OK;
+  }
+  // first call with these inputs: run eagerly (this call's result; it also
+  // builds the per-cutoff tables), then capture the same launches into a
+  // graph that later calls replay with one launch
+  batch_drop_graph(b);
+  b->ld = N + 1;
+  r = batch_enqueue(b, d_offsets, d_t, d_logp, N, d_sigma_or_null, d_R, st);
+  if (r != MM_OK) return r;
+  const bool prof = p->prof;
+  p->prof = false;
+  const int64_t l0 = p->launches;
+  MM_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
+  r = batch_enqueue(b, d_offsets, d_t, d_logp, N, d_sigma_or_null, d_R, b->cap);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(b->cap, &g);
+  p->prof = prof;
+  p->last = st;
+  b->kernels = (int)(p->launches - l0);
+  p->launches = l0;
+  if (r != MM_OK || ce != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return r != MM_OK ? r : MM_ERR_CUDA;
+  }
+  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    b->exec = nullptr;
+    cudaGetLastError();
+    return MM_ERR_CUDA;
+  }
+  b->graph = g;
+  for (int i = 0; i < 5; ++i) b->key[i] = key[i];
+  b->key_cfg = b->cfg_gen;
+  b->captures += 1;
+  return MM_OK;
+}
+
+mm_status mm_batch_autotune(mm_batch b, const int64_t* d_offsets, const double* d_t, const double* d_logp,
+                            int32_t N, int32_t reps, void* stream) {
+  if (!b) return MM_ERR_INVALID_ARG;
+  if (N < 1 || N > b->desc.N_max) return MM_ERR_CUTOFF;
+  mm_status r = mm_autotune(b->p, d_offsets, d_t, d_logp, N, 0.0, 0.0, b->coef, reps, stream);
+  b->cfg_gen += 1;  // a captured graph holds the old configuration
+  return r;
+}
+
+mm_status mm_batch_coeffs(mm_batch b, const void** d_coeffs, int32_t* ld) {
+  if (!b || !d_coeffs || !ld) return MM_ERR_INVALID_ARG;
+  *d_coeffs = b->coef;
+  *ld = b->ld;
+  return MM_OK;
+}
+
+mm_status mm_batch_copy_coeffs(mm_batch b, void* d_dst, void* stream) {
+  if (!b || !d_dst) return MM_ERR_INVALID_ARG;
+  mm_status r = check_plan(b->p);
+  if (r != MM_OK) return r;
+  MM_CUDA(cudaMemcpyAsync(d_dst, b->coef, (size_t)b->p->desc.D * b->ld * 8, cudaMemcpyDeviceToDevice,
+                          (cudaStream_t)stream));
+  return MM_OK;
+}
+
+mm_status mm_batch_sync(mm_batch b) {
+  if (!b) return MM_ERR_INVALID_ARG;
+  b->p->last = b->last;
+  return mm_plan_sync(b->p);
+}
+
+mm_status mm_batch_get_info(mm_batch b, mm_batch_info* info) {
+  if (!b || !info) return MM_ERR_INVALID_ARG;
+  memset(info, 0, sizeof(*info));
+  mm_plan_info pi;
+  mm_plan_get_info(b->p, &pi);
+  info->graph_launches = b->graph_launches;
+  info->graph_captures = b->captures;
+  info->graph_kernels = b->kernels;
+  info->launches = pi.launches;
+  info->Mr = pi.Mr;
+  info->spread_tile = pi.spread_tile;
+  info->fft_algo = pi.fft_algo;
+  info->fft_split = pi.fft_split;
+  info->fft_passes = pi.fft_passes;
+  info->tuned_ms = pi.tuned_ms;
+  return MM_OK;
+}
+
+}  // extern "C"
+

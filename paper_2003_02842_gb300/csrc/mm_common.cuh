@@ -125,18 +125,27 @@ struct GramParams {
   int Dp;            // row stride of the FP32 accumulator (D rounded up to 4)
 };
 
+struct GroupScale;  // per-problem fixed-point scales (mm_spread_dev.cuh)
+
+// Batched cutoff sweep (mm_epps.cu).
+constexpr int kMaxCutoffs = 128;
+constexpr int kMaxEppsAssets = 12;
+
 // ---------------------------------------------------------------- launchers
 // Each returns cudaGetLastError() of its launch.
-cudaError_t launch_bounds(const int64_t* off, const double* t, int D, int64_t max_events,
+cudaError_t launch_bounds(const int64_t* off, const double* t, int D, int gsize, int64_t max_events,
                           double w0, double w1, Rescale* rs, int* status, cudaStream_t s);
+cudaError_t launch_group_scales(const Rescale* rs, int G, int64_t Mr, GroupScale* out, const int* status,
+                                cudaStream_t s);
+size_t group_scale_bytes();
 cudaError_t launch_min_gap(const int64_t* off, const double* t, int D, const Rescale* rs,
                            unsigned long long* gapbits, int* nyq, int* status, cudaStream_t s);
-cudaError_t launch_prep_f32(const int64_t* off, const double* t, const double* logp, const Rescale* rs, int D,
-                            int64_t Mr, int64_t max_events, int* rb0, void* rd, void* rv, int* status,
-                            cudaStream_t s);
-cudaError_t launch_prep_f64(const int64_t* off, const double* t, const double* logp, const Rescale* rs, int D,
-                            int64_t Mr, int64_t max_events, int* rb0, void* rd, void* rv, int* status,
-                            cudaStream_t s);
+cudaError_t launch_prep_f32(const int64_t* off, const double* t, const double* logp, const Rescale* rs,
+                            const GroupScale* gsc, int gsize, int D, int64_t Mr, int64_t max_events, int* rb0,
+                            void* rd, void* rv, int* status, cudaStream_t s);
+cudaError_t launch_prep_f64(const int64_t* off, const double* t, const double* logp, const Rescale* rs,
+                            const GroupScale* gsc, int gsize, int D, int64_t Mr, int64_t max_events, int* rb0,
+                            void* rd, void* rv, int* status, cudaStream_t s);
 cudaError_t launch_spread_f32(const int64_t* off, const int* rb0, const void* rd, const void* rv,
                               const SpreadParams& p, float* grid, const int* status, cudaStream_t s);
 cudaError_t launch_spread_f64(const int64_t* off, const int* rb0, const void* rd, const void* rv,
@@ -177,5 +186,8 @@ cudaError_t launch_corr_acc(const float* acc, const GramParams& g, float* sigma,
 cudaError_t launch_reduce_corr(bool fp64, const void* partial, const GramParams& g,
                                void* sigma, void* R, int* status, cudaStream_t s);
 size_t gram_tc_smem(int mode, bool two_tiles);
+int epps_max_assets();
+cudaError_t launch_epps(int Dg, bool fejer, const void* coef, int ld, const int* cut, int ncut, int G, float* sigma,
+                        float* R, int* status, int grid, cudaStream_t s);
 
 }  // namespace mmgpu

@@ -31,29 +31,36 @@
 namespace mmgpu {
 
 // ------------------------------------------------------------------ bounds
-// Validates the CSR offsets, finds t_min / t_max over all assets (Algorithm
-// 4) or takes the caller's window, fixes the time fixed-point format and
-// writes the per-call gate word (0 = proceed). One block.
-__global__ void k_bounds(const int64_t* __restrict__ off, const double* __restrict__ t, int D,
+// Validates the CSR offsets, finds t_min / t_max (Algorithm 4) or takes the
+// caller's window, fixes the time fixed-point format and writes the gate word
+// (0 = proceed). Block g handles problem g of a batch (assets g*gsize ..
+// (g+1)*gsize - 1; a single problem has one block with gsize = D). A block
+// reads event times only after checking that its own offsets are
+// non-decreasing and lie in [0, max_events], so a malformed offsets array
+// anywhere leaves every read in bounds.
+__global__ void k_bounds(const int64_t* __restrict__ off, const double* __restrict__ t, int D, int gsize,
                          int64_t max_events, double w0, double w1, Rescale* rs, int* status) {
   __shared__ double s_lo[256], s_hi[256];
   __shared__ int s_bad;
   int* gate = status + 1;
+  const int g = blockIdx.x;
+  const int i0 = g * gsize, i1 = min(i0 + gsize, D);
   if (threadIdx.x == 0) s_bad = 0;
   __syncthreads();
   // 1) the offsets alone: non-decreasing from 0 up to at most max_events.
   //    Only when all of them hold is any event time read.
   int bad = 0;
-  for (int i = threadIdx.x; i < D; i += blockDim.x)
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x)
     if (off[i + 1] < off[i]) bad = 1;
-  if (threadIdx.x == 0 && (off[0] != 0 || off[D] > max_events)) bad = 1;
+  if (threadIdx.x == 0 && (off[i0] < 0 || off[i1] > max_events || (g == 0 && off[0] != 0))) bad = 1;
   if (bad) atomicOr(&s_bad, 1);
   __syncthreads();
   if (s_bad) {
     if (threadIdx.x == 0) {
       atomicOr(status, ST_BAD_OFFSETS);
-      rs->t0 = rs->t1 = 0.0;
-      *gate = 1;
+      rs[g].t0 = rs[g].t1 = 0.0;
+      if (gridDim.x == 1) *gate = 1;
+      else atomicOr(gate, 1);
     }
     return;
   }
@@ -61,7 +68,7 @@ __global__ void k_bounds(const int64_t* __restrict__ off, const double* __restri
   const bool window = w1 > w0;
   double lo = INFINITY, hi = -INFINITY;
   int outwin = 0;
-  for (int i = threadIdx.x; i < D; i += blockDim.x) {
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const int64_t a = off[i], b = off[i + 1];
     if (b > a) {
       const double f = t[a], l = t[b - 1];
@@ -84,30 +91,58 @@ __global__ void k_bounds(const int64_t* __restrict__ off, const double* __restri
   if (threadIdx.x == 0) {
     const double t0 = window ? w0 : s_lo[0];
     const double t1 = window ? w1 : s_hi[0];
-    int g = 0;
-    if (s_bad & 2) { atomicOr(status, ST_OUT_OF_WINDOW); g = 1; }
-    if (!g && !(t1 > t0 && isfinite(t0) && isfinite(t1))) {
+    int gt = 0;
+    if (s_bad & 2) { atomicOr(status, ST_OUT_OF_WINDOW); gt = 1; }
+    if (!gt && !(t1 > t0 && isfinite(t0) && isfinite(t1))) {
       // all assets empty, a single instant, or non-finite times
       if (s_hi[0] >= s_lo[0] || window || isnan(s_lo[0]) || isnan(s_hi[0])) atomicOr(status, ST_SPAN);
-      g = 1;
+      gt = 1;
     }
     Rescale r{};
     r.t0 = t0;
     r.t1 = t1;
-    if (!g) {
+    if (!gt) {
       int ex;
       frexp(fmax(fabs(t0), fabs(t1)), &ex);  // max |t| < 2^ex
       r.F = 62 - (ex + 1);                   // |t_fix| < 2^61
       r.t0_fix = to_fix(t0, r.F);
     }
-    *rs = r;
-    *gate = g;
+    rs[g] = r;
+    if (gridDim.x == 1) *gate = gt;  // one problem: this call's gate
+    else if (gt) atomicOr(gate, 1);  // batched: cleared before the launch
   }
 }
 
-cudaError_t launch_bounds(const int64_t* off, const double* t, int D, int64_t max_events, double w0,
+cudaError_t launch_bounds(const int64_t* off, const double* t, int D, int gsize, int64_t max_events, double w0,
                           double w1, Rescale* rs, int* status, cudaStream_t s) {
-  k_bounds<<<1, 256, 0, s>>>(off, t, D, max_events, w0, w1, rs, status);
+  const int G = (D + gsize - 1) / gsize;
+  if (G > 1) {
+    cudaError_t e = cudaMemsetAsync(status + 1, 0, sizeof(int), s);  // the gate of this call
+    if (e != cudaSuccess) return e;
+  }
+  k_bounds<<<G, 256, 0, s>>>(off, t, D, gsize, max_events, w0, w1, rs, status);
+  return cudaGetLastError();
+}
+
+// Per-problem fixed-point cell scales for the grid size of this call.
+__global__ void k_group_scales(const Rescale* __restrict__ rs, int G, int64_t Mr, const int* __restrict__ gate,
+                               GroupScale* out) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G || *gate) return;
+  const Rescale r = rs[g];
+  GroupScale q;
+  q.us = make_uscale(r, Mr);
+  q.usf = make_uscale_f(r, Mr);
+  q.t0_fix = r.t0_fix;
+  q.F = r.F;
+  out[g] = q;
+}
+
+size_t group_scale_bytes() { return sizeof(GroupScale); }
+
+cudaError_t launch_group_scales(const Rescale* rs, int G, int64_t Mr, GroupScale* out, const int* status,
+                                cudaStream_t s) {
+  k_group_scales<<<(G + 127) / 128, 128, 0, s>>>(rs, G, Mr, status + 1, out);
   return cudaGetLastError();
 }
 
@@ -175,6 +210,7 @@ constexpr int kNoCell = -0x40000000;  // cell of a skipped event (outside every 
 template <typename T>
 __global__ void __launch_bounds__(256) k_prep(const int64_t* __restrict__ off, const double* __restrict__ t,
                                               const double* __restrict__ logp, const Rescale* __restrict__ rsp,
+                                              const GroupScale* __restrict__ gsc, int gsize,
                                               const int* __restrict__ gate, int D, int64_t Mr, int* __restrict__ rb0,
                                               T* __restrict__ rd, T* __restrict__ rv, int* status) {
   __shared__ UScale s_us;
@@ -183,9 +219,11 @@ __global__ void __launch_bounds__(256) k_prep(const int64_t* __restrict__ off, c
   __shared__ int s_flags;
   if (*gate) return;  // uniform
   if (threadIdx.x == 0) {
-    s_rs = *rsp;
-    if (sizeof(T) == 8) s_us = make_uscale(s_rs, Mr);
-    else s_usf = make_uscale_f(s_rs, Mr);
+    if (!gsc) {
+      s_rs = *rsp;
+      if (sizeof(T) == 8) s_us = make_uscale(s_rs, Mr);
+      else s_usf = make_uscale_f(s_rs, Mr);
+    }
     s_flags = 0;
   }
   __syncthreads();
@@ -222,7 +260,18 @@ __global__ void __launch_bounds__(256) k_prep(const int64_t* __restrict__ off, c
     int lo = s_a0;
     while (lo + 1 < D && off[lo + 1] <= h) ++lo;
     if (h + 1 < off[lo + 1]) {
-      const Rescale rs = s_rs;
+      // this event's problem: its fixed-point scale (batched form) or the
+      // call's single one
+      Rescale rs = s_rs;
+      UScale us = s_us;
+      UScaleF usf = s_usf;
+      if (gsc) {
+        const GroupScale q = gsc[lo / gsize];
+        rs.t0_fix = q.t0_fix;
+        rs.F = q.F;
+        us = q.us;
+        usf = q.usf;
+      }
       const double th = t[h], tn = t[h + 1];
       const double p0 = logp[h], p1 = logp[h + 1];
       const long long kh = order_key(th), kn = order_key(tn);
@@ -236,12 +285,12 @@ __global__ void __launch_bounds__(256) k_prep(const int64_t* __restrict__ off, c
         int cb;
         T cd;
         if (sizeof(T) == 8) {
-          const unsigned long long uf = u_fix_of(th, rs.t0_fix, rs.F, s_us);
+          const unsigned long long uf = u_fix_of(th, rs.t0_fix, rs.F, us);
           cb = (int)(uf >> kUFrac);
           cd = frac_to<T>(uf & ((1ull << kUFrac) - 1));
         } else {
           float fd;
-          cell_f32(dt, s_usf, cb, fd);
+          cell_f32(dt, usf, cb, fd);
           cd = (T)fd;
         }
         if (dt < 0 || cb > Mr || (cb == Mr && cd > (T)0)) {
@@ -264,23 +313,26 @@ __global__ void __launch_bounds__(256) k_prep(const int64_t* __restrict__ off, c
 
 template <typename T>
 static cudaError_t launch_prep_t(const int64_t* off, const double* t, const double* logp, const Rescale* rs,
-                                 int D, int64_t Mr, int64_t max_events, int* rb0, T* rd, T* rv, int* status,
-                                 cudaStream_t s) {
+                                 const GroupScale* gsc, int gsize, int D, int64_t Mr, int64_t max_events, int* rb0,
+                                 T* rd, T* rv, int* status, cudaStream_t s) {
   if (max_events <= 0) return cudaSuccess;
   const int64_t blocks = (max_events + 255) / 256;
-  k_prep<T><<<(unsigned)blocks, 256, 0, s>>>(off, t, logp, rs, status + 1, D, Mr, rb0, rd, rv, status);
+  k_prep<T><<<(unsigned)blocks, 256, 0, s>>>(off, t, logp, rs, gsc, gsize, status + 1, D, Mr, rb0, rd, rv, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_prep_f32(const int64_t* off, const double* t, const double* logp, const Rescale* rs, int D,
+cudaError_t launch_prep_f32(const int64_t* off, const double* t, const double* logp, const Rescale* rs,
+                            const GroupScale* gsc, int gsize, int D,
                             int64_t Mr, int64_t max_events, int* rb0, void* rd, void* rv, int* status,
                             cudaStream_t s) {
-  return launch_prep_t<float>(off, t, logp, rs, D, Mr, max_events, rb0, (float*)rd, (float*)rv, status, s);
+  return launch_prep_t<float>(off, t, logp, rs, gsc, gsize, D, Mr, max_events, rb0, (float*)rd, (float*)rv, status, s);
 }
-cudaError_t launch_prep_f64(const int64_t* off, const double* t, const double* logp, const Rescale* rs, int D,
+cudaError_t launch_prep_f64(const int64_t* off, const double* t, const double* logp, const Rescale* rs,
+                            const GroupScale* gsc, int gsize, int D,
                             int64_t Mr, int64_t max_events, int* rb0, void* rd, void* rv, int* status,
                             cudaStream_t s) {
-  return launch_prep_t<double>(off, t, logp, rs, D, Mr, max_events, rb0, (double*)rd, (double*)rv, status, s);
+  return launch_prep_t<double>(off, t, logp, rs, gsc, gsize, D, Mr, max_events, rb0, (double*)rd, (double*)rv, status,
+                               s);
 }
 
 // ------------------------------------------------------------------ spread

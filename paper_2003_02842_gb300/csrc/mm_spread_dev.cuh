@@ -119,6 +119,14 @@ __device__ __forceinline__ void cell_f32(long long dt, const UScaleF& us, int& b
   d = r;
 }
 
+// Fixed-point time format and cell scales of one problem of a batch.
+struct GroupScale {
+  UScale us;
+  UScaleF usf;
+  long long t0_fix;
+  int F;
+};
+
 // Exact split of a float64 into float32 hi + lo (hi = x truncated to 24
 // significant bits, lo = the remaining 29 bits rounded to 24), by bit
 // operations; hi_a - hi_b is exact for nearby values (Sterbenz), so a return

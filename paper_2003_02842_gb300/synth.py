@@ -189,6 +189,60 @@ def batch_replications(seed, reps, D=10, T=28800.0, rho=0.35, sig2_range=(0.1, 0
     return out
 
 
+def c4_batch(seed=0, reps=4096, D=10, T=28800, rho=0.35, sig2_range=(0.1, 0.2), median_n=2000, sdlog=1.0,
+             clip=(100, 50000), mu=0.01, s0=100.0):
+    """Batched Monte Carlo workload: `reps` replications of D equicorrelated
+    GBM assets (pairwise rho, sigma^2 ~ U(sig2_range)) observed on the 1-s
+    grid over T seconds. Per-asset event counts are lognormal (median
+    median_n, log-sd sdlog) clipped to `clip` and then to the T grid
+    seconds; an asset observes each second independently with probability
+    count / T (so its count is Binomial around the drawn value). Log-prices
+    are exact in law at the observed seconds (one common Brownian factor
+    plus one per asset). Returns one CSR Events over reps * D assets in
+    replication-major order, plus meta with the per-replication Nyquist
+    cutoff floor(span / 2) (unit gaps)."""
+    rng = rng_for(4, seed)
+    ts, ps = [], []
+    nyq = np.empty(reps, dtype=np.int64)
+    a_c, a_i = np.sqrt(rho), np.sqrt(1.0 - rho)
+    for r in range(reps):
+        sig2 = rng.uniform(*sig2_range, size=D)
+        n = np.clip(np.round(np.exp(np.log(median_n) + sdlog * rng.standard_normal(D))), clip[0], clip[1])
+        n = np.minimum(n, T)
+        keep = rng.random((D, T)) < (n / T)[:, None]
+        keep[:, 0] |= ~keep.any(axis=1)  # every asset keeps at least one second
+        union = keep.any(axis=0)
+        sec = np.flatnonzero(union)
+        dtd = np.diff(sec, prepend=0).astype(np.float64) / SECONDS_PER_DAY
+        G = np.cumsum(rng.standard_normal(len(sec)) * np.sqrt(dtd))
+        gpos = np.full(T, -1, dtype=np.int64)
+        gpos[sec] = np.arange(len(sec))
+        lo, hi = T, 0
+        for i in range(D):
+            si = np.flatnonzero(keep[i])
+            di = si.astype(np.float64) / SECONDS_PER_DAY
+            E = np.cumsum(rng.standard_normal(len(si)) * np.sqrt(np.diff(di, prepend=0.0)))
+            W = a_c * G[gpos[si]] + a_i * E
+            ps.append(np.log(s0) + (mu - 0.5 * sig2[i]) * di + np.sqrt(sig2[i]) * W)
+            ts.append(si.astype(np.float64))
+            lo, hi = min(lo, int(si[0])), max(hi, int(si[-1]))
+        nyq[r] = (hi - lo) // 2
+    ev = from_lists(ts, ps)
+    ev.meta = {"workload": f"c4_batch_gbm_R{reps}_D{D}", "reps": reps, "D": D, "nyquist": nyq}
+    return ev
+
+
+def sweep_cutoffs(N_max, count=64):
+    """`count` strictly increasing cutoffs, log-spaced from 1 to N_max."""
+    x = np.exp(np.linspace(0.0, np.log(max(N_max, 1)), count))
+    out = []
+    for v in x:
+        c = max(int(round(v)), out[-1] + 1 if out else 1)
+        out.append(c)
+    out = [min(c, N_max) for c in out]
+    return sorted(set(out))
+
+
 def random_events(seed, D, n_range=(2, 50), T=1000.0, grid=None, scale=1e-2):
     """Small random test inputs: per-asset event counts uniform in n_range,
     times uniform on [0, T] (or distinct grid points if grid is an integer),

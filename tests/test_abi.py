@@ -78,3 +78,17 @@ def test_binding_refuses_missing_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         _lib.load()
+
+
+@pytest.mark.parametrize("field,value,code", [
+    ("reps", 0, 1), ("D", 0, 1), ("N_max", 0, 1), ("max_events", -1, 1), ("reserved0", 1, 1),
+    ("D", 13, 11), ("prec", 0, 11),
+])
+def test_bad_batch_desc_rejected_on_host(lib, field, value, code):
+    from paper_2003_02842_gb300 import _lib
+    d = _lib.BatchDesc()
+    d.reps, d.D, d.N_max, d.max_events, d.tol, d.kernel, d.basis, d.prec = 4, 3, 10, 100, 1e-6, 2, 0, 1
+    setattr(d, field, value)
+    h = ctypes.c_void_p()
+    assert lib.mm_batch_create(ctypes.byref(d), ctypes.byref(h)) == code
+    assert not h.value
