@@ -319,6 +319,13 @@ mm_status mm_batch_coeffs(mm_batch batch, const void** d_coeffs, int32_t* ld);
 /* Copy those coefficients (reps * D * ld complex64) into d_dst on stream. */
 mm_status mm_batch_copy_coeffs(mm_batch batch, void* d_dst, void* stream);
 
+/* Per-stage timing of the batch's launches, as mm_profile_enable /
+ * mm_profile_read (the sweep is counted as the contraction stage). While
+ * profiling is on, mm_batch_epps launches eagerly instead of replaying its
+ * graph, so that every stage can be timed. */
+mm_status mm_batch_profile_enable(mm_batch batch, int32_t on);
+mm_status mm_batch_profile_read(mm_batch batch, double* ms, int64_t* launches, int32_t reset);
+
 /* Synchronise the last call's stream and return its device status as
  * mm_plan_sync does. */
 mm_status mm_batch_sync(mm_batch batch);

@@ -24,7 +24,7 @@ __all__ = [
     "mm_estimate_host", "mm_nyquist", "mm_plan_sync", "mm_plan_get_info", "mm_profile_enable",
     "mm_profile_read", "mm_status_string", "mm_version", "mm_corr_noalloc", "mm_autotune", "KERNELS", "BASES", "PRECISIONS", "STAGES",
     "Batch", "mm_batch_create", "mm_batch_destroy", "mm_batch_epps", "mm_batch_autotune", "mm_batch_coeffs",
-    "mm_batch_sync", "mm_batch_get_info",
+    "mm_batch_sync", "mm_batch_get_info", "mm_batch_profile_enable", "mm_batch_profile_read",
 ]
 
 
@@ -387,4 +387,15 @@ def mm_batch_get_info(batch) -> dict:
     info = _lib.BatchInfo()
     _check(_lib.load().mm_batch_get_info(batch.handle, ctypes.byref(info)), "mm_batch_get_info")
     return {k: getattr(info, k) for k, _ in _lib.BatchInfo._fields_}
+
+
+def mm_batch_profile_enable(batch, on=True):
+    _check(_lib.load().mm_batch_profile_enable(batch.handle, 1 if on else 0), "mm_batch_profile_enable")
+
+
+def mm_batch_profile_read(batch, reset=False) -> dict:
+    ms = (ctypes.c_double * len(STAGES))()
+    nl = (ctypes.c_int64 * len(STAGES))()
+    _check(_lib.load().mm_batch_profile_read(batch.handle, ms, nl, 1 if reset else 0), "mm_batch_profile_read")
+    return {s: (ms[i], nl[i]) for i, s in enumerate(STAGES)}
 

@@ -133,6 +133,8 @@ def load():
         "mm_batch_coeffs": ([p, ctypes.POINTER(p), ctypes.POINTER(i32)], st),
         "mm_batch_copy_coeffs": ([p, p, p], st),
         "mm_batch_sync": ([p], st),
+        "mm_batch_profile_enable": ([p, i32], st),
+        "mm_batch_profile_read": ([p, p, p, i32], st),
         "mm_batch_get_info": ([p, ctypes.POINTER(BatchInfo)], st),
     }
     for name, (args, res) in sig.items():

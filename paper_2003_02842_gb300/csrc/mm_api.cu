@@ -1103,6 +1103,13 @@ mm_status mm_batch_epps(mm_batch b, const int64_t* d_offsets, const double* d_t,
     b->cut = cut;
   }
   const void* key[5] = {d_offsets, d_t, d_logp, d_sigma_or_null, d_R};
+  if (p->prof) {
+    // per-stage timing needs the eager launch sequence (graph nodes carry no
+    // stage events): run without a graph
+    b->last = st;
+    b->ld = N + 1;
+    return batch_enqueue(b, d_offsets, d_t, d_logp, N, d_sigma_or_null, d_R, st);
+  }
   bool same = b->exec && !new_cut && b->key_cfg == b->cfg_gen && b->ld == N + 1;
   for (int i = 0; i < 5 && same; ++i) same = key[i] == b->key[i];
   b->last = st;
@@ -1171,6 +1178,16 @@ mm_status mm_batch_copy_coeffs(mm_batch b, void* d_dst, void* stream) {
   MM_CUDA(cudaMemcpyAsync(d_dst, b->coef, (size_t)b->p->desc.D * b->ld * 8, cudaMemcpyDeviceToDevice,
                           (cudaStream_t)stream));
   return MM_OK;
+}
+
+mm_status mm_batch_profile_enable(mm_batch b, int32_t on) {
+  if (!b) return MM_ERR_INVALID_ARG;
+  return mm_profile_enable(b->p, on);
+}
+
+mm_status mm_batch_profile_read(mm_batch b, double* ms, int64_t* launches, int32_t reset) {
+  if (!b) return MM_ERR_INVALID_ARG;
+  return mm_profile_read(b->p, ms, launches, reset);
 }
 
 mm_status mm_batch_sync(mm_batch b) {

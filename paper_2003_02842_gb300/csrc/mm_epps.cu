@@ -14,14 +14,13 @@
 // contraction at N_max plus O(#cutoffs Dg^2) additions, not one contraction
 // per cutoff.
 //
-// One CTA per problem (grid-stride over problems). Thread t of a 256-mode
-// tile takes mode k = tile + t, loads the Dg coefficients F_i(k) (coalesced
-// across threads) and adds the Dg (Dg+1)/2 products into registers; a warp
-// whose 32 modes lie in one segment keeps accumulating, and a warp-wide
-// shuffle reduction flushes its registers into the segment's shared-memory
-// slots when its segment changes. Accumulation is float32 (the products are
-// well within range; the sums run over at most N_max + 1 modes); the
-// correlation normalisation is float64.
+// One CTA per problem (grid-stride over problems). The modes are cut into
+// chunks of at most 512 that never cross a cutoff; each warp takes whole
+// chunks, its lanes step through the chunk's modes (coalesced loads of the
+// Dg coefficients F_i(k)) adding the Dg (Dg+1)/2 products into registers,
+// and one warp-shuffle reduction per chunk adds them into the chunk's segment
+// in shared memory. Accumulation is float32 (the sums run over at most
+// N_max + 1 modes); the diagonal normalisation is float64.
 #include "mm_common.cuh"
 
 namespace mmgpu {
@@ -29,22 +28,12 @@ namespace mmgpu {
 namespace {
 
 constexpr int kEppsThreads = 256;
+constexpr int kChunkModes = 512;  // modes per warp work item (16 per lane)
 
 template <int DG>
 struct Pairs {
   static constexpr int n = DG * (DG + 1) / 2;
 };
-
-// First segment j with cut[j] >= k (k <= cut[ncut - 1]).
-__device__ __forceinline__ int segment_of(const int* cut, int ncut, int k) {
-  int lo = 0, hi = ncut - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (cut[mid] >= k) hi = mid;
-    else lo = mid + 1;
-  }
-  return lo;
-}
 
 template <int DG, bool FEJER>
 __global__ void __launch_bounds__(kEppsThreads) k_epps(const float2* __restrict__ coef, int ld, const int* __restrict__ cut_g,
@@ -53,63 +42,71 @@ __global__ void __launch_bounds__(kEppsThreads) k_epps(const float2* __restrict_
                                                        int* status) {
   constexpr int NP = Pairs<DG>::n;
   constexpr int NS = FEJER ? 2 : 1;
+  constexpr int NW = kEppsThreads / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sacc = reinterpret_cast<float*>(smem_raw);                     // [NS][ncut][NP]
   double* ssig = reinterpret_cast<double*>(smem_raw + (((size_t)NS * ncut * NP * 4 + 15) & ~(size_t)15));  // [ncut][NP]
   __shared__ int scut[kMaxCutoffs];
+  __shared__ int cstart[kMaxCutoffs + 1];                  // first chunk of each segment
+  __shared__ double swt[kMaxCutoffs], swt1[kMaxCutoffs];  // basis weights per cutoff
+  __shared__ float sinv[kMaxCutoffs * DG];                 // 1 / sqrt(Sigma_aa(N_j))
   if (*gate) return;  // uniform
-  const int lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < ncut; i += kEppsThreads) scut[i] = cut_g[i];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < ncut; i += kEppsThreads) {
+    const int c = cut_g[i];
+    scut[i] = c;
+    const double four_pi2 = 4.0 * kPi * kPi;
+    swt[i] = FEJER ? four_pi2 / ((double)c + 1.0) : four_pi2 / (2.0 * (double)c + 1.0);
+    swt1[i] = FEJER ? 1.0 / (double)c : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // segment j holds the modes (N_{j-1}, N_j] (j = 0: [0, N_0]), in chunks
+    // of at most kChunkModes
+    int c = 0;
+    for (int j = 0; j < ncut; ++j) {
+      cstart[j] = c;
+      const int len = scut[j] - (j ? scut[j - 1] : -1);
+      c += (len + kChunkModes - 1) / kChunkModes;
+    }
+    cstart[ncut] = c;
+  }
+  __syncthreads();
+  const int nchunks = cstart[ncut];
   int zero_var = 0;
   for (int g = blockIdx.x; g < G; g += gridDim.x) {
     for (int i = threadIdx.x; i < NS * ncut * NP; i += kEppsThreads) sacc[i] = 0.f;
     __syncthreads();
-    const int Kuse = scut[ncut - 1] + 1;
     const float2* cg = coef + (size_t)g * DG * ld;
-    float acc[NP], acc1[FEJER ? NP : 1];
-#pragma unroll
-    for (int p = 0; p < NP; ++p) acc[p] = 0.f;
-#pragma unroll
-    for (int p = 0; p < (FEJER ? NP : 1); ++p) acc1[p] = 0.f;
-    int cs = -1;  // segment held in the registers (uniform across the warp)
-    auto flush = [&]() {
-      if (cs >= 0) {
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-          float v = acc[p];
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          if (lane == 0) atomicAdd(&sacc[cs * NP + p], v);
-          acc[p] = 0.f;
-          if (FEJER) {
-            float w = acc1[p];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-            if (lane == 0) atomicAdd(&sacc[(ncut + cs) * NP + p], w);
-            acc1[p] = 0.f;
-          }
+    // each warp takes whole chunks: all 32 lanes in one segment, registers
+    // accumulate over the chunk, one warp reduction per chunk
+    for (int ch = warp; ch < nchunks; ch += NW) {
+      int sj = 0;
+      {
+        int lo = 0, hi = ncut - 1;  // last segment with cstart <= ch
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (cstart[mid] <= ch) lo = mid;
+          else hi = mid - 1;
         }
+        sj = lo;
       }
-      cs = -1;
-    };
-    for (int t0 = 0; t0 < Kuse; t0 += kEppsThreads) {
-      const int k = t0 + threadIdx.x;
-      const bool valid = k < Kuse;
-      float2 c[DG];
-      const float sc = k == 0 ? 1.0f : 1.41421356237309515f;  // sqrt(d_k)
+      const int kb = (sj ? scut[sj - 1] + 1 : 0) + (ch - cstart[sj]) * kChunkModes;
+      const int ke = min(kb + kChunkModes, scut[sj] + 1);
+      float acc[NP], acc1[FEJER ? NP : 1];
 #pragma unroll
-      for (int i = 0; i < DG; ++i) {
-        const float2 v = valid ? __ldg(cg + (size_t)i * ld + k) : make_float2(0.f, 0.f);
-        c[i] = make_float2(v.x * sc, v.y * sc);
-      }
-      const int seg = valid ? segment_of(scut, ncut, k) : -1;
-      const int s0 = __shfl_sync(0xffffffffu, seg, 0), s31 = __shfl_sync(0xffffffffu, seg, 31);
-      const float kf = (float)k;
-      if (s0 == s31 && s0 >= 0) {
-        if (s0 != cs) {
-          flush();
-          cs = s0;
+      for (int p = 0; p < NP; ++p) acc[p] = 0.f;
+#pragma unroll
+      for (int p = 0; p < (FEJER ? NP : 1); ++p) acc1[p] = 0.f;
+      for (int k = kb + lane; k < ke; k += 32) {
+        float2 c[DG];
+        const float sc = k == 0 ? 1.0f : 1.41421356237309515f;  // sqrt(d_k)
+#pragma unroll
+        for (int i = 0; i < DG; ++i) {
+          const float2 v = __ldg(cg + (size_t)i * ld + k);
+          c[i] = make_float2(v.x * sc, v.y * sc);
         }
+        const float kf = (float)k;
         int p = 0;
 #pragma unroll
         for (int i = 0; i < DG; ++i)
@@ -119,34 +116,39 @@ __global__ void __launch_bounds__(kEppsThreads) k_epps(const float2* __restrict_
             acc[p] += q;
             if (FEJER) acc1[p] = fmaf(kf, q, acc1[p]);
           }
-      } else {
-        // the warp straddles a cutoff (or the end): per-lane shared atomics
-        flush();
-        if (seg >= 0) {
-          int p = 0;
+      }
 #pragma unroll
-          for (int i = 0; i < DG; ++i)
+      for (int p = 0; p < NP; ++p) {
+        float v = acc[p];
 #pragma unroll
-            for (int j = i; j < DG; ++j, ++p) {
-              const float q = fmaf(c[i].x, c[j].x, c[i].y * c[j].y);
-              atomicAdd(&sacc[seg * NP + p], q);
-              if (FEJER) atomicAdd(&sacc[(ncut + seg) * NP + p], kf * q);
-            }
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) atomicAdd(&sacc[sj * NP + p], v);
+        if (FEJER) {
+          float w = acc1[p];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+          if (lane == 0) atomicAdd(&sacc[(ncut + sj) * NP + p], w);
         }
       }
     }
-    flush();
     __syncthreads();
-    // prefix over segments and the basis weights (float64 from here on)
-    const double four_pi2 = 4.0 * kPi * kPi;
+    // prefix over segments with the basis weights (float64), then the
+    // diagonal normalisation: 1/sqrt(Sigma_aa) in float64 once per asset and
+    // cutoff, the off-diagonal products in float32
     for (int p = threadIdx.x; p < NP; p += kEppsThreads) {
       double P = 0.0, P1 = 0.0;
       for (int j = 0; j < ncut; ++j) {
         P += (double)sacc[j * NP + p];
         if (FEJER) P1 += (double)sacc[(ncut + j) * NP + p];
-        const double Nj = (double)scut[j];
-        ssig[j * NP + p] = FEJER ? four_pi2 / (Nj + 1.0) * (P - P1 / Nj) : four_pi2 / (2.0 * Nj + 1.0) * P;
+        ssig[j * NP + p] = FEJER ? swt[j] * (P - P1 * swt1[j]) : swt[j] * P;
       }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ncut * DG; e += kEppsThreads) {
+      const int j = e / DG, a = e - j * DG;
+      const double d = ssig[j * NP + a * DG - a * (a - 1) / 2];
+      sinv[e] = d > 0.0 ? (float)rsqrt(d) : __int_as_float(0x7fc00000);
+      if (!(d > 0.0)) zero_var = 1;
     }
     __syncthreads();
     // Sigma and R for every cutoff, both triangles
@@ -155,16 +157,11 @@ __global__ void __launch_bounds__(kEppsThreads) k_epps(const float2* __restrict_
       const int a = r / DG, b = r - a * DG;
       const int lo = a < b ? a : b, hi = a < b ? b : a;
       const int p = lo * DG - lo * (lo - 1) / 2 + (hi - lo);  // index of pair (lo, hi)
-      const int pa = a * DG - a * (a - 1) / 2, pb = b * DG - b * (b - 1) / 2;  // (a, a), (b, b)
-      const double s = ssig[j * NP + p];
-      const double da = ssig[j * NP + pa], db = ssig[j * NP + pb];
+      const float sv = (float)ssig[j * NP + p];
       const size_t o = ((size_t)g * ncut + j) * DG * DG + r;
-      if (sigma) sigma[o] = (float)s;
-      double rv;
-      if (a == b) rv = da > 0.0 ? 1.0 : __longlong_as_double(0x7ff8000000000000LL);
-      else rv = (da > 0.0 && db > 0.0) ? s / (sqrt(da) * sqrt(db)) : __longlong_as_double(0x7ff8000000000000LL);
-      if (!(da > 0.0)) zero_var = 1;
-      Rout[o] = (float)rv;
+      if (sigma) sigma[o] = sv;
+      Rout[o] = a == b ? (sinv[j * DG + a] == sinv[j * DG + a] ? 1.0f : sinv[j * DG + a])
+                       : sv * sinv[j * DG + a] * sinv[j * DG + b];
     }
     __syncthreads();
   }
@@ -178,10 +175,9 @@ cudaError_t launch_dg(bool fejer, const void* coef, int ld, const int* cut, int 
   const int NS = fejer ? 2 : 1;
   const size_t smem = (((size_t)NS * ncut * NP * 4 + 15) & ~(size_t)15) + (size_t)ncut * NP * 8;
   auto go = [&](auto fn) -> cudaError_t {
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
+    // static + dynamic shared memory may pass 48 KB: always opt in
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     fn<<<grid, kEppsThreads, smem, s>>>((const float2*)coef, ld, cut, ncut, G, sigma, R, status_gate, status);
     return cudaGetLastError();
   };
