@@ -331,6 +331,80 @@ mm_status mm_batch_profile_read(mm_batch batch, double* ms, int64_t* launches, i
 mm_status mm_batch_sync(mm_batch batch);
 mm_status mm_batch_get_info(mm_batch batch, mm_batch_info* info);
 
+/* ------------------------------------------------------------------------
+ * Serving form: a request loop over one day's events kept resident on the
+ * device (per-asset sorted CSR, loaded once). A request asks for Sigma and
+ * R (Algorithm 3) of an asset subset over a window [t0, t1] at a cutoff N:
+ * given, from Eq. (19) for a sampling interval dt_equiv, or (N = 0 and
+ * dt_equiv = 0) the window's Nyquist cutoff (Algorithm 2, capped at N_max).
+ * Times are rescaled with the window (Algorithm 4 over [t0, t1]), so an
+ * asset's coefficients do not depend on the other requested assets.
+ *
+ * Continuous batching: a native scheduler thread admits queued requests into
+ * execution slots as slots free up; each slot runs on its own CUDA stream, so
+ * requests in flight overlap on the GPU. The slot count is the number of
+ * slots (each sized for the largest admissible request: D assets,
+ * request_max_events events in the window, N_max) that fit in hbm_budget,
+ * at least one and at most max_slots. Results are written to the caller's
+ * host buffers; completions are polled, out of order, with host timestamps.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t D;                   /* assets in the resident store, 1 .. 4096 */
+  int32_t N_max;               /* largest cutoff served */
+  int64_t max_events;          /* events in the resident store (upper bound) */
+  int64_t request_max_events;  /* events a request's window may hold (0 = max_events) */
+  int64_t hbm_budget;          /* bytes for the slots' workspace (0 = max_slots slots) */
+  int32_t max_slots;           /* 1 .. 64 */
+  int32_t reserved0;           /* must be zero */
+  double tol;
+  mm_kernel kernel;
+  mm_basis basis;
+  mm_precision prec;
+  int32_t reserved[4];         /* must be zero */
+} mm_server_desc;
+
+typedef struct {
+  double t0, t1;               /* window, t0 < t1, in the store's time unit */
+  int32_t n_assets;            /* 1 .. D */
+  int32_t N;                   /* > 0: cutoff; 0: from dt_equiv, or Nyquist when dt_equiv = 0 */
+  const int32_t* assets;       /* host, n_assets distinct asset ids (copied at submit) */
+  double dt_equiv;             /* > 0 with N = 0: N = floor((T/dt - 1)/2), T = t1 - t0 (Eq. (19)) */
+  void* h_R;                   /* host, n_assets^2 elements (float32, float64 for FP64) */
+  void* h_sigma_or_null;       /* host, same layout, or NULL */
+} mm_request;
+
+typedef struct {
+  int64_t ticket;
+  int32_t status;              /* mm_status of the request */
+  int32_t n_assets;
+  int32_t N;                   /* cutoff used */
+  int32_t reserved;
+  double t_submit, t_start, t_done;  /* seconds on the server's clock */
+} mm_completion;
+
+typedef struct {
+  int64_t submitted, completed;
+  int64_t slot_bytes;          /* device workspace per slot */
+  int64_t resident_bytes;      /* the resident event store */
+  int32_t slots, inflight, peak_inflight, queued;
+} mm_server_stats;
+
+typedef struct mm_server_s* mm_server;
+
+mm_status mm_server_create(const mm_server_desc* desc, mm_server* out);
+/* Upload the store: h_offsets[D+1], h_t and h_logp (h_offsets[D] each),
+ * strictly increasing times per asset (checked on the host). Only while no
+ * request is queued or in flight. */
+mm_status mm_server_load(mm_server server, const int64_t* h_offsets, const double* h_t, const double* h_logp);
+/* Queue a request; returns at once with its ticket. */
+mm_status mm_server_submit(mm_server server, const mm_request* request, int64_t* ticket);
+/* Up to max completions (waiting up to wait_s seconds for the first). The
+ * request's h_R / h_sigma hold its result once its completion is returned. */
+mm_status mm_server_poll(mm_server server, mm_completion* out, int32_t max, int32_t* n_out, double wait_s);
+mm_status mm_server_get_stats(mm_server server, mm_server_stats* stats);
+/* Finish queued and in-flight requests, stop the scheduler, free everything. */
+mm_status mm_server_destroy(mm_server server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,6 +25,8 @@ __all__ = [
     "mm_profile_read", "mm_status_string", "mm_version", "mm_corr_noalloc", "mm_autotune", "KERNELS", "BASES", "PRECISIONS", "STAGES",
     "Batch", "mm_batch_create", "mm_batch_destroy", "mm_batch_epps", "mm_batch_autotune", "mm_batch_coeffs",
     "mm_batch_sync", "mm_batch_get_info", "mm_batch_profile_enable", "mm_batch_profile_read",
+    "Server", "mm_server_create", "mm_server_load", "mm_server_submit", "mm_server_poll", "mm_server_get_stats",
+    "mm_server_destroy",
 ]
 
 
@@ -398,4 +400,98 @@ def mm_batch_profile_read(batch, reset=False) -> dict:
     nl = (ctypes.c_int64 * len(STAGES))()
     _check(_lib.load().mm_batch_profile_read(batch.handle, ms, nl, 1 if reset else 0), "mm_batch_profile_read")
     return {s: (ms[i], nl[i]) for i, s in enumerate(STAGES)}
+
+
+# --------------------------------------------------------------------------
+# Serving form: request loop over a resident event store (see include/mm.h)
+# --------------------------------------------------------------------------
+class Server:
+    """Owns an mm_server handle and the host result buffers of requests in
+    flight (kept alive until their completion is polled)."""
+
+    def __init__(self, handle, desc: dict):
+        self.handle = handle
+        self.desc = desc
+        self.pending = {}
+        self._store = None
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                _lib.load().mm_server_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def mm_server_create(D, N_max, max_events, request_max_events=0, hbm_budget=0, max_slots=4, tol=1e-6,
+                     kernel="es", basis="fejer", prec="bf16x3") -> Server:
+    d = _lib.ServerDesc()
+    d.D, d.N_max, d.max_events, d.request_max_events = int(D), int(N_max), int(max_events), int(request_max_events)
+    d.hbm_budget, d.max_slots, d.tol = int(hbm_budget), int(max_slots), float(tol)
+    d.kernel, d.basis, d.prec = KERNELS[kernel], BASES[basis], PRECISIONS[prec]
+    h = ctypes.c_void_p()
+    _check(_lib.load().mm_server_create(ctypes.byref(d), ctypes.byref(h)), "mm_server_create")
+    return Server(h, dict(D=int(D), N_max=int(N_max), max_events=int(max_events), prec=prec, basis=basis,
+                          kernel=kernel, tol=float(tol)))
+
+
+def mm_server_load(server, offsets, t, logp):
+    """Upload the resident store from host numpy arrays (CSR, sorted per asset)."""
+    import numpy as np
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    tt = np.ascontiguousarray(t, dtype=np.float64)
+    pp = np.ascontiguousarray(logp, dtype=np.float64)
+    server._store = (off, tt, pp)
+    _check(_lib.load().mm_server_load(server.handle, off.ctypes.data, tt.ctypes.data, pp.ctypes.data),
+           "mm_server_load")
+
+
+def mm_server_submit(server, t0, t1, assets, N=0, dt=0.0, sigma=False) -> int:
+    """Queue a request; returns its ticket. N > 0: that cutoff; N = 0 with
+    dt > 0: Eq. (19) for dt; N = 0, dt = 0: the window's Nyquist cutoff."""
+    import numpy as np
+    a = np.ascontiguousarray(assets, dtype=np.int32)
+    n = len(a)
+    dt_ = np.float64 if server.desc["prec"] == "fp64" else np.float32
+    R = np.empty((n, n), dtype=dt_)
+    S = np.empty((n, n), dtype=dt_) if sigma else None
+    rq = _lib.Request()
+    rq.t0, rq.t1, rq.n_assets, rq.N, rq.dt_equiv = float(t0), float(t1), n, int(N), float(dt)
+    rq.assets = a.ctypes.data
+    rq.h_R = R.ctypes.data
+    rq.h_sigma_or_null = S.ctypes.data if S is not None else None
+    tk = ctypes.c_int64()
+    _check(_lib.load().mm_server_submit(server.handle, ctypes.byref(rq), ctypes.byref(tk)), "mm_server_submit")
+    server.pending[tk.value] = (a, R, S)
+    return tk.value
+
+
+def mm_server_poll(server, max_items=256, wait=0.0) -> list:
+    """Completed requests: dicts with ticket, status, N, n_assets, t_submit,
+    t_start, t_done (seconds) and the result arrays R (and Sigma)."""
+    buf = (_lib.Completion * int(max_items))()
+    n = ctypes.c_int32()
+    _check(_lib.load().mm_server_poll(server.handle, buf, int(max_items), ctypes.byref(n), float(wait)),
+           "mm_server_poll")
+    out = []
+    for i in range(n.value):
+        c = buf[i]
+        _, R, S = server.pending.pop(c.ticket)
+        out.append(dict(ticket=c.ticket, status=c.status, N=c.N, n_assets=c.n_assets, t_submit=c.t_submit,
+                        t_start=c.t_start, t_done=c.t_done, R=R, Sigma=S))
+    return out
+
+
+def mm_server_get_stats(server) -> dict:
+    st = _lib.ServerStats()
+    _check(_lib.load().mm_server_get_stats(server.handle, ctypes.byref(st)), "mm_server_get_stats")
+    return {k: getattr(st, k) for k, _ in _lib.ServerStats._fields_}
+
+
+def mm_server_destroy(server):
+    if server.handle:
+        _check(_lib.load().mm_server_destroy(server.handle), "mm_server_destroy")
+        server.handle = None
 

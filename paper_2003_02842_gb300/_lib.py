@@ -94,6 +94,62 @@ class BatchInfo(ctypes.Structure):
     ]
 
 
+class ServerDesc(ctypes.Structure):
+    _fields_ = [
+        ("D", ctypes.c_int32),
+        ("N_max", ctypes.c_int32),
+        ("max_events", ctypes.c_int64),
+        ("request_max_events", ctypes.c_int64),
+        ("hbm_budget", ctypes.c_int64),
+        ("max_slots", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("tol", ctypes.c_double),
+        ("kernel", ctypes.c_int),
+        ("basis", ctypes.c_int),
+        ("prec", ctypes.c_int),
+        ("reserved", ctypes.c_int32 * 4),
+    ]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [
+        ("t0", ctypes.c_double),
+        ("t1", ctypes.c_double),
+        ("n_assets", ctypes.c_int32),
+        ("N", ctypes.c_int32),
+        ("assets", ctypes.c_void_p),
+        ("dt_equiv", ctypes.c_double),
+        ("h_R", ctypes.c_void_p),
+        ("h_sigma_or_null", ctypes.c_void_p),
+    ]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [
+        ("ticket", ctypes.c_int64),
+        ("status", ctypes.c_int32),
+        ("n_assets", ctypes.c_int32),
+        ("N", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("t_submit", ctypes.c_double),
+        ("t_start", ctypes.c_double),
+        ("t_done", ctypes.c_double),
+    ]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_int64),
+        ("completed", ctypes.c_int64),
+        ("slot_bytes", ctypes.c_int64),
+        ("resident_bytes", ctypes.c_int64),
+        ("slots", ctypes.c_int32),
+        ("inflight", ctypes.c_int32),
+        ("peak_inflight", ctypes.c_int32),
+        ("queued", ctypes.c_int32),
+    ]
+
+
 _lib = None
 
 
@@ -134,6 +190,12 @@ def load():
         "mm_batch_copy_coeffs": ([p, p, p], st),
         "mm_batch_sync": ([p], st),
         "mm_batch_profile_enable": ([p, i32], st),
+        "mm_server_create": ([ctypes.POINTER(ServerDesc), ctypes.POINTER(p)], st),
+        "mm_server_load": ([p, p, p, p], st),
+        "mm_server_submit": ([p, ctypes.POINTER(Request), ctypes.POINTER(i64)], st),
+        "mm_server_poll": ([p, ctypes.POINTER(Completion), i32, ctypes.POINTER(i32), d], st),
+        "mm_server_get_stats": ([p, ctypes.POINTER(ServerStats)], st),
+        "mm_server_destroy": ([p], st),
         "mm_batch_profile_read": ([p, p, p, i32], st),
         "mm_batch_get_info": ([p, ctypes.POINTER(BatchInfo)], st),
     }

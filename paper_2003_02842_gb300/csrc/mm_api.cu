@@ -165,6 +165,8 @@ struct mm_plan_s {
   size_t rs = 4;   // bytes per real grid cell / output element
   int msp = 0, klo = 0, khi = 0;
   int64_t n_max = 0;
+  int D = 0;                      // assets of the current call (<= desc.D; a server slot varies it)
+  int cfg_D = -1;                 // D of the cached configuration
   int gsize = 0;                  // assets per problem (D for a single problem)
   int G = 1;                      // problems (a batch has G > 1)
   bool batch = false;             // created for a batch: no contraction or host-staging workspace
@@ -190,6 +192,7 @@ struct mm_plan_s {
   float* acc[2] = {nullptr, nullptr};  // mixed path: FP32 accumulators, used alternately
   int acc_sel = 0;
   bool acc_dirty = true;          // clear both before the next contraction
+  int acc_D = -1;                 // D whose D x Dp region the last epilogue cleared
   int64_t* s_off = nullptr;
   double* s_t = nullptr;
   double* s_p = nullptr;
@@ -299,7 +302,7 @@ struct StageScope {
 // Per-cutoff configuration: grid size, FFT factorisation, tiles and the
 // kernel constants of Sec. 2.2.5 with sigma = M_r / M.
 mm_status configure(mm_plan p, int N) {
-  if (p->cfg_N == N) return MM_OK;
+  if (p->cfg_N == N && p->cfg_D == p->D) return MM_OK;
   const int64_t M = 2 * (int64_t)N + 1;
   int64_t n;
   int P, Q;
@@ -340,7 +343,7 @@ mm_status configure(mm_plan p, int N) {
   f.N = N;
 
   SpreadParams s{};
-  s.D = p->desc.D;
+  s.D = p->D;
   s.Mr = Mr;
   s.msp = p->msp;
   s.klo = p->klo;
@@ -372,7 +375,7 @@ mm_status configure(mm_plan p, int N) {
   // per-asset FFT: mixed path, the complex grid fits in shared memory and n
   // factors into at most kMaxAssetPasses compiled radices
   AssetFft af{};
-  int split = p->desc.D < kSMs ? 2 : 1;  // fewer assets than SMs: two CTAs per asset
+  int split = p->D < kSMs ? 2 : 1;  // fewer assets than SMs: two CTAs per asset
   if (p->tune_split == 1 || p->tune_split == 2) split = p->tune_split;
   const int maxr = p->tune_maxr == 16 ? 16 : 32;
   auto fits_split = [&](int sp_) {
@@ -393,6 +396,7 @@ mm_status configure(mm_plan p, int N) {
   p->sp = s;
   p->Mr = Mr;
   p->cfg_N = N;
+  p->cfg_D = p->D;
   return MM_OK;
 }
 
@@ -420,7 +424,7 @@ mm_status check_plan(mm_plan p) {
 
 GramParams gram_params(mm_plan p, int N) {
   GramParams g{};
-  g.D = p->desc.D;
+  g.D = p->D;
   g.N = N;
   g.ld = N + 1;
   g.Dp = (g.D + 3) / 4 * 4;
@@ -449,7 +453,7 @@ GramParams gram_params(mm_plan p, int N) {
 
 mm_status coeffs_impl(mm_plan p, const int64_t* off, const double* t, const double* logp, int N, double t0,
                       double t1, void* coeffs, int32_t* N_used, cudaStream_t st) {
-  const int D = p->desc.D;
+  const int D = p->D;
   p->last = st;
   {
     StageScope sc(p, MM_STAGE_PREP, st);
@@ -545,6 +549,7 @@ mm_status corr_impl(mm_plan p, const void* coeffs, int N, void* sigma, void* R, 
     MM_CUDA(launch_reduce_corr(true, p->partial, g, sigma, R, p->status, st));
   } else {
     const size_t acc_bytes = (size_t)g.D * g.Dp * sizeof(float);
+    if (p->acc_D != g.D) p->acc_dirty = true;  // the cleared region was sized for another D
     if (p->acc_dirty) {
       MM_CUDA(cudaMemsetAsync(p->acc[0], 0, acc_bytes, st));
       MM_CUDA(cudaMemsetAsync(p->acc[1], 0, acc_bytes, st));
@@ -564,6 +569,7 @@ mm_status corr_impl(mm_plan p, const void* coeffs, int N, void* sigma, void* R, 
     }
     p->acc_sel ^= 1;
     p->acc_dirty = false;
+    p->acc_D = g.D;
   }
   p->gram = g;
   return MM_OK;
@@ -600,7 +606,7 @@ namespace {
 // Plan for D = G * gsize assets in G independent problems of gsize assets
 // each (G = 1: the single-problem plan of mm_plan_create). A batch plan
 // allocates no contraction or host-staging workspace.
-mm_status plan_create_impl(const mm_plan_desc* desc, int gsize, bool batch, mm_plan* out) {
+mm_status plan_create_impl(const mm_plan_desc* desc, int gsize, bool batch, mm_plan* out, bool staging = true) {
   if (!out) return MM_ERR_INVALID_ARG;
   *out = nullptr;
   if (!desc) return MM_ERR_INVALID_ARG;
@@ -623,6 +629,7 @@ mm_status plan_create_impl(const mm_plan_desc* desc, int gsize, bool batch, mm_p
   p->desc = d;
   p->gsize = gsize;
   p->G = d.D / gsize;
+  p->D = d.D;
   p->batch = batch;
   p->fp64 = d.prec == MM_PREC_FP64;
   p->cs = p->fp64 ? 16 : 8;
@@ -677,7 +684,7 @@ mm_status plan_create_impl(const mm_plan_desc* desc, int gsize, bool batch, mm_p
       A((void**)&p->acc[1], D * (size_t)g.Dp * sizeof(float));
     }
   }
-  if (d.max_events > 0 && !batch) {
+  if (d.max_events > 0 && !batch && staging) {
     A((void**)&p->s_off, (D + 1) * sizeof(int64_t));
     A((void**)&p->s_t, (size_t)d.max_events * sizeof(double));
     A((void**)&p->s_p, (size_t)d.max_events * sizeof(double));
@@ -772,7 +779,7 @@ mm_status mm_estimate_host(mm_plan p, const int64_t* h_offsets, const double* h_
   mm_status r = check_plan(p);
   if (r != MM_OK) return r;
   if (!h_offsets || !h_t || !h_logp || !h_R || !p->s_off) return MM_ERR_INVALID_ARG;
-  const int D = p->desc.D;
+  const int D = p->D;
   const int64_t ne = h_offsets[D];
   if (h_offsets[0] != 0 || ne < 0 || ne > p->desc.max_events) return MM_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -895,11 +902,11 @@ mm_status mm_nyquist(mm_plan p, const int64_t* d_offsets, const double* d_t, dou
   p->last = st;
   {
     StageScope sc(p, MM_STAGE_PREP, st);
-    MM_CUDA(launch_bounds(d_offsets, d_t, p->desc.D, p->gsize, p->desc.max_events, t0, t1, p->bounds, p->status, st));
+    MM_CUDA(launch_bounds(d_offsets, d_t, p->D, p->gsize, p->desc.max_events, t0, t1, p->bounds, p->status, st));
   }
   {
     StageScope sc(p, MM_STAGE_PREP, st, 2);
-    MM_CUDA(launch_min_gap(d_offsets, d_t, p->desc.D, p->bounds, p->gapbits, p->status + 2, p->status, st));
+    MM_CUDA(launch_min_gap(d_offsets, d_t, p->D, p->bounds, p->gapbits, p->status + 2, p->status, st));
   }
   int hv[3];
   MM_CUDA(cudaMemcpyAsync(hv, p->status, sizeof(hv), cudaMemcpyDeviceToHost, st));
@@ -980,6 +987,27 @@ mm_status mm_profile_read(mm_plan p, double* ms, int64_t* launches, int32_t rese
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ internal
+namespace mmgpu {
+
+mm_status plan_create_no_staging(const mm_plan_desc* desc, mm_plan* out) {
+  if (!desc) return MM_ERR_INVALID_ARG;
+  return plan_create_impl(desc, desc->D > 0 ? desc->D : 1, false, out, false);
+}
+
+mm_status plan_set_active_assets(mm_plan p, int D) {
+  if (!p || D < 1 || D > p->desc.D || p->G != 1) return MM_ERR_INVALID_ARG;
+  p->D = D;
+  p->gsize = D;
+  return MM_OK;
+}
+
+int* plan_status_word(mm_plan p) { return p ? p->status : nullptr; }
+
+mm_status plan_flags_to_status(int flags) { return flags_to_status(flags); }
+
+}  // namespace mmgpu
 
 // ------------------------------------------------------------------ batch
 struct mm_batch_s {

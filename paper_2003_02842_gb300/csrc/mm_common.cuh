@@ -187,6 +187,12 @@ cudaError_t launch_reduce_corr(bool fp64, const void* partial, const GramParams&
                                void* sigma, void* R, int* status, cudaStream_t s);
 size_t gram_tc_smem(int mode, bool two_tiles);
 int epps_max_assets();
+
+// Plan internals used by the serving engine (mm_server.cu).
+mm_status plan_create_no_staging(const mm_plan_desc* desc, mm_plan* out);  // no host-buffer entry staging
+mm_status plan_set_active_assets(mm_plan p, int D);
+int* plan_status_word(mm_plan p);
+mm_status plan_flags_to_status(int flags);
 cudaError_t launch_epps(int Dg, bool fejer, const void* coef, int ld, const int* cut, int ncut, int G, float* sigma,
                         float* R, int* status, int grid, cudaStream_t s);
 

@@ -232,6 +232,67 @@ def c4_batch(seed=0, reps=4096, D=10, T=28800, rho=0.35, sig2_range=(0.1, 0.2), 
     return ev
 
 
+def c5_day(seed=0, D=500, T=28800, n_factors=3, load_sd=0.3, idio_var=0.1, mu=0.01, s0=100.0,
+           lam_lo=0.01, lam_hi=1.0, shape=0.45):
+    """Serving workload: one trading day of D assets on the 1-s grid. Arrival
+    intensity is U-shaped, lambda(t) = lam_lo + (lam_hi - lam_lo) |2t/T - 1|^shape
+    per second (busy open and close, quiet midday); an asset observes second
+    t with probability 1 - exp(-lambda(t)). Log-prices follow a factor GBM,
+    exact in law at the observed seconds: n_factors common Brownian factors
+    with loadings ~ N(0, load_sd^2) plus an idiosyncratic one of variance
+    idio_var (per day)."""
+    rng = rng_for(5, seed)
+    tsec = np.arange(T)
+    lam = lam_lo + (lam_hi - lam_lo) * np.abs(2.0 * tsec / T - 1.0) ** shape
+    pobs = 1.0 - np.exp(-lam)
+    dt = 1.0 / SECONDS_PER_DAY
+    Fac = np.cumsum(rng.standard_normal((T, n_factors)) * np.sqrt(dt), axis=0)  # factors on every second
+    L = rng.normal(0.0, load_sd, size=(D, n_factors))
+    ts, ps = [], []
+    for i in range(D):
+        sec = np.flatnonzero(rng.random(T) < pobs)
+        if len(sec) == 0:
+            sec = np.array([0])
+        di = sec.astype(np.float64) * dt
+        E = np.cumsum(rng.standard_normal(len(sec)) * np.sqrt(np.diff(di, prepend=0.0)))
+        var_i = float(L[i] @ L[i]) + idio_var
+        W = Fac[sec] @ L[i] + np.sqrt(idio_var) * E
+        ps.append(np.log(s0) + (mu - 0.5 * var_i) * di + W)
+        ts.append(sec.astype(np.float64))
+    ev = from_lists(ts, ps)
+    ev.meta = {"workload": f"c5_day_D{D}", "T": T}
+    return ev
+
+
+def c5_requests(seed=0, n=10000, D=500, T=28800, w_range=(300, 28800), k_range=(10, 500),
+                dt_modes=(0.0, 60.0, 600.0)):
+    """Request stream of the serving workload: window length ~ U(w_range)
+    seconds at a uniform start, asset subset of size ~ U{k_range} drawn
+    without replacement, cutoff mode uniform over dt_modes (0: the window's
+    Nyquist cutoff, else Eq. (19) at that sampling interval)."""
+    rng = rng_for(6, seed)
+    out = []
+    for _ in range(n):
+        W = float(rng.uniform(*w_range))
+        t0 = float(rng.uniform(0.0, T - W))
+        k = int(rng.integers(k_range[0], min(k_range[1], D) + 1))
+        assets = np.sort(rng.choice(D, size=k, replace=False)).astype(np.int32)
+        dtm = float(dt_modes[int(rng.integers(len(dt_modes)))])
+        out.append({"t0": t0, "t1": t0 + W, "assets": assets, "dt": dtm})
+    return out
+
+
+def window_events(ev, assets, t0, t1):
+    """The events of the given assets inside [t0, t1], as their own Events."""
+    ts, ps = [], []
+    for a in assets:
+        t, p = ev.asset(int(a))
+        m = (t >= t0) & (t <= t1)
+        ts.append(t[m])
+        ps.append(p[m])
+    return from_lists(ts, ps)
+
+
 def sweep_cutoffs(N_max, count=64):
     """`count` strictly increasing cutoffs, log-spaced from 1 to N_max."""
     x = np.exp(np.linspace(0.0, np.log(max(N_max, 1)), count))

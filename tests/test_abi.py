@@ -92,3 +92,16 @@ def test_bad_batch_desc_rejected_on_host(lib, field, value, code):
     h = ctypes.c_void_p()
     assert lib.mm_batch_create(ctypes.byref(d), ctypes.byref(h)) == code
     assert not h.value
+
+
+@pytest.mark.parametrize("field,value", [
+    ("D", 0), ("D", 5000), ("N_max", 0), ("max_events", 0), ("max_slots", 0), ("max_slots", 65), ("reserved0", 2),
+])
+def test_bad_server_desc_rejected_on_host(lib, field, value):
+    from paper_2003_02842_gb300 import _lib
+    d = _lib.ServerDesc()
+    d.D, d.N_max, d.max_events, d.max_slots, d.tol, d.kernel, d.basis, d.prec = 4, 10, 100, 2, 1e-6, 2, 1, 1
+    setattr(d, field, value)
+    h = ctypes.c_void_p()
+    assert lib.mm_server_create(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert not h.value
