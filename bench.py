@@ -39,12 +39,17 @@ NCU_TRAFFIC = {}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "c4"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "c4", "c5"])
     ap.add_argument("--reps", type=int, default=4096, help="c4: Monte Carlo replications per step")
     ap.add_argument("--cutoffs", type=int, default=64, help="c4: cutoffs of the Epps sweep")
+    ap.add_argument("--requests", type=int, default=10000, help="c5: requests in the stream")
+    ap.add_argument("--slots", type=int, default=8, help="c5: execution slots at most")
+    ap.add_argument("--hbm-budget-gb", type=float, default=16.0, help="c5: HBM budget for the slots")
+    ap.add_argument("--load", type=float, default=0.7, help="c5: offered load of the latency phase, "
+                                                            "as a fraction of the measured throughput")
     ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "3xtf32", "fp64"])
     ap.add_argument("--kernel", default="es", choices=["gauss", "kb", "es"])
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
@@ -400,6 +405,99 @@ def bench_batch(args):
         dist.destroy_process_group()
 
 
+def bench_serve(args):
+    """c5: the serving form. Phase 1 submits the whole request stream at once
+    and measures completed requests (and the events of their windows) per
+    second; phase 2 replays requests as a Poisson stream at `--load` times
+    that throughput and reports p50 / p99 latency (submit to result on the
+    host) with continuous batching over the server's slots."""
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    import __graft_entry__ as g
+    g.build()
+    import paper_2003_02842_gb300 as mm
+    from paper_2003_02842_gb300 import synth
+
+    ev = synth.c5_day(seed=rank)
+    reqs = synth.c5_requests(seed=rank, n=args.requests, D=ev.D)
+    Nmax = 14400
+    srv = mm.mm_server_create(D=ev.D, N_max=Nmax, max_events=ev.n_events, hbm_budget=int(args.hbm_budget_gb * 2**30),
+                              max_slots=args.slots, tol=1e-6, kernel="es", basis="fejer", prec=args.prec)
+    mm.mm_server_load(srv, ev.offsets, ev.t, ev.logp)
+    counts = np.diff(ev.offsets)
+
+    def window_events(r):
+        n = 0
+        for a in r["assets"]:
+            t = ev.t[ev.offsets[a]:ev.offsets[a + 1]]
+            n += int(np.searchsorted(t, r["t1"], "right") - np.searchsorted(t, r["t0"], "left"))
+        return n
+
+    def drain(n, timeout=600.0):
+        got, t_end = [], time.time() + timeout
+        while len(got) < n and time.time() < t_end:
+            got += mm.mm_server_poll(srv, max_items=1024, wait=0.01)
+        return got
+
+    # warm-up (first calls build per-cutoff tables)
+    for r in reqs[:16]:
+        mm.mm_server_submit(srv, r["t0"], r["t1"], r["assets"], dt=r["dt"])
+    drain(16)
+    with ClockSampler(dev.index) as clk:
+        t0 = time.time()
+        for r in reqs:
+            mm.mm_server_submit(srv, r["t0"], r["t1"], r["assets"], dt=r["dt"])
+        done = drain(len(reqs))
+        wall = time.time() - t0
+        ok = [c for c in done if c["status"] in (0, 9)]
+        thr = len(done) / wall
+        # latency phase: open-loop Poisson arrivals at load x throughput
+        rng = np.random.default_rng(7)
+        nlat = min(len(reqs), max(200, int(thr * 3)))
+        gaps = rng.exponential(1.0 / (args.load * thr), size=nlat)
+        lat_done = []
+        t_start = time.time()
+        due = t_start
+        for i in range(nlat):
+            due += gaps[i]
+            while time.time() < due:
+                lat_done += mm.mm_server_poll(srv, max_items=1024, wait=0.0)
+            r = reqs[i]
+            mm.mm_server_submit(srv, r["t0"], r["t1"], r["assets"], dt=r["dt"])
+        lat_done += drain(nlat - len(lat_done))
+    clocks = clk.summary()
+    stats = mm.mm_server_get_stats(srv)
+    ev_per_req = np.array([window_events(r) for r in reqs[:500]])
+    lat = np.array([c["t_done"] - c["t_submit"] for c in lat_done]) * 1e3
+    svc = np.array([c["t_done"] - c["t_start"] for c in lat_done]) * 1e3
+    mm.mm_server_destroy(srv)
+    line = {
+        "metric": METRIC, "value": float(ev_per_req.mean()) * len(done) / wall, "unit": "events/s",
+        "n_gpus": 1, "steps": len(reqs), "warmup": 16, "ms_per_step": 1e3 * wall / len(reqs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (one day of factor-GBM prices, U-shaped Poisson arrivals, 1-s grid)",
+        "config": {"workload": ev.meta["workload"], "D": ev.D, "events": ev.n_events, "requests": len(reqs),
+                   "N_max": Nmax, "kernel": "es", "tol": 1e-6, "basis": "fejer", "contraction": args.prec,
+                   "slots": stats["slots"], "slot_bytes": stats["slot_bytes"], "hbm_budget_gb": args.hbm_budget_gb,
+                   "l2": "window events of a request exceed L2 on average (no flush)"},
+        "requests_per_s": thr,
+        "matrices_per_s": thr,
+        "requests_ok": len(ok),
+        "mean_events_per_request": float(ev_per_req.mean()),
+        "latency_ms": {"offered_load": args.load, "requests": len(lat), "p50": float(np.percentile(lat, 50)),
+                       "p99": float(np.percentile(lat, 99)), "service_p50": float(np.percentile(svc, 50)),
+                       "service_p99": float(np.percentile(svc, 99))},
+        "peak_inflight": stats["peak_inflight"],
+        "clocks": clocks,
+        "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -407,6 +505,10 @@ def main():
         return
     if args.workload == "c4":
         bench_batch(args)
+        return
+    if args.workload == "c5":
+        if int(os.environ.get("RANK", "0")) == 0:
+            bench_serve(args)
         return
     import torch
     import torch.distributed as dist
