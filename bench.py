@@ -33,7 +33,13 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # dram bytes (read + write) per launch of the dominant kernel, from the ncu
 # capture summarised in profiles/ (None until a capture of the current kernel)
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/c3_block_D100_N10000_kernels_ncu.md (default configuration)
+    ("spread", "c3", "bf16x3", "es"): 9217536,
+    ("fft", "c3", "bf16x3", "es"): 16519424,
+    ("prep", "c3", "bf16x3", "es"): 12272896,
+    ("gram", "c3", "bf16x3", "es"): 8135680,
+}
 
 
 def parse():
@@ -55,7 +61,10 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison path")
     ap.add_argument("--spread-algo", default="default", choices=["default", "scatter", "gather", "fused"])
-    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default configuration")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time the library's spreading / FFT variants on this workload first and keep the fastest "
+                         "(off by default: the default configuration is deterministic, so a profiler run of the "
+                         "same command launches the same kernels)")
     return ap.parse_args()
 
 
@@ -240,7 +249,7 @@ def bench_batch(args):
     b = mm.mm_batch_create(reps, Dg, Nmax, ev.n_events, tol=1e-6, kernel=args.kernel, basis="dirichlet",
                            prec=args.prec)
     tuned = None
-    if not args.no_autotune:
+    if args.autotune:
         tuned = mm.mm_batch_autotune(b, off, tt, lp, Nmax, reps=2)
     S = torch.empty((reps, J, Dg, Dg), dtype=torch.float32, device=dev)
     R = torch.empty_like(S)
@@ -546,7 +555,7 @@ def main():
     # autotune stages (a)-(c) on this workload (kept in the plan), then the
     # first call builds the per-cutoff tables; then check the status
     tuned = None
-    if not args.no_autotune and args.spread_algo == "default":
+    if args.autotune and args.spread_algo == "default":
         tuned = mm.mm_autotune(plan, off, tt, lp, N, coeffs=coef, reps=3)
     step()
     st = mm.mm_plan_sync(plan)

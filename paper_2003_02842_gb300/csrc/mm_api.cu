@@ -178,6 +178,8 @@ struct mm_plan_s {
   void* W = nullptr;
   void* atw = nullptr;            // per-asset FFT pass twiddles (mixed path)
   int64_t atw_cap = 0;            // entries allocated
+  int atw_n = -1, atw_npass = -1;  // plan the twiddles were built for
+  int atw_rad[kMaxAssetPasses] = {};
   void* U = nullptr;
   void* decon = nullptr;
   double* glx = nullptr;
@@ -351,7 +353,8 @@ mm_status configure(mm_plan p, int N) {
   s.kernel = p->desc.kernel;
   s.max_events = p->desc.max_events;
   const int tmax = spread_max_tile(p->fp64);
-  int tile = p->desc.spread_tile > 0 ? std::min(p->desc.spread_tile, tmax) : tmax;
+  // default tile: half the largest in float32 (measured faster on GB300), the largest in float64
+  int tile = p->desc.spread_tile > 0 ? std::min(p->desc.spread_tile, tmax) : (p->fp64 ? tmax : tmax / 2);
   if (p->tune_tile > 0) tile = std::min(p->tune_tile, tmax);
   if (Mr <= (int64_t)tile) {
     tile = (int)Mr;
@@ -405,12 +408,22 @@ mm_status ensure_tables(mm_plan p, int N, cudaStream_t st) {
   StageScope sc(p, MM_STAGE_SETUP, st);
   MM_CUDA(launch_setup_tables(p->desc.kernel, p->msp, p->Mr, N, p->fft.n, p->sp, p->tau, p->glx, p->glw, kGlNodes,
                               p->W, p->U, p->decon, p->fp64, st));
-  if (!p->fp64 && p->afft.npass > 0 && asset_twiddle_count(p->afft) <= p->atw_cap) {
-    p->launches += 1;
-    p->nl[MM_STAGE_SETUP] += 1;
-    MM_CUDA(launch_asset_twiddles(p->afft, p->atw, st));
-  }
   p->tab_N = N;
+  return MM_OK;
+}
+
+// Pass twiddles of the per-asset FFT plan in use (rebuilt when the plan changes).
+mm_status ensure_asset_twiddles(mm_plan p, cudaStream_t st) {
+  const AssetFft& f = p->afft;
+  if (p->fp64 || f.npass == 0 || asset_twiddle_count(f) > p->atw_cap) return MM_OK;
+  const bool same = p->atw_n == f.nl && p->atw_npass == f.npass &&
+                    std::equal(f.rad, f.rad + kMaxAssetPasses, p->atw_rad);
+  if (same) return MM_OK;
+  StageScope sc(p, MM_STAGE_SETUP, st);
+  MM_CUDA(launch_asset_twiddles(f, p->atw, st));
+  p->atw_n = f.nl;
+  p->atw_npass = f.npass;
+  std::copy(f.rad, f.rad + kMaxAssetPasses, p->atw_rad);
   return MM_OK;
 }
 
@@ -477,6 +490,8 @@ mm_status coeffs_impl(mm_plan p, const int64_t* off, const double* t, const doub
   mm_status r = configure(p, N);
   if (r != MM_OK) return r;
   r = ensure_tables(p, N, st);
+  if (r != MM_OK) return r;
+  r = ensure_asset_twiddles(p, st);
   if (r != MM_OK) return r;
   if (p->sp.fused) {
     StageScope sc(p, MM_STAGE_FUSED, st);
@@ -844,7 +859,6 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
     p->tune_split = c.split;
     p->tune_maxr = c.maxr;
     p->cfg_N = -1;  // force reconfiguration
-    p->tab_N = -1;
     if (configure(p, N) != MM_OK) continue;
     if (c.algo == 2 && !p->sp.fused) continue;  // fused variant does not fit
     if (c.fft == 0 && (!p->use_afft || p->afft.split != c.split)) continue;  // not available
@@ -876,7 +890,6 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
     p->tune_split = saved.split;
     p->tune_maxr = saved.maxr;
     p->cfg_N = -1;
-    p->tab_N = -1;
     cudaGetLastError();
     return MM_ERR_CUDA;
   }
@@ -889,7 +902,6 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
   p->tune_maxr = bestc.maxr;
   p->tune_ms = best;
   p->cfg_N = -1;
-  p->tab_N = -1;
   return configure(p, N);
 }
 
