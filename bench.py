@@ -85,6 +85,21 @@ def workload(name, seed, reps=4096):
     return ev, N
 
 
+def reduce_over_ranks(times_ms, n_events, device):
+    """Weak scaling across ranks: the slowest rank's times (max) and the
+    events all ranks processed (sum). One all-reduce each over the process
+    group (NCCL on the GPUs, gloo in the CPU tests); identity for one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(times_ms), float(n_events)
+    t = torch.tensor(list(times_ms), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ne = torch.tensor([float(n_events)], dtype=torch.float64, device=device)
+    dist.all_reduce(ne, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t], float(ne[0])
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -350,14 +365,7 @@ def bench_batch(args):
                 "replications_sampled": len(sample), "max_abs_dcorr": worst}
         mm.mm_destroy(p64)
 
-    n_total = float(ev.n_events)
-    if world > 1:
-        t_ = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t_, op=dist.ReduceOp.MAX)
-        total_ms = float(t_.item())
-        ne = torch.tensor([n_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(ne)
-        n_total = float(ne[0])
+    (total_ms,), n_total = reduce_over_ranks([total_ms], ev.n_events, dev)
     if rank == 0:
         peaks, peak_src = load_peaks()
         stage_ms = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in stages.items()}
@@ -646,16 +654,8 @@ def main():
                 "max_abs_dcorr": dR, "max_rel_l2_dcoef": dF}
         mm.mm_destroy(p64)
 
-    # max over ranks
-    t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms, e2e_ms = float(t[0]), float(t[1])
-    n_total = ev.n_events * world  # replicas are equal in size up to the Poisson draw
-    if world > 1:
-        ne = torch.tensor([float(ev.n_events)], dtype=torch.float64, device=dev)
-        dist.all_reduce(ne, op=dist.ReduceOp.SUM)
-        n_total = float(ne[0])
+    # max over ranks of the times, sum over ranks of the events
+    (total_ms, e2e_ms), n_total = reduce_over_ranks([total_ms, e2e_ms], ev.n_events, dev)
 
     if rank == 0:
         ms_step = total_ms / args.steps
