@@ -102,8 +102,10 @@ typedef struct {
   int32_t spread_algo;  /* 0 library default (= 1 unless mm_autotune chose otherwise);
                            1 separate prep / scatter-into-tile / FFT kernels; 2 as 1
                            with a gather per grid cell; 3 stages (a)-(c) fused in one
-                           CTA per asset when the grid fits in shared memory, else 1.
-                           All compute Eq. (12) exactly. */
+                           CTA per asset when the grid fits in shared memory, else 1;
+                           4 as 1 with the kernel evaluated directly per tap and float
+                           accumulation (the mixed-path default 1 uses per-tap
+                           polynomials and integer accumulation). All compute Eq. (12). */
   int32_t fft_algo;     /* stages (b)-(c) in the mixed precisions: 0 library default
                            (one CTA per asset with the grid in shared memory when it
                            fits, else 1); 1 two-pass FFT through global memory. The
@@ -136,6 +138,8 @@ typedef struct {
   int32_t fft_passes;    /* per-asset FFT: number of radix passes (0 when not in use) */
   int32_t fft_radix[4];  /* per-asset FFT: radix of each pass */
   int32_t fft_split;     /* per-asset FFT: CTAs per asset (1 or 2; 0 when not in use) */
+  int32_t spread_poly;   /* 1: float32 spreading evaluates the kernel as per-tap polynomials
+                            (error <= max(3e-7, tol/10)) and accumulates exactly in integers */
 } mm_plan_info;
 
 /* Create a plan: validates desc, allocates the workspace on the current

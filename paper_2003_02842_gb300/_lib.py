@@ -21,7 +21,7 @@ STATUS_NAMES = {
 KERNELS = {"gauss": 0, "kb": 1, "es": 2}
 BASES = {"dirichlet": 0, "fejer": 1}
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "3xtf32": 2}
-SPREAD_ALGOS = {"default": 0, "scatter": 1, "gather": 2, "fused": 3}
+SPREAD_ALGOS = {"default": 0, "scatter": 1, "gather": 2, "fused": 3, "scatter_direct": 4}
 FFT_ALGOS = {"default": 0, "two_pass": 1}
 STAGES = ["prep", "spread", "fft_cols", "fft_rows", "gram", "reduce", "setup", "fused", "fft"]
 
@@ -61,6 +61,7 @@ class PlanInfo(ctypes.Structure):
         ("fft_passes", ctypes.c_int32),
         ("fft_radix", ctypes.c_int32 * 4),
         ("fft_split", ctypes.c_int32),
+        ("spread_poly", ctypes.c_int32),
     ]
 
 

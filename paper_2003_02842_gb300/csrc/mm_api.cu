@@ -133,6 +133,63 @@ bool plan_asset_fft(int64_t n, int split, int N, int maxr, AssetFft* out) {
 // Twiddle entries (complex) of an asset FFT plan: four anchors per row.
 int64_t asset_twiddle_count(const AssetFft& f) { return 4 * (int64_t)f.tw_rows; }
 
+// The averaging kernel at signed distance x (grid cells) as the device
+// evaluates it (Eqs. (5), (7), (9) with the plan's constants), in float64.
+double kernel_at(const SpreadParams& s, double x) {
+  if (s.kernel == MM_KERNEL_GAUSS) return exp(-s.g_t1 * x * x);
+  if (s.kernel == MM_KERNEL_ES) {
+    const double y = x * s.es_inv_w, v = 1.0 - y * y;
+    return v >= 0.0 ? exp(s.es_beta * (sqrt(v) - 1.0)) : 0.0;
+  }
+  const double b = s.kb_b, ck = s.kb_inv_phi0 / kPi;
+  const double s2 = (double)s.msp * s.msp - x * x;
+  if (s2 > 0.0) return sinh(b * sqrt(s2)) / sqrt(s2) * ck;
+  if (s2 < 0.0) return sin(b * sqrt(-s2)) / sqrt(-s2) * ck;
+  return b * ck;
+}
+
+// Per-tap polynomials of the float32 spreading kernel: Chebyshev
+// interpolation of phi(k - d), d in [0, 1], at kPolyDeg + 1 nodes, rewritten
+// in powers of z = d - 1/2 and rounded to float32. Returns the largest error
+// of the float32 Horner evaluation over a fine sample of d.
+double fit_kernel_poly(const SpreadParams& s, KernelPoly* out) {
+  constexpr int n = kPolyDeg + 1;
+  memset(out, 0, sizeof(*out));
+  const int nt = s.khi - s.klo + 1;
+  if (nt > kPolyMaxTaps) return 1e300;
+  double tn[n], T[n][n];  // nodes; monomial coefficients of T_i in t
+  for (int m = 0; m < n; ++m) tn[m] = cos(kPi * (m + 0.5) / n);
+  memset(T, 0, sizeof(T));
+  T[0][0] = 1.0;
+  if (n > 1) T[1][1] = 1.0;
+  for (int i = 2; i < n; ++i)
+    for (int q = 0; q < n; ++q) T[i][q] = (q > 0 ? 2.0 * T[i - 1][q - 1] : 0.0) - T[i - 2][q];
+  double worst = 0.0;
+  for (int j = 0; j < nt; ++j) {
+    const int k = s.klo + j;
+    double y[n], a[n], mono[n];
+    for (int m = 0; m < n; ++m) y[m] = kernel_at(s, (double)k - (0.5 * tn[m] + 0.5));
+    for (int i = 0; i < n; ++i) {
+      double acc = 0.0;
+      for (int m = 0; m < n; ++m) acc += y[m] * cos(kPi * i * (m + 0.5) / n);
+      a[i] = (i == 0 ? 1.0 : 2.0) * acc / n;
+    }
+    for (int q = 0; q < n; ++q) {
+      mono[q] = 0.0;
+      for (int i = 0; i < n; ++i) mono[q] += a[i] * T[i][q];
+      out->c[j][q] = (float)(mono[q] * ldexp(1.0, q));  // t = 2z
+    }
+    for (int q = 0; q <= 128; ++q) {
+      const double d = q / 128.0;
+      const float z = (float)(d - 0.5);
+      float acc = out->c[j][n - 1];
+      for (int i = n - 2; i >= 0; --i) acc = fmaf(acc, z, out->c[j][i]);
+      worst = std::max(worst, fabs((double)acc - kernel_at(s, (double)k - d)));
+    }
+  }
+  return worst;
+}
+
 // M_sp rules of Sec. 2.2.5 (sigma = 2).
 int msp_rule(mm_kernel k, double eps) {
   const double sigma = 2.0;
@@ -222,6 +279,9 @@ struct mm_plan_s {
   double tau = 0;
   int w_N = -1, w_basis = -1;
   GramParams gram{};
+  KernelPoly poly{};
+  bool poly_ok = false;   // float32 spreading with polynomial taps and integer accumulation
+  int tune_poly = -1;     // autotuner override: 0 off
   cudaStream_t last = nullptr;
   // instrumentation
   bool prof = false;
@@ -362,6 +422,7 @@ mm_status configure(mm_plan p, int N) {
   }
   const bool fits = fused_smem(f, Mr, p->fp64) + 2048 <= (size_t)p->smem_optin;
   int algo = p->desc.spread_algo == 2 ? 1 : (p->desc.spread_algo == 3 ? 2 : 0);
+  const bool direct_taps = p->desc.spread_algo == 4;  // scatter evaluating the kernel directly
   if (p->tune_algo >= 0) algo = p->tune_algo;
   if (algo == 2 && (!fits || p->G > 1)) algo = 0;
   s.algo = algo == 1 ? 1 : 0;
@@ -375,6 +436,13 @@ mm_status configure(mm_plan p, int N) {
   s.kb_b = kPi * (2.0 - 1.0 / sigma);
   s.kb_inv_phi0 = kPi * p->msp / sinh(s.kb_b * p->msp);
   p->tau = kPi * lam / ((double)Mr * (double)Mr);
+  p->poly_ok = false;
+  if (!p->fp64 && s.algo == 0 && !s.fused && p->tune_poly != 0 && !direct_taps &&
+      spread_poly_supported(s.khi - s.klo + 1)) {
+    // the fit must stay far below the NUFFT tolerance and near float32 rounding
+    const double err = fit_kernel_poly(s, &p->poly);
+    p->poly_ok = err <= std::max(3.0e-7, 0.1 * p->desc.tol);
+  }
   // per-asset FFT: mixed path, the complex grid fits in shared memory and n
   // factors into at most kMaxAssetPasses compiled radices
   AssetFft af{};
@@ -516,6 +584,9 @@ mm_status coeffs_impl(mm_plan p, const int64_t* off, const double* t, const doub
       StageScope sc(p, MM_STAGE_SPREAD, st);
       if (p->fp64)
         MM_CUDA(launch_spread_f64(off, p->rec_b0, p->rec_d, p->rec_v, p->sp, (double*)p->grid, p->status, st));
+      else if (p->poly_ok)
+        MM_CUDA(launch_spread_poly(off, p->rec_b0, p->rec_d, p->rec_v, p->sp, p->poly, (float*)p->grid, p->status,
+                                   st));
       else
         MM_CUDA(launch_spread_f32(off, p->rec_b0, p->rec_d, p->rec_v, p->sp, (float*)p->grid, p->status, st));
     }
@@ -633,7 +704,7 @@ mm_status plan_create_impl(const mm_plan_desc* desc, int gsize, bool batch, mm_p
   if (d.basis < MM_BASIS_DIRICHLET || d.basis > MM_BASIS_FEJER) return MM_ERR_INVALID_ARG;
   if (d.prec < MM_PREC_FP64 || d.prec > MM_PREC_MIXED_3XTF32) return MM_ERR_INVALID_ARG;
   if (d.spread_tile < 0 || d.spread_tile > 50000) return MM_ERR_INVALID_ARG;
-  if (d.spread_algo < 0 || d.spread_algo > 3) return MM_ERR_INVALID_ARG;
+  if (d.spread_algo < 0 || d.spread_algo > 4) return MM_ERR_INVALID_ARG;
   if (d.fft_algo < 0 || d.fft_algo > 1) return MM_ERR_INVALID_ARG;
   for (int i = 0; i < 4; ++i)
     if (d.reserved[i] != 0) return MM_ERR_INVALID_ARG;
@@ -827,14 +898,15 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
   cudaStream_t st = (cudaStream_t)stream;
   const bool prof = p->prof;
   p->prof = false;
-  struct Cand { int algo, tile, lgc, rb, fft, split, maxr; };
+  struct Cand { int algo, tile, lgc, rb, fft, split, maxr, poly = 1; };
   std::vector<Cand> cands;
   const int tmax = spread_max_tile(p->fp64);
   if (!p->fp64) {
     for (int split : {1, 2})
       for (int maxr : {16, 32}) {
-        for (int tile : {tmax / 4, tmax / 2, tmax}) cands.push_back({0, tile, -1, -1, 0, split, maxr});
-        for (int tile : {tmax / 2, tmax}) cands.push_back({1, tile, -1, -1, 0, split, maxr});
+        for (int tile : {tmax / 4, tmax / 2, tmax}) cands.push_back({0, tile, -1, -1, 0, split, maxr, 1});
+        for (int tile : {tmax / 4, tmax / 2}) cands.push_back({0, tile, -1, -1, 0, split, maxr, 0});
+        for (int tile : {tmax / 2, tmax}) cands.push_back({1, tile, -1, -1, 0, split, maxr, 1});
       }
   }
   for (int tile : {tmax / 4, tmax / 2, tmax})
@@ -847,9 +919,9 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
   MM_CUDA(cudaEventCreate(&e0));
   MM_CUDA(cudaEventCreate(&e1));
   float best = 3.0e38f;
-  Cand bestc{-1, -1, -1, -1, -1, -1, -1};
+  Cand bestc{-1, -1, -1, -1, -1, -1, -1, -1};
   const Cand saved{p->tune_algo, p->tune_tile, p->tune_lgcols, p->tune_rowblk, p->tune_fft, p->tune_split,
-                   p->tune_maxr};
+                   p->tune_maxr, p->tune_poly};
   for (const Cand& c : cands) {
     p->tune_algo = c.algo;
     p->tune_tile = c.tile;
@@ -858,6 +930,7 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
     p->tune_fft = c.fft;
     p->tune_split = c.split;
     p->tune_maxr = c.maxr;
+    p->tune_poly = c.poly;
     p->cfg_N = -1;  // force reconfiguration
     if (configure(p, N) != MM_OK) continue;
     if (c.algo == 2 && !p->sp.fused) continue;  // fused variant does not fit
@@ -889,6 +962,7 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
     p->tune_fft = saved.fft;
     p->tune_split = saved.split;
     p->tune_maxr = saved.maxr;
+    p->tune_poly = saved.poly;
     p->cfg_N = -1;
     cudaGetLastError();
     return MM_ERR_CUDA;
@@ -900,6 +974,7 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
   p->tune_fft = bestc.fft;
   p->tune_split = bestc.split;
   p->tune_maxr = bestc.maxr;
+  p->tune_poly = bestc.poly;
   p->tune_ms = best;
   p->cfg_N = -1;
   return configure(p, N);
@@ -957,6 +1032,7 @@ mm_status mm_plan_get_info(mm_plan p, mm_plan_info* info) {
   info->launches = p->launches;
   info->gram_splits = p->gram.splits;
   info->spread_algo = p->sp.fused ? 3 : (p->sp.algo == 1 ? 2 : 1);
+  info->spread_poly = p->poly_ok ? 1 : 0;
   info->spread_tile = p->sp.tile;
   info->fft_lg_cols = p->fft.lg_cols;
   info->fft_rowblk = p->fft.rowblk;

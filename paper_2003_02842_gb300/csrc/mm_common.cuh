@@ -68,6 +68,16 @@ struct SpreadParams {
   int64_t max_events;
 };
 
+// Averaging kernel of the float32 path as one polynomial per stencil tap:
+// phi(k - d) ~ sum_i c[j][i] (d - 1/2)^i for tap k = klo + j and d in [0, 1),
+// fitted on the host (Chebyshev interpolation, float64) for the plan's
+// kernel, M_sp and sigma; evaluated by Horner's rule on the FMA pipe.
+constexpr int kPolyDeg = 8;
+constexpr int kPolyMaxTaps = 32;
+struct KernelPoly {
+  float c[kPolyMaxTaps][kPolyDeg + 1];
+};
+
 // Rescaling of Algorithm 4 in exact fixed point, written by k_bounds for the
 // current call: t_fix = trunc(t * 2^F) (int64, |t| < 2^(62-F)); the cell
 // coordinate u = (t - t0) M_r / span is u_fix = ((t_fix - t0_fix) * S) >> sh
@@ -148,6 +158,13 @@ cudaError_t launch_prep_f64(const int64_t* off, const double* t, const double* l
                             void* rd, void* rv, int* status, cudaStream_t s);
 cudaError_t launch_spread_f32(const int64_t* off, const int* rb0, const void* rd, const void* rv,
                               const SpreadParams& p, float* grid, const int* status, cudaStream_t s);
+// float32 scatter with the polynomial taps and int32 fixed-point shared
+// accumulation (per-tile power-of-two scale); false if the tap count has no
+// instantiation
+bool spread_poly_supported(int ntaps);
+cudaError_t launch_spread_poly(const int64_t* off, const int* rb0, const void* rd, const void* rv,
+                               const SpreadParams& p, const KernelPoly& poly, float* grid, const int* status,
+                               cudaStream_t s);
 cudaError_t launch_spread_f64(const int64_t* off, const int* rb0, const void* rd, const void* rv,
                               const SpreadParams& p, double* grid, const int* status, cudaStream_t s);
 

@@ -536,6 +536,145 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_scatter(const int64_t
   }
 }
 
+// Float32 scatter with polynomial taps and exact integer accumulation.
+// Float atomics in shared memory run as compare-and-swap loops; integer ones
+// are native. Each tile therefore accumulates round(v phi 2^e) in int32 with
+// 2^e the largest power of two for which 2^e sum|v| over the tile's events
+// stays below 2^30: no cell can overflow (|phi| <= 1 + 1e-6), the sums are
+// exact and independent of the order of the atomics, and a cell is off by at
+// most half a unit (2^-e-1) per tap -- below float32 rounding of the cell
+// for the event densities of these workloads.
+template <int NT>
+__global__ void __launch_bounds__(kSpreadThreads) k_spread_poly(const int64_t* __restrict__ off,
+                                                               const int* __restrict__ rb0,
+                                                               const float* __restrict__ rd,
+                                                               const float* __restrict__ rv,
+                                                               const int* __restrict__ gate, SpreadParams p,
+                                                               KernelPoly poly, float* __restrict__ grid) {
+  constexpr int EC = EvChunk<float>::n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int* ev_p = reinterpret_cast<int*>(smem_raw);
+  float* ev_d = reinterpret_cast<float*>(smem_raw + EC * sizeof(int));
+  float* ev_v = ev_d + EC;
+  int* tile = reinterpret_cast<int*>(ev_v + EC);
+  __shared__ float s_part[kSpreadThreads / 32];
+  if (*gate) return;  // uniform: the whole block leaves
+  const int a = blockIdx.y;
+  const int64_t L = (int64_t)blockIdx.x * p.tile;
+  const int Tlen = (int)min((int64_t)p.tile, p.Mr - L);
+  {
+    int4* t4 = reinterpret_cast<int4*>(tile);
+    const int n4 = (Tlen + 3) / 4;
+    for (int c = threadIdx.x; c < n4; c += kSpreadThreads) t4[c] = make_int4(0, 0, 0, 0);
+  }
+  TileRanges tr;
+  tile_ranges(off, rb0, p, a, L, Tlen, tr);
+  const int64_t ntot = tr.n2 + tr.n1 + tr.n0;
+  const int klo = p.klo;
+  // the tile's scale: sum |v| over its records (staged with the first chunk
+  // when one chunk holds them all, else a pass over the returns)
+  float part = 0.f;
+  const int n_first = (int)min((int64_t)EC, ntot);
+  for (int i = threadIdx.x; i < n_first; i += kSpreadThreads) {
+    load_record<float>(rb0, rd, rv, p, tr, L, i, ev_p[i], ev_d[i], ev_v[i]);
+    part += fabsf(ev_v[i]);
+  }
+  for (int64_t i = EC + threadIdx.x; i < ntot; i += kSpreadThreads) {
+    int pp;
+    float dd, vv;
+    load_record<float>(rb0, rd, rv, p, tr, L, i, pp, dd, vv);
+    part += fabsf(vv);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = part;
+  __syncthreads();
+  float B = 0.f;
+#pragma unroll
+  for (int w = 0; w < kSpreadThreads / 32; ++w) B += s_part[w];
+  int ex = 0;
+  if (B > 0.f && B < 3.0e38f) frexpf(B, &ex);  // B < 2^ex
+  const int e = B > 0.f ? 30 - ex : 0;         // 2^e B < 2^30
+  const float scale = ldexpf(1.0f, e), inv = ldexpf(1.0f, -e);
+  for (int64_t cs = 0; cs < ntot; cs += EC) {
+    const int n = (int)min((int64_t)EC, ntot - cs);
+    if (cs > 0) {
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += kSpreadThreads)
+        load_record<float>(rb0, rd, rv, p, tr, L, cs + i, ev_p[i], ev_d[i], ev_v[i]);
+    }
+    __syncthreads();
+    for (int ei = threadIdx.x; ei < n; ei += kSpreadThreads) {
+      const int pe = ev_p[ei];
+      if (pe == kNoCell) continue;
+      const float z = ev_d[ei] - 0.5f;
+      const float vs = ev_v[ei] * scale;
+      float w[NT];
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        float acc = poly.c[j][kPolyDeg];
+#pragma unroll
+        for (int i = kPolyDeg - 1; i >= 0; --i) acc = fmaf(acc, z, poly.c[j][i]);
+        w[j] = acc;
+      }
+      const int c0 = pe + klo;
+      if (c0 >= 0 && c0 + NT <= Tlen) {
+#pragma unroll
+        for (int j = 0; j < NT; ++j) atomicAdd(tile + c0 + j, __float2int_rn(vs * w[j]));
+      } else {
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+          const unsigned c = (unsigned)(c0 + j);
+          if (c < (unsigned)Tlen) atomicAdd(tile + c, __float2int_rn(vs * w[j]));
+        }
+      }
+    }
+  }
+  __syncthreads();
+  float* g = grid + (int64_t)a * p.Mr + L;
+  if (((reinterpret_cast<uintptr_t>(g) & 15) == 0) && (Tlen & 3) == 0) {
+    const int4* t4 = reinterpret_cast<const int4*>(tile);
+    float4* g4 = reinterpret_cast<float4*>(g);
+    for (int c = threadIdx.x; c < Tlen / 4; c += kSpreadThreads) {
+      const int4 q = t4[c];
+      g4[c] = make_float4((float)q.x * inv, (float)q.y * inv, (float)q.z * inv, (float)q.w * inv);
+    }
+  } else {
+    for (int c = threadIdx.x; c < Tlen; c += kSpreadThreads) g[c] = (float)tile[c] * inv;
+  }
+}
+
+bool spread_poly_supported(int ntaps) {
+  return ntaps == 9 || ntaps == 13 || ntaps == 14 || (ntaps >= 1 && ntaps <= kPolyMaxTaps);
+}
+
+cudaError_t launch_spread_poly(const int64_t* off, const int* rb0, const void* rd, const void* rv,
+                               const SpreadParams& p, const KernelPoly& poly, float* grid, const int* status,
+                               cudaStream_t s) {
+  if (p.tile > spread_max_tile(false)) return cudaErrorInvalidValue;
+  const int nt = p.khi - p.klo + 1;
+  const size_t smem = (size_t)EvChunk<float>::n * (sizeof(int) + 2 * sizeof(float)) + ((size_t)p.tile + 3) / 4 * 16;
+  dim3 grd(p.ntiles, p.D);
+  auto go = [&](auto fn) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fn<<<grd, kSpreadThreads, smem, s>>>(off, rb0, (const float*)rd, (const float*)rv, status + 1, p, poly, grid);
+    return cudaGetLastError();
+  };
+  switch (nt) {
+    case 9: return go(k_spread_poly<9>);
+    case 13: return go(k_spread_poly<13>);
+    case 14: return go(k_spread_poly<14>);
+    default: break;
+  }
+  // other tap counts: the next instantiation up, padded with zero taps
+  if (nt <= 8) return go(k_spread_poly<8>);
+  if (nt <= 16) return go(k_spread_poly<16>);
+  if (nt <= 24) return go(k_spread_poly<24>);
+  if (nt <= 32) return go(k_spread_poly<32>);
+  return cudaErrorInvalidValue;
+}
+
 template <typename T, int K>
 static cudaError_t launch_variant(bool gather, int nk, dim3 grd, const int64_t* off, const int* rb0, const T* rd,
                                   const T* rv, const int* gate, const SpreadParams& p, T* grid, cudaStream_t s) {

@@ -46,6 +46,19 @@ WORKLOADS = {
 }
 
 
+@pytest.mark.parametrize("tol", [1e-2, 1e-4, 1e-9, 1e-12])
+@pytest.mark.parametrize("kernel", ["gauss", "kb", "es"])
+def test_polynomial_taps_across_tolerances(kernel, tol):
+    # the float32 spreading's per-tap polynomials for every kernel width the
+    # tolerance rule gives, against the direct sum at the float32 bound
+    ev = synth.c2_async(6)
+    N = ev.meta["N"]
+    out = run(dict(tol=tol, kernel=kernel, basis="dirichlet", prec="bf16x3", spread_algo="scatter"), ev, N)
+    assert out["info"]["spread_poly"] == 1
+    ref = oracle.coeffs_F(ev.offsets, ev.t, ev.logp, N)
+    assert np.all(rel_l2_rows(out["F"], ref) <= max(1e-5, 10 * tol))
+
+
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 @pytest.mark.parametrize("kernel", ["gauss", "kb", "es"])
 @pytest.mark.parametrize("wl", list(WORKLOADS))
@@ -83,7 +96,7 @@ def test_covariance_and_correlation(prec, basis, wl):
     assert np.array_equal(S, S.T) and np.array_equal(R, R.T, equal_nan=True)
 
 
-@pytest.mark.parametrize("algo", ["scatter", "gather"])
+@pytest.mark.parametrize("algo", ["scatter", "gather", "scatter_direct"])
 @pytest.mark.parametrize("tile", [64, 257, 1000, 0])
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 def test_many_tiles_and_periodic_halos(tile, prec, algo):
@@ -96,6 +109,7 @@ def test_many_tiles_and_periodic_halos(tile, prec, algo):
         out = run(dict(tol=tl["tol"], kernel=kernel, basis="dirichlet", prec=prec, spread_tile=tile,
                        spread_algo=algo), ev, N)
         assert out["status"] == 0
+        assert out["info"]["spread_poly"] == (1 if (prec != "fp64" and algo == "scatter") else 0)
         ref = oracle.coeffs_F(ev.offsets, ev.t, ev.logp, N)
         assert np.all(rel_l2_rows(out["F"], ref) <= tl["coef"])
 
