@@ -107,9 +107,15 @@ typedef struct {
                            accumulation (the mixed-path default 1 uses per-tap
                            polynomials and integer accumulation). All compute Eq. (12). */
   int32_t fft_algo;     /* stages (b)-(c) in the mixed precisions: 0 library default
-                           (one CTA per asset with the grid in shared memory when it
-                           fits, else 1); 1 two-pass FFT through global memory. The
-                           FP64 path always uses 1. Both compute Eqs. (13)-(14). */
+                           (the grid in shared memory when it fits, as 4 for fewer
+                           assets than SMs else 2; otherwise 1); 1 two-pass FFT through
+                           global memory; 2 one CTA per asset; 3 two CTAs per asset
+                           (radix-2 step on load); 4 a cluster of two CTAs per asset
+                           (decimation in time by 2, halves joined through distributed
+                           shared memory); 5 as 2 with the polynomial scatter storing
+                           the grid in the FFT's digit-reversed input order (one bulk
+                           copy per row). The FP64 path always uses 1. All compute
+                           Eqs. (13)-(14). */
   int32_t reserved[4];  /* must be zero */
 } mm_plan_desc;
 
@@ -137,7 +143,9 @@ typedef struct {
   int32_t fft_algo;      /* stages (b)-(c) in use: 0 per-asset shared-memory FFT, 1 two-pass */
   int32_t fft_passes;    /* per-asset FFT: number of radix passes (0 when not in use) */
   int32_t fft_radix[4];  /* per-asset FFT: radix of each pass */
-  int32_t fft_split;     /* per-asset FFT: CTAs per asset (1 or 2; 0 when not in use) */
+  int32_t fft_split;     /* per-asset FFT: 1 one CTA per asset, 2 two CTAs (radix-2 step on
+                            load), 3 a cluster of two CTAs joined through distributed shared
+                            memory; 0 when not in use */
   int32_t spread_poly;   /* 1: float32 spreading evaluates the kernel as per-tap polynomials
                             (error <= max(3e-7, tol/10)) and accumulates exactly in integers */
 } mm_plan_info;

@@ -249,6 +249,7 @@ struct mm_plan_s {
   void* partial = nullptr;        // FP64 path: per-split partial tiles
   size_t partial_bytes = 0;
   float* acc[2] = {nullptr, nullptr};  // mixed path: FP32 accumulators, used alternately
+  int* gram_done = nullptr;       // contraction CTAs finished (the last one runs the epilogue)
   int acc_sel = 0;
   bool acc_dirty = true;          // clear both before the next contraction
   int acc_D = -1;                 // D whose D x Dp region the last epilogue cleared
@@ -271,6 +272,7 @@ struct mm_plan_s {
   int tune_fft = -1;      // 0 per-asset shared-memory FFT, 1 two-pass FFT
   int tune_split = -1;    // per-asset FFT: CTAs per asset (1 or 2)
   int tune_maxr = -1;     // per-asset FFT: largest radix (16 or 32)
+  int tune_perm = -1;     // 1: the scatter stores the grid in the FFT's input order (split 1)
   int64_t Mr = 0;
   FftParams fft{};
   AssetFft afft{};
@@ -313,7 +315,7 @@ mm_status dalloc(mm_plan p, void** ptr, size_t bytes) {
 
 void free_all(mm_plan p) {
   void* ptrs[] = {p->grid, p->rec_b0, p->rec_d, p->rec_v, p->W, p->atw, p->U, p->decon, p->glx, p->glw, p->bounds, p->gscale, p->status, p->gapbits, p->wsq,
-                  p->partial, p->acc[0], p->acc[1], p->s_off, p->s_t, p->s_p, p->s_coef, p->s_sigma, p->s_R};
+                  p->partial, p->acc[0], p->acc[1], p->gram_done, p->s_off, p->s_t, p->s_p, p->s_coef, p->s_sigma, p->s_R};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& e : p->pending) {
@@ -446,21 +448,54 @@ mm_status configure(mm_plan p, int N) {
   // per-asset FFT: mixed path, the complex grid fits in shared memory and n
   // factors into at most kMaxAssetPasses compiled radices
   AssetFft af{};
-  int split = p->D < kSMs ? 2 : 1;  // fewer assets than SMs: two CTAs per asset
-  if (p->tune_split == 1 || p->tune_split == 2) split = p->tune_split;
+  // at most half as many assets as SMs: two CTAs per asset as a cluster
+  // (decimation in time by 2, joined through distributed shared memory);
+  // fewer assets than SMs: two CTAs per asset (radix-2 step on load);
+  // otherwise one CTA per asset
+  int split = p->D < kSMs ? 2 : 1;
+  int pair = 2 * p->D <= kSMs ? 1 : 0;
+  if (p->desc.fft_algo >= 2 && p->tune_split < 1) {  // the caller's choice of per-asset variant
+    split = (p->desc.fft_algo == 2 || p->desc.fft_algo == 5) ? 1 : 2;
+    pair = p->desc.fft_algo == 4 ? 1 : 0;
+  }
+  if (p->tune_split == 1 || p->tune_split == 2) {
+    split = p->tune_split;
+    pair = 0;
+  } else if (p->tune_split == 3) {
+    split = 2;
+    pair = 1;
+  }
   const int maxr = p->tune_maxr == 16 ? 16 : 32;
   auto fits_split = [&](int sp_) {
     return plan_asset_fft(n, sp_, N, maxr, &af) && asset_fft_smem(af) + 2048 <= (size_t)p->smem_optin &&
            asset_twiddle_count(af) <= p->atw_cap;
   };
   bool afft = !p->fp64 && fits_split(split);
-  if (!p->fp64 && !afft && p->tune_split != 1 && p->tune_split != 2) {
+  if (!p->fp64 && !afft && p->tune_split < 1 && p->desc.fft_algo < 2) {
     split = 3 - split;  // the other split (a large grid fits in shared memory only as two halves)
+    pair = split == 2 ? 1 : 0;
     afft = fits_split(split);
   }
-  int fft_algo = p->desc.fft_algo;
+  af.pair = afft && split == 2 ? pair : 0;
+  int fft_algo = p->desc.fft_algo == 1 ? 1 : 0;
   if (p->tune_fft >= 0) fft_algo = p->tune_fft == 0 ? 0 : 1;
   if (fft_algo == 1) afft = false;
+  // one CTA per asset after the polynomial scatter: the scatter stores the
+  // grid in the FFT's digit-reversed input order, so the FFT loads the row
+  // with one bulk copy
+  s.perm_np = 0;
+  af.pre_perm = 0;
+  const bool want_perm = p->tune_perm == 1 || (p->tune_perm < 0 && p->desc.fft_algo == 5);
+  if (afft && !s.fused && split == 1 && p->poly_ok && want_perm) {
+    af.pre_perm = 1;
+    s.perm_np = af.npass;
+    for (int q = 0; q < 4; ++q) {
+      const int R = q < af.npass ? af.rad[q] : 1;
+      s.perm_rad[q] = R;
+      s.perm_stride[q] = q < af.npass ? af.stride[q] : 0;
+      s.perm_magic[q] = R <= 1 ? 0u : 0xFFFFFFFFu / (unsigned)R + 1u;
+    }
+  }
   p->afft = af;
   p->use_afft = afft && !s.fused;
   p->fft = f;
@@ -644,12 +679,15 @@ mm_status corr_impl(mm_plan p, const void* coeffs, int N, void* sigma, void* R, 
     float* cur = p->acc[p->acc_sel];
     float* next = p->acc[p->acc_sel ^ 1];
     p->acc_dirty = true;  // until both launches below are queued
+    // few assets: the last contraction CTA writes Sigma and R itself (one
+    // launch less); beyond that the separate epilogue's parallelism wins
+    const bool fuse = g.D <= 32 && R;
     {
       StageScope sc(p, MM_STAGE_GRAM, st);
       MM_CUDA(launch_gram_tc(p->desc.prec == MM_PREC_MIXED_BF16X3 ? 0 : 1, coeffs, g, (const float*)p->wsq, cur,
-                             p->status, st));
+                             p->status, fuse ? p->gram_done : nullptr, (float*)sigma, (float*)R, next, st));
     }
-    {
+    if (!fuse) {
       StageScope sc(p, MM_STAGE_REDUCE, st);
       MM_CUDA(launch_corr_acc(cur, g, (float*)sigma, (float*)R, next, p->status, st));
     }
@@ -705,7 +743,7 @@ mm_status plan_create_impl(const mm_plan_desc* desc, int gsize, bool batch, mm_p
   if (d.prec < MM_PREC_FP64 || d.prec > MM_PREC_MIXED_3XTF32) return MM_ERR_INVALID_ARG;
   if (d.spread_tile < 0 || d.spread_tile > 50000) return MM_ERR_INVALID_ARG;
   if (d.spread_algo < 0 || d.spread_algo > 4) return MM_ERR_INVALID_ARG;
-  if (d.fft_algo < 0 || d.fft_algo > 1) return MM_ERR_INVALID_ARG;
+  if (d.fft_algo < 0 || d.fft_algo > 5) return MM_ERR_INVALID_ARG;
   for (int i = 0; i < 4; ++i)
     if (d.reserved[i] != 0) return MM_ERR_INVALID_ARG;
   const int msp = msp_rule(d.kernel, d.tol);
@@ -768,6 +806,7 @@ mm_status plan_create_impl(const mm_plan_desc* desc, int gsize, bool batch, mm_p
     } else {
       A((void**)&p->acc[0], D * (size_t)g.Dp * sizeof(float));
       A((void**)&p->acc[1], D * (size_t)g.Dp * sizeof(float));
+      A((void**)&p->gram_done, sizeof(int));
     }
   }
   if (d.max_events > 0 && !batch && staging) {
@@ -780,6 +819,7 @@ mm_status plan_create_impl(const mm_plan_desc* desc, int gsize, bool batch, mm_p
   }
   if (r == MM_OK) {
     if (cudaMemset(p->status, 0, 4 * sizeof(int)) != cudaSuccess) r = MM_ERR_CUDA;
+    if (p->gram_done && cudaMemset(p->gram_done, 0, sizeof(int)) != cudaSuccess) r = MM_ERR_CUDA;
   }
   if (r == MM_OK) {
     if (launch_gl_nodes(kGlNodes, p->glx, p->glw, 0) != cudaSuccess) r = MM_ERR_CUDA;
@@ -898,13 +938,14 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
   cudaStream_t st = (cudaStream_t)stream;
   const bool prof = p->prof;
   p->prof = false;
-  struct Cand { int algo, tile, lgc, rb, fft, split, maxr, poly = 1; };
+  struct Cand { int algo, tile, lgc, rb, fft, split, maxr, poly = 1, perm = -1; };
   std::vector<Cand> cands;
   const int tmax = spread_max_tile(p->fp64);
   if (!p->fp64) {
-    for (int split : {1, 2})
+    for (int split : {1, 2, 3})  // 3: two CTAs per asset as a cluster
       for (int maxr : {16, 32}) {
         for (int tile : {tmax / 4, tmax / 2, tmax}) cands.push_back({0, tile, -1, -1, 0, split, maxr, 1});
+        if (split == 1) cands.push_back({0, tmax / 2, -1, -1, 0, split, maxr, 1, 1});
         for (int tile : {tmax / 4, tmax / 2}) cands.push_back({0, tile, -1, -1, 0, split, maxr, 0});
         for (int tile : {tmax / 2, tmax}) cands.push_back({1, tile, -1, -1, 0, split, maxr, 1});
       }
@@ -919,9 +960,9 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
   MM_CUDA(cudaEventCreate(&e0));
   MM_CUDA(cudaEventCreate(&e1));
   float best = 3.0e38f;
-  Cand bestc{-1, -1, -1, -1, -1, -1, -1, -1};
+  Cand bestc{-1, -1, -1, -1, -1, -1, -1, -1, -1};
   const Cand saved{p->tune_algo, p->tune_tile, p->tune_lgcols, p->tune_rowblk, p->tune_fft, p->tune_split,
-                   p->tune_maxr, p->tune_poly};
+                   p->tune_maxr, p->tune_poly, p->tune_perm};
   for (const Cand& c : cands) {
     p->tune_algo = c.algo;
     p->tune_tile = c.tile;
@@ -931,10 +972,13 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
     p->tune_split = c.split;
     p->tune_maxr = c.maxr;
     p->tune_poly = c.poly;
+    p->tune_perm = c.perm;
     p->cfg_N = -1;  // force reconfiguration
     if (configure(p, N) != MM_OK) continue;
     if (c.algo == 2 && !p->sp.fused) continue;  // fused variant does not fit
-    if (c.fft == 0 && (!p->use_afft || p->afft.split != c.split)) continue;  // not available
+    if (c.fft == 0 && (!p->use_afft || p->afft.split != (c.split == 3 ? 2 : c.split) ||
+                       p->afft.pair != (c.split == 3 ? 1 : 0)))
+      continue;  // not available
     // warm-up (also builds the tables for N)
     if (coeffs_impl(p, d_offsets, d_t, d_logp, N, t0, t1, d_coeffs, nullptr, st) != MM_OK) continue;
     cudaEventRecord(e0, st);
@@ -963,6 +1007,7 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
     p->tune_split = saved.split;
     p->tune_maxr = saved.maxr;
     p->tune_poly = saved.poly;
+    p->tune_perm = saved.perm;
     p->cfg_N = -1;
     cudaGetLastError();
     return MM_ERR_CUDA;
@@ -975,6 +1020,7 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
   p->tune_split = bestc.split;
   p->tune_maxr = bestc.maxr;
   p->tune_poly = bestc.poly;
+  p->tune_perm = bestc.perm;
   p->tune_ms = best;
   p->cfg_N = -1;
   return configure(p, N);
@@ -1039,7 +1085,7 @@ mm_status mm_plan_get_info(mm_plan p, mm_plan_info* info) {
   info->tuned_ms = p->tune_ms;
   info->fft_algo = p->use_afft ? 0 : 1;
   info->fft_passes = p->use_afft ? p->afft.npass : 0;
-  info->fft_split = p->use_afft ? p->afft.split : 0;
+  info->fft_split = p->use_afft ? (p->afft.pair ? 3 : p->afft.split) : 0;
   for (int q = 0; q < 4; ++q) info->fft_radix[q] = p->use_afft && q < p->afft.npass ? p->afft.rad[q] : 0;
   return MM_OK;
 }

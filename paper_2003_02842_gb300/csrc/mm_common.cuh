@@ -59,6 +59,13 @@ struct SpreadParams {
   int single_tile;   // 1: one block covers the whole (small) grid
   int algo;          // 0: scatter into a shared-memory tile, 1: gather per cell
   int fused;         // 1: stages (a)-(c) in one CTA per asset (grid in shared memory)
+  // grid layout for the per-asset FFT: with perm_np > 0 the complex point m
+  // of an asset's grid row (cells 2m, 2m+1) is stored at its mixed-radix
+  // digit reversal sum_p q_p perm_stride[p], m = q_0 + rad_0 (q_1 + ...)
+  int perm_np;
+  int perm_rad[4];
+  int perm_stride[4];
+  unsigned perm_magic[4];  // exact-division multipliers of perm_rad
   // kernel constants
   double es_beta;    // ES: beta
   double es_inv_w;   // ES: 1 / M_sp  (support half-width in cells)
@@ -113,6 +120,8 @@ struct AssetFft {
   int n;
   int nl;
   int split;
+  int pair;     // split 2 as a cluster of two CTAs (decimation in time by 2)
+  int pre_perm; // split 1: the spread kernel stored the grid in digit-reversed order
   int N;
   int npass;
   int tw_rows;  // anchor rows over all passes
@@ -190,14 +199,15 @@ size_t asset_fft_smem(const AssetFft& f);
 int asset_fft_threads(int split);
 cudaError_t launch_asset_twiddles(const AssetFft& f, void* tw, cudaStream_t s);
 cudaError_t launch_fft_asset(const float* grid, const AssetFft& f, int D, const void* W, const void* tw,
-                             const void* U, const void* decon, void* coeffs, const int* status, cudaStream_t s);
+                             const void* U, const void* decon, void* coeffs, int* status, cudaStream_t s);
 size_t fft_rows_smem(const FftParams& f, bool fp64);
 
 cudaError_t launch_gram_weights(int basis, int N, bool fp64, void* wsq, cudaStream_t s);
 cudaError_t launch_gram_f64(const void* coeffs, const GramParams& g, const double* wsq,
                             double* partial, cudaStream_t s);
 cudaError_t launch_gram_tc(int mode, const void* coeffs, const GramParams& g, const float* wsq,
-                           float* acc, int* status, cudaStream_t s);
+                           float* acc, int* status, int* done, float* sigma, float* R, float* zero_next,
+                           cudaStream_t s);  // done != NULL: the last CTA writes Sigma and R (D <= 256)
 cudaError_t launch_corr_acc(const float* acc, const GramParams& g, float* sigma, float* R, float* zero_next,
                             int* status, cudaStream_t s);
 cudaError_t launch_reduce_corr(bool fp64, const void* partial, const GramParams& g,

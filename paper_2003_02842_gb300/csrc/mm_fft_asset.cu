@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <utility>
 
+#include "mm_async.cuh"
 #include "mm_common.cuh"
 #include "mm_fft_dev.cuh"
 
@@ -233,13 +234,16 @@ __device__ __forceinline__ int digit_rev(int j, const AssetFft& f, const unsigne
 __host__ __device__ __forceinline__ size_t anchor_offset(int nl) { return ((size_t)nl * 8 + 15) & ~(size_t)15; }
 
 constexpr int kLoadBatch = 8;     // global loads in flight per thread (split load)
+constexpr uint32_t kBulkChunk = 32768;  // bytes per bulk copy instruction
 constexpr int kUnpackBatch = 8;   // table reads in flight per thread in the unpacking step
+constexpr int kPairBatch = 4;     // the same for the cluster variant (more values per mode)
 
 template <int NTH>
 __global__ void __launch_bounds__(NTH, 512 / NTH)
     k_fft_asset(const float* __restrict__ grid, AssetFft f, const Cplx<float>* __restrict__ W,
                 const Cplx<float>* __restrict__ tw, const Cplx<float>* __restrict__ U,
-                const float* __restrict__ decon, Cplx<float>* __restrict__ out, const int* __restrict__ gate) {
+                const float* __restrict__ decon, Cplx<float>* __restrict__ out, const int* __restrict__ gate,
+                int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (*gate) return;  // uniform: the whole block leaves
   Cplx<float>* s = reinterpret_cast<Cplx<float>*>(smem_raw);
@@ -261,7 +265,38 @@ __global__ void __launch_bounds__(NTH, 512 / NTH)
 
   // load into digit-reversed order (with the first radix-2 step when S = 2)
   const Cplx<float>* z = reinterpret_cast<const Cplx<float>*>(grid) + (size_t)a * f.n;
-  if (f.split == 1) {
+  if (f.pre_perm) {
+    // the spread kernel already stored the row in digit-reversed order: one
+    // bulk asynchronous copy of the whole row (the anchors' cp.async copies
+    // are waited for below)
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t bytes = (uint32_t)f.n * 8u;
+    if (threadIdx.x == 0) {
+      mbar_init(&bar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(&bar, bytes);
+      const unsigned char* src = reinterpret_cast<const unsigned char*>(z);
+      for (uint32_t o = 0; o < bytes; o += kBulkChunk) {
+        const uint32_t cb = bytes - o < kBulkChunk ? bytes - o : kBulkChunk;
+        bulk_g2s(smem_raw + o, src + o, cb, &bar);
+      }
+    }
+    const bool ok = mbar_wait(&bar, 0, kWaitLimitNs);
+    if (!__syncthreads_and(ok)) {
+      // the copy did not land in time: report it, give it a bounded second
+      // wait so no write into shared memory stays in flight, and leave
+      if (threadIdx.x == 0) {
+        atomicOr(status, ST_TIMEOUT);
+        mbar_wait(&bar, 0, kWaitLimitNs);
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      __syncthreads();
+      return;
+    }
+  } else if (f.split == 1) {
     // asynchronous 8-byte copies straight into their shared-memory slots:
     // the whole grid row is in flight at once, no registers held
     for (int j = threadIdx.x; j < L; j += NTH) {
@@ -329,6 +364,102 @@ __global__ void __launch_bounds__(NTH, 512 / NTH)
   }
 }
 
+// Two CTAs per asset as a thread-block cluster (decimation in time by 2):
+// CTA c transforms x_c[m] = z[2m + c], m < L = n/2, loaded straight into
+// its shared memory by asynchronous copies; then
+//   Z_k = X_0[k mod L] + w_n^k X_1[k mod L]
+// joins the halves, each CTA reading its partner's X through distributed
+// shared memory while it unpacks and deconvolves every other mode.
+__device__ __forceinline__ uint32_t peer_addr(const void* p, unsigned rank) {
+  uint32_t a = (uint32_t)__cvta_generic_to_shared(p), r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ Cplx<float> ld_cluster(uint32_t addr) {
+  float x, y;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(addr) : "memory");
+  return Cplx<float>{x, y};
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <int NTH>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 512 / NTH)
+    k_fft_asset_pair(const float* __restrict__ grid, AssetFft f, const Cplx<float>* __restrict__ W,
+                     const Cplx<float>* __restrict__ tw, const Cplx<float>* __restrict__ U,
+                     const float* __restrict__ decon, Cplx<float>* __restrict__ out, const int* __restrict__ gate) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // every CTA of the cluster reads the same gate word: both leave or neither
+  if (*gate) return;
+  Cplx<float>* s = reinterpret_cast<Cplx<float>*>(smem_raw);
+  float4* anc = reinterpret_cast<float4*>(smem_raw + anchor_offset(f.nl));
+  unsigned c;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(c));
+  const int a = blockIdx.y;
+  const int L = f.nl;
+  unsigned mr[kMaxAssetPasses];
+#pragma unroll
+  for (int p = 0; p < kMaxAssetPasses; ++p) mr[p] = magic_of((unsigned)f.rad[p]);
+  {
+    const float4* src = reinterpret_cast<const float4*>(tw);
+    for (int i = threadIdx.x; i < 2 * f.tw_rows; i += NTH) {
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(anc + i);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src + i) : "memory");
+    }
+  }
+  const Cplx<float>* z = reinterpret_cast<const Cplx<float>*>(grid) + (size_t)a * f.n + c;
+  for (int m = threadIdx.x; m < L; m += NTH) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s + digit_rev(m, f, mr));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(z + 2 * (size_t)m) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  for (int p = f.npass - 1; p >= 0; --p) {
+    run_pass(f.rad[p], s, L, f.stride[p], anc + 2 * f.tw_off[p], NTH);
+    __syncthreads();
+  }
+  cluster_sync_all();  // both halves transformed and visible to the partner
+  const uint32_t peer = peer_addr(s, c ^ 1u);
+  Cplx<float>* oa = out + (size_t)a * (f.N + 1);
+  for (int k0 = (int)c + 2 * (int)threadIdx.x; k0 <= f.N; k0 += 2 * NTH * kPairBatch) {
+    float dk[kPairBatch];
+    Cplx<float> Uk[kPairBatch], Wk[kPairBatch], A0[kPairBatch], A1[kPairBatch], B0[kPairBatch],
+        B1[kPairBatch];
+#pragma unroll
+    for (int u = 0; u < kPairBatch; ++u) {
+      const int k = k0 + u * 2 * NTH;
+      if (k <= f.N) {
+        const int j = k == 0 ? 0 : L - k;  // (n - k) mod L
+        dk[u] = __ldg(decon + k);
+        Uk[u] = U[k];
+        Wk[u] = W[k];
+        const Cplx<float> lk = s[k], lj = s[j];
+        const Cplx<float> rk = ld_cluster(peer + 8u * (uint32_t)k), rj = ld_cluster(peer + 8u * (uint32_t)j);
+        A0[u] = c == 0 ? lk : rk;  // X_0[k]
+        A1[u] = c == 0 ? rk : lk;  // X_1[k]
+        B0[u] = c == 0 ? lj : rj;  // X_0[(n-k) mod L]
+        B1[u] = c == 0 ? rj : lj;  // X_1[(n-k) mod L]
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPairBatch; ++u) {
+      const int k = k0 + u * 2 * NTH;
+      if (k <= f.N) {
+        const Cplx<float> Zk = cadd(A0[u], cmul(Wk[u], A1[u]));
+        const Cplx<float> Znk = cadd(B0[u], cmul(cconj(Wk[u]), B1[u]));  // w_n^{n-k} = conj(w_n^k)
+        const Cplx<float> Zc = cconj(Znk);
+        const Cplx<float> E = {0.5f * (Zk.x + Zc.x), 0.5f * (Zk.y + Zc.y)};
+        const Cplx<float> dlt = csub(Zk, Zc);
+        const Cplx<float> O = {0.5f * dlt.y, -0.5f * dlt.x};  // (Z_k - conj Z_{n-k}) / (2i)
+        const Cplx<float> G = cadd(E, cmul(Uk[u], O));
+        oa[k] = Cplx<float>{G.x * dk[u], G.y * dk[u]};
+      }
+    }
+  }
+  cluster_sync_all();  // the partner has finished reading this CTA's shared memory
+}
+
 // Twiddle anchors of each pass: row j < m_p holds w^1..w^4 of w = w_{L_p}^j,
 // from float64 angles.
 __global__ void k_asset_twiddles(AssetFft f, Cplx<float>* tw) {
@@ -371,18 +502,28 @@ cudaError_t launch_asset_twiddles(const AssetFft& f, void* tw, cudaStream_t s) {
 }
 
 cudaError_t launch_fft_asset(const float* grid, const AssetFft& f, int D, const void* W, const void* tw,
-                             const void* U, const void* decon, void* coeffs, const int* status, cudaStream_t s) {
+                             const void* U, const void* decon, void* coeffs, int* status, cudaStream_t s) {
   const size_t smem = asset_fft_smem(f);
   dim3 grd(f.split, D);
-  auto go = [&](auto fn, int nth) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    fn<<<grd, nth, smem, s>>>(grid, f, (const Cplx<float>*)W, (const Cplx<float>*)tw, (const Cplx<float>*)U,
-                              (const float*)decon, (Cplx<float>*)coeffs, status + 1);
-    return cudaGetLastError();
-  };
-  if (asset_fft_threads(f.split) == 256) return go(k_fft_asset<256>, 256);
-  return go(k_fft_asset<512>, 512);
+  auto set = [&](auto fn) { return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); };
+  cudaError_t e;
+  if (f.pair) {
+    if ((e = set(k_fft_asset_pair<256>)) != cudaSuccess) return e;
+    k_fft_asset_pair<256><<<grd, 256, smem, s>>>(grid, f, (const Cplx<float>*)W, (const Cplx<float>*)tw,
+                                                 (const Cplx<float>*)U, (const float*)decon, (Cplx<float>*)coeffs,
+                                                 status + 1);
+  } else if (asset_fft_threads(f.split) == 256) {
+    if ((e = set(k_fft_asset<256>)) != cudaSuccess) return e;
+    k_fft_asset<256><<<grd, 256, smem, s>>>(grid, f, (const Cplx<float>*)W, (const Cplx<float>*)tw,
+                                            (const Cplx<float>*)U, (const float*)decon, (Cplx<float>*)coeffs,
+                                            status + 1, status);
+  } else {
+    if ((e = set(k_fft_asset<512>)) != cudaSuccess) return e;
+    k_fft_asset<512><<<grd, 512, smem, s>>>(grid, f, (const Cplx<float>*)W, (const Cplx<float>*)tw,
+                                            (const Cplx<float>*)U, (const float*)decon, (Cplx<float>*)coeffs,
+                                            status + 1, status);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace mmgpu

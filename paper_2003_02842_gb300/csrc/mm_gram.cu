@@ -254,10 +254,40 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
 // One CTA per (output tile pair I <= J, K-split): the split's partial
 // 128 x 128 product accumulates in TMEM and is then added into the FP32
 // accumulator acc (row stride Dp) with vector reductions in L2.
+// Sigma and R from the accumulator by one CTA (the last split to finish):
+// the same arithmetic as k_corr_acc, block-strided over the D x Dp entries.
+__device__ void corr_epilogue_block(const float* __restrict__ acc, const GramParams& g, float* __restrict__ sigma,
+                                    float* __restrict__ R, float* __restrict__ zero_next, double* s_inv, int* status) {
+  for (int d = threadIdx.x; d < g.D; d += blockDim.x) {
+    const double v = __ldcg(acc + (int64_t)d * g.Dp + d);
+    s_inv[d] = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
+  }
+  __syncthreads();
+  bool zero = false;
+  for (int e = threadIdx.x; e < g.D * g.Dp; e += blockDim.x) {
+    const int i = e / g.Dp, j = e - i * g.Dp;
+    if (zero_next) zero_next[e] = 0.0f;
+    if (j >= g.D) continue;
+    const bool up = (i / kTile) <= (j / kTile);
+    const double v = up ? (double)__ldcg(acc + (int64_t)i * g.Dp + j) : (double)__ldcg(acc + (int64_t)j * g.Dp + i);
+    const double a = s_inv[i], b = s_inv[j];
+    double r;
+    if (a > 0.0 && b > 0.0) r = (i == j) ? 1.0 : v * a * b;
+    else {
+      r = __longlong_as_double(0x7ff8000000000000ll);
+      if (i == j) zero = true;
+    }
+    if (sigma) sigma[(int64_t)i * g.D + j] = (float)v;
+    if (R) R[(int64_t)i * g.D + j] = (float)r;
+  }
+  if (zero) atomicOr(status, ST_ZERO_VAR);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restrict__ F, GramParams g,
                                                            const float* __restrict__ wsq, float* __restrict__ acc,
-                                                           int* status) {
+                                                           int* status, int* done, float* sigma, float* Rout,
+                                                           float* zero_next) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ uint32_t s_tmem;
@@ -373,10 +403,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restr
   if (threadIdx.x < 32) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
+  if (done) {
+    // the last CTA to finish turns the accumulator into Sigma and R (the
+    // correlation epilogue without a separate launch) and re-arms the counter
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(done, 1) == (int)(gridDim.x * gridDim.y) - 1;
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      corr_epilogue_block(acc, g, sigma, Rout, zero_next, reinterpret_cast<double*>(base), status);
+      if (threadIdx.x == 0) *done = 0;
+    }
+  }
 }
 
 cudaError_t launch_gram_tc(int mode, const void* coeffs, const GramParams& g, const float* wsq, float* acc,
-                           int* status, cudaStream_t s) {
+                           int* status, int* done, float* sigma, float* R, float* zero_next, cudaStream_t s) {
   const bool two = g.ntiles > 1;
   const size_t smem = gram_tc_smem(mode, two);
   dim3 grd(g.splits, g.npairs);
@@ -384,11 +428,13 @@ cudaError_t launch_gram_tc(int mode, const void* coeffs, const GramParams& g, co
   if (mode == 0) {
     e = cudaFuncSetAttribute(k_gram_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_gram_tc<0><<<grd, kTcThreads, smem, s>>>((const float2*)coeffs, g, wsq, acc, status);
+    k_gram_tc<0><<<grd, kTcThreads, smem, s>>>((const float2*)coeffs, g, wsq, acc, status, done, sigma, R,
+                                                zero_next);
   } else {
     e = cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_gram_tc<1><<<grd, kTcThreads, smem, s>>>((const float2*)coeffs, g, wsq, acc, status);
+    k_gram_tc<1><<<grd, kTcThreads, smem, s>>>((const float2*)coeffs, g, wsq, acc, status, done, sigma, R,
+                                                zero_next);
   }
   return cudaGetLastError();
 }

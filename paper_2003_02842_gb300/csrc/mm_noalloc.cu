@@ -106,8 +106,8 @@ extern "C" mm_status mm_corr_noalloc(int32_t D, int32_t N, mm_basis basis, mm_pr
   } else {
     float* acc = (float*)partial;
     if (cudaMemsetAsync(acc, 0, (size_t)D * g.Dp * sizeof(float), st) != cudaSuccess) return MM_ERR_CUDA;
-    if (launch_gram_tc(prec == MM_PREC_MIXED_BF16X3 ? 0 : 1, d_coeffs, g, (const float*)wsq, acc, status, st) !=
-        cudaSuccess)
+    if (launch_gram_tc(prec == MM_PREC_MIXED_BF16X3 ? 0 : 1, d_coeffs, g, (const float*)wsq, acc, status, nullptr,
+                       nullptr, nullptr, nullptr, st) != cudaSuccess)
       return MM_ERR_CUDA;
     if (launch_corr_acc(acc, g, (float*)d_sigma_or_null, (float*)d_R, nullptr, status, st) != cudaSuccess)
       return MM_ERR_CUDA;

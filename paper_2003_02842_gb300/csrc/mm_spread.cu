@@ -631,6 +631,28 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_poly(const int64_t* _
     }
   }
   __syncthreads();
+  if (p.perm_np > 0) {
+    // the per-asset FFT's input order: complex point m = (L + c) / 2 goes to
+    // its digit reversal (tiles and M_r are even, so cells pair up)
+    float2* gz = reinterpret_cast<float2*>(grid + (int64_t)a * p.Mr);
+    const int2* t2 = reinterpret_cast<const int2*>(tile);
+    const int m0 = (int)(L >> 1);
+    for (int c2 = threadIdx.x; c2 < (Tlen >> 1); c2 += kSpreadThreads) {
+      int m = m0 + c2, pos = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (q < p.perm_np) {
+          const int R = p.perm_rad[q];
+          const int h = (int)__umulhi((unsigned)m, p.perm_magic[q]);
+          pos += (m - h * R) * p.perm_stride[q];
+          m = h;
+        }
+      }
+      const int2 v = t2[c2];
+      gz[pos] = make_float2((float)v.x * inv, (float)v.y * inv);
+    }
+    return;
+  }
   float* g = grid + (int64_t)a * p.Mr + L;
   if (((reinterpret_cast<uintptr_t>(g) & 15) == 0) && (Tlen & 3) == 0) {
     const int4* t4 = reinterpret_cast<const int4*>(tile);

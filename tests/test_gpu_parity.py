@@ -131,16 +131,23 @@ def test_cutoffs_small_and_non_smooth(N, algo, fft):
 # cutoffs whose grids need different radix plans of the per-asset FFT: one
 # to four passes, odd and even last radices, the largest grid that fits in
 # shared memory (n = 28800, N = 14399)
+@pytest.mark.parametrize("variant,split", [("default", 3), ("asset", 1), ("asset_split", 2), ("asset_pair", 3),
+                                           ("asset_perm", 1)])
 @pytest.mark.parametrize("N", [3, 14, 100, 365, 729, 2047, 5000, 10000, 14399])
-def test_per_asset_fft_radix_plans(N):
+def test_per_asset_fft_radix_plans(N, variant, split):
     ev = synth.random_events(12, D=3, n_range=(200, 1500), T=28800.0, grid=28800)
     tl = TOL["bf16x3"]
     ref = oracle.coeffs_F(ev.offsets, ev.t, ev.logp, N)
     for kernel in ("gauss", "kb", "es"):
-        out = run(dict(tol=tl["tol"], kernel=kernel, basis="dirichlet", prec="bf16x3"), ev, N)
+        out = run(dict(tol=tl["tol"], kernel=kernel, basis="dirichlet", prec="bf16x3", fft_algo=variant), ev, N)
         info = out["info"]
-        assert info["fft_algo"] == 0 and info["fft_split"] == 2, info  # D = 3: two CTAs per asset
-        assert int(np.prod(info["fft_radix"])) * 2 * info["fft_split"] == info["Mr"]
+        if N == 14399 and split == 1:
+            # n = 28800: the whole grid does not fit one CTA's shared memory
+            assert info["fft_algo"] == 1, info
+        else:
+            assert info["fft_algo"] == 0 and info["fft_split"] == split, info  # D = 3 < SMs: a pair by default
+            nl = int(np.prod(info["fft_radix"]))
+            assert nl * 2 * (1 if split == 1 else 2) == info["Mr"]
         assert np.all(rel_l2_rows(out["F"], ref) <= tl["coef"]), (kernel, info["fft_radix"])
 
 
@@ -299,8 +306,9 @@ def test_profiling_counts_launches():
         mm.mm_estimate(plan, off, t, p, 500)
     prof = mm.mm_profile_read(plan)
     assert prof["prep"][1] == 6 and prof["prep"][0] > 0  # bounds + per-event prep
-    for stage in ("spread", "fft", "gram", "reduce"):
+    for stage in ("spread", "fft", "gram"):
         assert prof[stage][1] == 3 and prof[stage][0] > 0
+    assert prof["reduce"][1] == 0  # small D: the contraction's last CTA writes Sigma and R
     assert prof["fused"][1] == 0 and prof["fft_cols"][1] == 0 and prof["fft_rows"][1] == 0
     assert prof["setup"][1] == 0  # tables are cached per cutoff
     mm.mm_destroy(plan)
