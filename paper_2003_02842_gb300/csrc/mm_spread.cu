@@ -536,6 +536,11 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_scatter(const int64_t
   }
 }
 
+// Shared-memory integer reduction without a returned value.
+__device__ __forceinline__ void red_shared_add(uint32_t addr, int v) {
+  asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
 // Float32 scatter with polynomial taps and exact integer accumulation.
 // Float atomics in shared memory run as compare-and-swap loops; integer ones
 // are native. Each tile therefore accumulates round(v phi 2^e) in int32 with
@@ -557,6 +562,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_poly(const int64_t* _
   float* ev_d = reinterpret_cast<float*>(smem_raw + EC * sizeof(int));
   float* ev_v = ev_d + EC;
   int* tile = reinterpret_cast<int*>(ev_v + EC);
+  const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile);
   __shared__ float s_part[kSpreadThreads / 32];
   if (*gate) return;  // uniform: the whole block leaves
   const int a = blockIdx.y;
@@ -619,13 +625,14 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_poly(const int64_t* _
       }
       const int c0 = pe + klo;
       if (c0 >= 0 && c0 + NT <= Tlen) {
+        const uint32_t a0 = tile_s + 4u * (uint32_t)c0;
 #pragma unroll
-        for (int j = 0; j < NT; ++j) atomicAdd(tile + c0 + j, __float2int_rn(vs * w[j]));
+        for (int j = 0; j < NT; ++j) red_shared_add(a0 + 4u * j, __float2int_rn(vs * w[j]));
       } else {
 #pragma unroll
         for (int j = 0; j < NT; ++j) {
           const unsigned c = (unsigned)(c0 + j);
-          if (c < (unsigned)Tlen) atomicAdd(tile + c, __float2int_rn(vs * w[j]));
+          if (c < (unsigned)Tlen) red_shared_add(tile_s + 4u * c, __float2int_rn(vs * w[j]));
         }
       }
     }
