@@ -35,10 +35,10 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # capture summarised in profiles/ (None until a capture of the current kernel)
 NCU_TRAFFIC = {
     # profiles/c3_block_D100_N10000_kernels_ncu.md (default configuration)
-    ("spread", "c3", "bf16x3", "es"): 9217536,
-    ("fft", "c3", "bf16x3", "es"): 16519424,
+    ("spread", "c3", "bf16x3", "es"): 9225216,
+    ("fft", "c3", "bf16x3", "es"): 16520448,
     ("prep", "c3", "bf16x3", "es"): 12272896,
-    ("gram", "c3", "bf16x3", "es"): 8135680,
+    ("gram", "c3", "bf16x3", "es"): 8143360,
 }
 
 
