@@ -107,15 +107,19 @@ typedef struct {
                            accumulation (the mixed-path default 1 uses per-tap
                            polynomials and integer accumulation). All compute Eq. (12). */
   int32_t fft_algo;     /* stages (b)-(c) in the mixed precisions: 0 library default
-                           (the grid in shared memory when it fits, as 4 for fewer
-                           assets than SMs else 2; otherwise 1); 1 two-pass FFT through
+                           (the grid in shared memory when it fits: as 4 for at most
+                           half as many assets as SMs, as 3 for fewer assets than
+                           SMs, else as 2; otherwise 1); 1 two-pass FFT through
                            global memory; 2 one CTA per asset; 3 two CTAs per asset
                            (radix-2 step on load); 4 a cluster of two CTAs per asset
                            (decimation in time by 2, halves joined through distributed
                            shared memory); 5 as 2 with the polynomial scatter storing
                            the grid in the FFT's digit-reversed input order (one bulk
-                           copy per row). The FP64 path always uses 1. All compute
-                           Eqs. (13)-(14). */
+                           copy per row); 6 three CTAs per asset (radix-3 step on
+                           load; the CTAs of the output classes k = 1, 2 mod 3 each
+                           form their terms of both classes' modes and combine them
+                           in the output, ordered by a per-asset counter). The FP64
+                           path always uses 1. All compute Eqs. (13)-(14). */
   int32_t reserved[4];  /* must be zero */
 } mm_plan_desc;
 
@@ -145,9 +149,11 @@ typedef struct {
   int32_t fft_radix[4];  /* per-asset FFT: radix of each pass */
   int32_t fft_split;     /* per-asset FFT: 1 one CTA per asset, 2 two CTAs (radix-2 step on
                             load), 3 a cluster of two CTAs joined through distributed shared
-                            memory; 0 when not in use */
+                            memory, 4 three CTAs (radix-3 step on load); 0 when not in use */
   int32_t spread_poly;   /* 1: float32 spreading evaluates the kernel as per-tap polynomials
                             (error <= max(3e-7, tol/10)) and accumulates exactly in integers */
+  int32_t graphs;        /* 1: steady mm_estimate calls replay a captured CUDA graph */
+  int64_t graph_launches; /* mm_estimate calls served by a graph replay since creation */
 } mm_plan_info;
 
 /* Create a plan: validates desc, allocates the workspace on the current
@@ -249,6 +255,17 @@ mm_status mm_plan_get_info(mm_plan plan, mm_plan_info* info);
  * synchronises the events it reads. */
 mm_status mm_profile_enable(mm_plan plan, int32_t on);
 mm_status mm_profile_read(mm_plan plan, double* ms, int64_t* launches, int32_t reset);
+
+/* CUDA graph replay of mm_estimate (and of the compute of mm_estimate_host),
+ * on (1, the default) or off (0). A call is steady when the plan's tables,
+ * contraction weights and configuration are already built for its N > 0 and
+ * stage timing is off; the first steady call with a given set of device
+ * pointers, N, window and configuration captures its launches (one graph for
+ * each of the two FP32 accumulators the contraction alternates between) and
+ * later ones replay them with one launch. The results are those of the eager
+ * launches; the graph reads the inputs' current contents. Other calls, and
+ * every call with graphs off, launch eagerly. */
+mm_status mm_plan_set_graphs(mm_plan plan, int32_t on);
 
 /* Static text for a status code. */
 const char* mm_status_string(mm_status s);

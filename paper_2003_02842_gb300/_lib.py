@@ -22,7 +22,8 @@ KERNELS = {"gauss": 0, "kb": 1, "es": 2}
 BASES = {"dirichlet": 0, "fejer": 1}
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "3xtf32": 2}
 SPREAD_ALGOS = {"default": 0, "scatter": 1, "gather": 2, "fused": 3, "scatter_direct": 4}
-FFT_ALGOS = {"default": 0, "two_pass": 1, "asset": 2, "asset_split": 3, "asset_pair": 4, "asset_perm": 5}
+FFT_ALGOS = {"default": 0, "two_pass": 1, "asset": 2, "asset_split": 3, "asset_pair": 4, "asset_perm": 5,
+             "asset_split3": 6}
 STAGES = ["prep", "spread", "fft_cols", "fft_rows", "gram", "reduce", "setup", "fused", "fft"]
 
 
@@ -62,6 +63,8 @@ class PlanInfo(ctypes.Structure):
         ("fft_radix", ctypes.c_int32 * 4),
         ("fft_split", ctypes.c_int32),
         ("spread_poly", ctypes.c_int32),
+        ("graphs", ctypes.c_int32),
+        ("graph_launches", ctypes.c_int64),
     ]
 
 
@@ -180,6 +183,7 @@ def load():
         "mm_plan_sync": ([p], st),
         "mm_plan_get_info": ([p, ctypes.POINTER(PlanInfo)], st),
         "mm_profile_enable": ([p, i32], st),
+        "mm_plan_set_graphs": ([p, i32], st),
         "mm_profile_read": ([p, p, p, i32], st),
         "mm_status_string": ([st], ctypes.c_char_p),
         "mm_version": ([], i32),

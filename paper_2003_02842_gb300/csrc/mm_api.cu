@@ -250,6 +250,7 @@ struct mm_plan_s {
   size_t partial_bytes = 0;
   float* acc[2] = {nullptr, nullptr};  // mixed path: FP32 accumulators, used alternately
   int* gram_done = nullptr;       // contraction CTAs finished (the last one runs the epilogue)
+  int* fft_sync = nullptr;        // per asset: arrival counter and flag of the three-CTA FFT split
   int acc_sel = 0;
   bool acc_dirty = true;          // clear both before the next contraction
   int acc_D = -1;                 // D whose D x Dp region the last epilogue cleared
@@ -285,6 +286,19 @@ struct mm_plan_s {
   bool poly_ok = false;   // float32 spreading with polynomial taps and integer accumulation
   int tune_poly = -1;     // autotuner override: 0 off
   cudaStream_t last = nullptr;
+  // replay of mm_estimate's launch sequence: one graph per accumulator in use
+  // (the sequence differs only in which accumulator it fills and clears)
+  struct EstGraph {
+    cudaGraphExec_t exec = nullptr;
+    const void* key[6] = {};  // inputs and outputs it was captured with
+    int N = -1, D = -1, cfg = -1;
+    double t0 = 0.0, t1 = 0.0;
+    int kernels = 0;
+  } eg[2];
+  cudaStream_t cap = nullptr;  // capture stream
+  int cfg_gen = 0;             // configuration generation (a graph holds one)
+  bool graphs = true;
+  int64_t graph_launches = 0;
   // instrumentation
   bool prof = false;
   std::vector<Prof> pending;
@@ -315,9 +329,13 @@ mm_status dalloc(mm_plan p, void** ptr, size_t bytes) {
 
 void free_all(mm_plan p) {
   void* ptrs[] = {p->grid, p->rec_b0, p->rec_d, p->rec_v, p->W, p->atw, p->U, p->decon, p->glx, p->glw, p->bounds, p->gscale, p->status, p->gapbits, p->wsq,
-                  p->partial, p->acc[0], p->acc[1], p->gram_done, p->s_off, p->s_t, p->s_p, p->s_coef, p->s_sigma, p->s_R};
+                  p->partial, p->acc[0], p->acc[1], p->gram_done, p->fft_sync, p->s_off, p->s_t, p->s_p, p->s_coef,
+                  p->s_sigma, p->s_R};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  for (auto& e : p->eg)
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+  if (p->cap) cudaStreamDestroy(p->cap);
   for (auto& e : p->pending) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -451,11 +469,14 @@ mm_status configure(mm_plan p, int N) {
   // at most half as many assets as SMs: two CTAs per asset as a cluster
   // (decimation in time by 2, joined through distributed shared memory);
   // fewer assets than SMs: two CTAs per asset (radix-2 step on load);
-  // otherwise one CTA per asset
+  // otherwise one CTA per asset. Each CTA's time is set by latency (a CTA
+  // alone on an SM takes as long as two sharing one), so three CTAs per
+  // asset (radix-3 step on load) is only taken on request.
   int split = p->D < kSMs ? 2 : 1;
   int pair = 2 * p->D <= kSMs ? 1 : 0;
-  if (p->desc.fft_algo >= 2 && p->tune_split < 1) {  // the caller's choice of per-asset variant
-    split = (p->desc.fft_algo == 2 || p->desc.fft_algo == 5) ? 1 : 2;
+  const bool caller_split = p->desc.fft_algo >= 2 && p->tune_split < 1;
+  if (caller_split) {  // the caller's choice of per-asset variant
+    split = (p->desc.fft_algo == 2 || p->desc.fft_algo == 5) ? 1 : p->desc.fft_algo == 6 ? 3 : 2;
     pair = p->desc.fft_algo == 4 ? 1 : 0;
   }
   if (p->tune_split == 1 || p->tune_split == 2) {
@@ -464,15 +485,27 @@ mm_status configure(mm_plan p, int N) {
   } else if (p->tune_split == 3) {
     split = 2;
     pair = 1;
+  } else if (p->tune_split == 4) {
+    split = 3;
+    pair = 0;
   }
-  const int maxr = p->tune_maxr == 16 ? 16 : 32;
+  // radices up to 16 by default: the fully unrolled codelets of 25 to 32
+  // points stall on instruction fetch, so four small passes beat three large
+  // ones; radices up to 32 where the small ones need too many passes or
+  // twiddle rows
   auto fits_split = [&](int sp_) {
-    return plan_asset_fft(n, sp_, N, maxr, &af) && asset_fft_smem(af) + 2048 <= (size_t)p->smem_optin &&
-           asset_twiddle_count(af) <= p->atw_cap;
+    for (int maxr : {16, 32}) {
+      if (p->tune_maxr > 0 && maxr != p->tune_maxr) continue;
+      if (plan_asset_fft(n, sp_, N, maxr, &af) && asset_fft_smem(af) + 2048 <= (size_t)p->smem_optin &&
+          asset_twiddle_count(af) <= p->atw_cap)
+        return true;
+    }
+    return false;
   };
   bool afft = !p->fp64 && fits_split(split);
   if (!p->fp64 && !afft && p->tune_split < 1 && p->desc.fft_algo < 2) {
-    split = 3 - split;  // the other split (a large grid fits in shared memory only as two halves)
+    // another split (a large grid fits in shared memory only as two halves)
+    split = split == 1 ? 2 : split == 3 ? 2 : 1;
     pair = split == 2 ? 1 : 0;
     afft = fits_split(split);
   }
@@ -503,6 +536,7 @@ mm_status configure(mm_plan p, int N) {
   p->Mr = Mr;
   p->cfg_N = N;
   p->cfg_D = p->D;
+  p->cfg_gen += 1;
   return MM_OK;
 }
 
@@ -628,7 +662,7 @@ mm_status coeffs_impl(mm_plan p, const int64_t* off, const double* t, const doub
     if (p->use_afft) {
       StageScope sc(p, MM_STAGE_FFT, st);
       MM_CUDA(launch_fft_asset((const float*)p->grid, p->afft, D, p->W, p->atw, p->U, p->decon, coeffs, p->status,
-                               st));
+                               p->fft_sync, st));
     } else {
     {
       StageScope sc(p, MM_STAGE_FFT_COLS, st);
@@ -699,11 +733,90 @@ mm_status corr_impl(mm_plan p, const void* coeffs, int N, void* sigma, void* R, 
   return MM_OK;
 }
 
+mm_status estimate_eager(mm_plan p, const int64_t* off, const double* t, const double* logp, int N, double t0,
+                         double t1, void* coeffs, void* sigma, void* R, int32_t* N_used, cudaStream_t st) {
+  int32_t Nu = 0;
+  mm_status r = coeffs_impl(p, off, t, logp, N, t0, t1, coeffs, &Nu, st);
+  if (r != MM_OK) return r;
+  if (N_used) *N_used = Nu;
+  return corr_impl(p, coeffs, Nu, sigma, R, st);
+}
+
+// Coefficients, Sigma and R with the launches of a steady call (tables,
+// weights and configuration already built for N; no per-stage timing)
+// replayed from a CUDA graph: one launch instead of six to eight, and no
+// launch gaps between the kernels. The first steady call with a given set of
+// inputs, outputs, cutoff, window and configuration captures the sequence
+// (for the accumulator it fills), later ones replay it. Anything else runs
+// eagerly.
+mm_status estimate_impl(mm_plan p, const int64_t* off, const double* t, const double* logp, int N, double t0,
+                        double t1, void* coeffs, void* sigma, void* R, int32_t* N_used, cudaStream_t st) {
+  const bool steady = p->graphs && !p->prof && N > 0 && p->G == 1 && p->cfg_N == N && p->cfg_D == p->D &&
+                      p->tab_N == N && p->w_N == N && p->w_basis == (int)p->desc.basis &&
+                      (p->fp64 || (!p->acc_dirty && p->acc_D == p->D));
+  if (!steady) return estimate_eager(p, off, t, logp, N, t0, t1, coeffs, sigma, R, N_used, st);
+  mm_plan_s::EstGraph& G = p->eg[p->fp64 ? 0 : p->acc_sel];
+  const void* key[6] = {off, t, logp, coeffs, sigma, R};
+  bool same = G.exec && G.N == N && G.D == p->D && G.cfg == p->cfg_gen && G.t0 == t0 && G.t1 == t1;
+  for (int i = 0; i < 6 && same; ++i) same = key[i] == G.key[i];
+  if (!same) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
+    if (!p->cap && cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return estimate_eager(p, off, t, logp, N, t0, t1, coeffs, sigma, R, N_used, st);
+    }
+    // capture from the current host state, which is then put back: the
+    // launches run when the graph does
+    const int acc_sel = p->acc_sel, acc_D = p->acc_D;
+    const bool acc_dirty = p->acc_dirty;
+    const int64_t l0 = p->launches;
+    cudaGraph_t g = nullptr;
+    mm_status r = MM_ERR_CUDA;
+    if (cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+      r = estimate_eager(p, off, t, logp, N, t0, t1, coeffs, sigma, R, nullptr, p->cap);
+      if (cudaStreamEndCapture(p->cap, &g) != cudaSuccess) r = MM_ERR_CUDA;
+    }
+    const int kernels = (int)(p->launches - l0);
+    p->launches = l0;
+    p->acc_sel = acc_sel;
+    p->acc_D = acc_D;
+    p->acc_dirty = acc_dirty;
+    cudaGraphExec_t ex = nullptr;
+    if (r == MM_OK && g && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) ex = nullptr;
+    if (g) cudaGraphDestroy(g);
+    if (!ex) {
+      cudaGetLastError();
+      return estimate_eager(p, off, t, logp, N, t0, t1, coeffs, sigma, R, N_used, st);
+    }
+    G.exec = ex;
+    for (int i = 0; i < 6; ++i) G.key[i] = key[i];
+    G.N = N;
+    G.D = p->D;
+    G.cfg = p->cfg_gen;
+    G.t0 = t0;
+    G.t1 = t1;
+    G.kernels = kernels;
+  }
+  MM_CUDA(cudaGraphLaunch(G.exec, st));
+  p->graph_launches += 1;
+  p->launches += G.kernels;
+  p->last = st;
+  // the host state the eager sequence leaves behind
+  if (!p->fp64) {
+    p->acc_sel ^= 1;
+    p->acc_dirty = false;
+    p->acc_D = p->D;
+  }
+  if (N_used) *N_used = N;
+  return MM_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
-int32_t mm_version(void) { return 100; }
+int32_t mm_version(void) { return 101; }
 
 const char* mm_status_string(mm_status s) {
   switch (s) {
@@ -743,7 +856,7 @@ mm_status plan_create_impl(const mm_plan_desc* desc, int gsize, bool batch, mm_p
   if (d.prec < MM_PREC_FP64 || d.prec > MM_PREC_MIXED_3XTF32) return MM_ERR_INVALID_ARG;
   if (d.spread_tile < 0 || d.spread_tile > 50000) return MM_ERR_INVALID_ARG;
   if (d.spread_algo < 0 || d.spread_algo > 4) return MM_ERR_INVALID_ARG;
-  if (d.fft_algo < 0 || d.fft_algo > 5) return MM_ERR_INVALID_ARG;
+  if (d.fft_algo < 0 || d.fft_algo > 6) return MM_ERR_INVALID_ARG;
   for (int i = 0; i < 4; ++i)
     if (d.reserved[i] != 0) return MM_ERR_INVALID_ARG;
   const int msp = msp_rule(d.kernel, d.tol);
@@ -787,6 +900,7 @@ mm_status plan_create_impl(const mm_plan_desc* desc, int gsize, bool batch, mm_p
   if (!p->fp64) {
     p->atw_cap = 2 * n;  // sum_p m_p (R_p - 1) < n (1 + 1/R_1 + ...) < 2n
     A(&p->atw, (size_t)p->atw_cap * p->cs);
+    A((void**)&p->fft_sync, 2 * D * sizeof(int));
   }
   A(&p->U, Np1 * p->cs);
   A(&p->decon, Np1 * p->rs);
@@ -820,6 +934,7 @@ mm_status plan_create_impl(const mm_plan_desc* desc, int gsize, bool batch, mm_p
   if (r == MM_OK) {
     if (cudaMemset(p->status, 0, 4 * sizeof(int)) != cudaSuccess) r = MM_ERR_CUDA;
     if (p->gram_done && cudaMemset(p->gram_done, 0, sizeof(int)) != cudaSuccess) r = MM_ERR_CUDA;
+    if (p->fft_sync && cudaMemset(p->fft_sync, 0, 2 * D * sizeof(int)) != cudaSuccess) r = MM_ERR_CUDA;
   }
   if (r == MM_OK) {
     if (launch_gl_nodes(kGlNodes, p->glx, p->glw, 0) != cudaSuccess) r = MM_ERR_CUDA;
@@ -892,11 +1007,8 @@ mm_status mm_estimate(mm_plan p, const int64_t* d_offsets, const double* d_t, co
   if (r != MM_OK) return r;
   if (!d_offsets || !d_t || !d_logp || !d_coeffs || !d_R) return MM_ERR_INVALID_ARG;
   if (!(isfinite(t0) && isfinite(t1))) return MM_ERR_INVALID_ARG;
-  int32_t Nu = 0;
-  r = coeffs_impl(p, d_offsets, d_t, d_logp, N, t0, t1, d_coeffs, &Nu, (cudaStream_t)stream);
-  if (r != MM_OK) return r;
-  if (N_used) *N_used = Nu;
-  return corr_impl(p, d_coeffs, Nu, d_sigma_or_null, d_R, (cudaStream_t)stream);
+  return estimate_impl(p, d_offsets, d_t, d_logp, N, t0, t1, d_coeffs, d_sigma_or_null, d_R, N_used,
+                       (cudaStream_t)stream);
 }
 
 mm_status mm_estimate_host(mm_plan p, const int64_t* h_offsets, const double* h_t, const double* h_logp, int32_t N,
@@ -942,7 +1054,7 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
   std::vector<Cand> cands;
   const int tmax = spread_max_tile(p->fp64);
   if (!p->fp64) {
-    for (int split : {1, 2, 3})  // 3: two CTAs per asset as a cluster
+    for (int split : {1, 2, 3, 4})  // 3: two CTAs per asset as a cluster; 4: three CTAs as a cluster
       for (int maxr : {16, 32}) {
         for (int tile : {tmax / 4, tmax / 2, tmax}) cands.push_back({0, tile, -1, -1, 0, split, maxr, 1});
         if (split == 1) cands.push_back({0, tmax / 2, -1, -1, 0, split, maxr, 1, 1});
@@ -976,7 +1088,7 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
     p->cfg_N = -1;  // force reconfiguration
     if (configure(p, N) != MM_OK) continue;
     if (c.algo == 2 && !p->sp.fused) continue;  // fused variant does not fit
-    if (c.fft == 0 && (!p->use_afft || p->afft.split != (c.split == 3 ? 2 : c.split) ||
+    if (c.fft == 0 && (!p->use_afft || p->afft.split != (c.split == 3 ? 2 : c.split == 4 ? 3 : c.split) ||
                        p->afft.pair != (c.split == 3 ? 1 : 0)))
       continue;  // not available
     // warm-up (also builds the tables for N)
@@ -1063,7 +1175,17 @@ mm_status mm_plan_sync(mm_plan p) {
   int f = 0;
   MM_CUDA(cudaMemcpy(&f, p->status, sizeof(int), cudaMemcpyDeviceToHost));
   if (f) MM_CUDA(cudaMemset(p->status, 0, sizeof(int)));
+  // a timed-out wait may leave a split FFT's pair words set: clear them
+  if ((f & ST_TIMEOUT) && p->fft_sync) MM_CUDA(cudaMemset(p->fft_sync, 0, 2 * (size_t)p->desc.D * sizeof(int)));
   return flags_to_status(f);
+}
+
+mm_status mm_plan_set_graphs(mm_plan p, int32_t on) {
+  mm_status r = check_plan(p);
+  if (r != MM_OK) return r;
+  if (on != 0 && on != 1) return MM_ERR_INVALID_ARG;
+  p->graphs = on == 1;
+  return MM_OK;
 }
 
 mm_status mm_plan_get_info(mm_plan p, mm_plan_info* info) {
@@ -1085,7 +1207,9 @@ mm_status mm_plan_get_info(mm_plan p, mm_plan_info* info) {
   info->tuned_ms = p->tune_ms;
   info->fft_algo = p->use_afft ? 0 : 1;
   info->fft_passes = p->use_afft ? p->afft.npass : 0;
-  info->fft_split = p->use_afft ? (p->afft.pair ? 3 : p->afft.split) : 0;
+  info->fft_split = p->use_afft ? (p->afft.pair ? 3 : p->afft.split == 3 ? 4 : p->afft.split) : 0;
+  info->graphs = p->graphs ? 1 : 0;
+  info->graph_launches = p->graph_launches;
   for (int q = 0; q < 4; ++q) info->fft_radix[q] = p->use_afft && q < p->afft.npass ? p->afft.rad[q] : 0;
   return MM_OK;
 }

@@ -131,8 +131,8 @@ def test_cutoffs_small_and_non_smooth(N, algo, fft):
 # cutoffs whose grids need different radix plans of the per-asset FFT: one
 # to four passes, odd and even last radices, the largest grid that fits in
 # shared memory (n = 28800, N = 14399)
-@pytest.mark.parametrize("variant,split", [("default", 3), ("asset", 1), ("asset_split", 2), ("asset_pair", 3),
-                                           ("asset_perm", 1)])
+@pytest.mark.parametrize("variant,split", [("default", 0), ("asset", 1), ("asset_split", 2), ("asset_pair", 3),
+                                           ("asset_perm", 1), ("asset_split3", 4)])
 @pytest.mark.parametrize("N", [3, 14, 100, 365, 729, 2047, 5000, 10000, 14399])
 def test_per_asset_fft_radix_plans(N, variant, split):
     ev = synth.random_events(12, D=3, n_range=(200, 1500), T=28800.0, grid=28800)
@@ -141,13 +141,16 @@ def test_per_asset_fft_radix_plans(N, variant, split):
     for kernel in ("gauss", "kb", "es"):
         out = run(dict(tol=tl["tol"], kernel=kernel, basis="dirichlet", prec="bf16x3", fft_algo=variant), ev, N)
         info = out["info"]
-        if N == 14399 and split == 1:
-            # n = 28800: the whole grid does not fit one CTA's shared memory
+        n = info["Mr"] // 2
+        want = split if split else 3  # D = 3 < SMs: a pair by default
+        if (N == 14399 and split == 1) or (want == 4 and n % 3):
+            # n = 28800: the whole grid does not fit one CTA's shared memory;
+            # a three-way split needs 3 | n
             assert info["fft_algo"] == 1, info
         else:
-            assert info["fft_algo"] == 0 and info["fft_split"] == split, info  # D = 3 < SMs: a pair by default
+            assert info["fft_algo"] == 0 and info["fft_split"] == want, info
             nl = int(np.prod(info["fft_radix"]))
-            assert nl * 2 * (1 if split == 1 else 2) == info["Mr"]
+            assert nl * 2 * {1: 1, 2: 2, 3: 2, 4: 3}[want] == info["Mr"]
         assert np.all(rel_l2_rows(out["F"], ref) <= tl["coef"]), (kernel, info["fft_radix"])
 
 
