@@ -107,9 +107,9 @@ typedef struct {
                            accumulation (the mixed-path default 1 uses per-tap
                            polynomials and integer accumulation). All compute Eq. (12). */
   int32_t fft_algo;     /* stages (b)-(c) in the mixed precisions: 0 library default
-                           (the grid in shared memory when it fits: as 4 for at most
-                           half as many assets as SMs, as 3 for fewer assets than
-                           SMs, else as 2; otherwise 1); 1 two-pass FFT through
+                           (the grid in shared memory when it fits: as 2 when one
+                           asset's row fits one CTA, else as 4; otherwise 1);
+                           1 two-pass FFT through
                            global memory; 2 one CTA per asset; 3 two CTAs per asset
                            (radix-2 step on load); 4 a cluster of two CTAs per asset
                            (decimation in time by 2, halves joined through distributed

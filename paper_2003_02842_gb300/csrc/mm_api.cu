@@ -70,11 +70,10 @@ bool choose_fft(int64_t nmin, int64_t* n_out, int* P_out, int* Q_out) {
 
 // Plan of the per-asset FFT of n points split over `split` CTAs: the local
 // length nl = n / split factored into the fewest radices from the compiled
-// set (largest smallest factor on ties), even radices first in the list so
-// that the last entry, the first decimation-in-time pass, whose butterflies
-// are contiguous in shared memory, has an odd radix where one exists (fewer
-// bank conflicts). Returns false when nl needs more than kMaxAssetPasses
-// factors.
+// set up to maxr (largest smallest factor on ties). Entry p has stride
+// nl / (R_0 ... R_p); the last entry (unit stride, butterflies contiguous in
+// shared memory) gets an odd radix where one exists. Returns false when nl
+// needs more than kMaxAssetPasses factors.
 bool plan_asset_fft(int64_t n, int split, int N, int maxr, AssetFft* out) {
   static const int kRad[] = {32, 30, 27, 25, 24, 20, 18, 16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
   if (split < 1 || n % split) return false;
@@ -100,11 +99,19 @@ bool plan_asset_fft(int64_t n, int split, int N, int maxr, AssetFft* out) {
   if (nl < 2 || nl > (1 << 15)) return false;
   rec(nl, maxr);
   if (best.empty()) return false;
-  // the last entry is the first DIT pass (unit stride): keep an odd radix there
-  std::stable_sort(best.begin(), best.end(), [](int a, int b) {
-    if ((a & 1) != (b & 1)) return (a & 1) == 0;
-    return a > b;
-  });
+  // descending, so that the pass of largest stride (entry 0, which needs
+  // stride rows of twiddle anchors) has the largest radix; the last entry is
+  // the unit-stride pass, where an odd radix keeps the 8-byte shared-memory
+  // accesses of a warp free of bank conflicts: the smallest odd radix goes
+  // there
+  std::sort(best.begin(), best.end(), [](int a, int b) { return a > b; });
+  for (int q = (int)best.size() - 1; q >= 0; --q)
+    if (best[q] & 1) {
+      const int r = best[q];
+      best.erase(best.begin() + q);
+      best.push_back(r);
+      break;
+    }
   AssetFft f{};
   f.n = (int)n;
   f.nl = (int)nl;
@@ -126,6 +133,10 @@ bool plan_asset_fft(int64_t n, int split, int N, int maxr, AssetFft* out) {
     f.tw_off[q] = off;
   }
   f.tw_rows = off;
+  // digit-reversal tables: the two largest radices' digits and the rest
+  f.rev_lo = f.npass >= 2 ? f.rad[0] * f.rad[1] : f.rad[0];
+  f.rev_hi = (int)(nl / f.rev_lo);
+  f.dif = 1;  // decimation in frequency unless the caller's input order says otherwise
   *out = f;
   return true;
 }
@@ -466,14 +477,15 @@ mm_status configure(mm_plan p, int N) {
   // per-asset FFT: mixed path, the complex grid fits in shared memory and n
   // factors into at most kMaxAssetPasses compiled radices
   AssetFft af{};
-  // at most half as many assets as SMs: two CTAs per asset as a cluster
-  // (decimation in time by 2, joined through distributed shared memory);
-  // fewer assets than SMs: two CTAs per asset (radix-2 step on load);
-  // otherwise one CTA per asset. Each CTA's time is set by latency (a CTA
-  // alone on an SM takes as long as two sharing one), so three CTAs per
-  // asset (radix-3 step on load) is only taken on request.
-  int split = p->D < kSMs ? 2 : 1;
-  int pair = 2 * p->D <= kSMs ? 1 : 0;
+  // one CTA per asset (its grid row lands in shared memory by bulk copies)
+  // whenever the row fits, whatever the number of assets: each CTA's time is
+  // set by latency (a CTA alone on an SM takes as long as two sharing one),
+  // so splitting an asset over more SMs does not pay for its extra loads.
+  // Larger rows: two CTAs per asset as a cluster (decimation in time by 2,
+  // joined through distributed shared memory). Two or three CTAs per asset
+  // with a radix-2 or radix-3 step on load are taken on request.
+  int split = 1;
+  int pair = 0;
   const bool caller_split = p->desc.fft_algo >= 2 && p->tune_split < 1;
   if (caller_split) {  // the caller's choice of per-asset variant
     split = (p->desc.fft_algo == 2 || p->desc.fft_algo == 5) ? 1 : p->desc.fft_algo == 6 ? 3 : 2;
@@ -529,6 +541,9 @@ mm_status configure(mm_plan p, int N) {
       s.perm_magic[q] = R <= 1 ? 0u : 0xFFFFFFFFu / (unsigned)R + 1u;
     }
   }
+  // decimation in frequency (natural-order input) except where the input
+  // arrives digit-reversed: the scatter's permuted grid, the cluster pair
+  af.dif = !af.pre_perm && !af.pair;
   p->afft = af;
   p->use_afft = afft && !s.fused;
   p->fft = f;

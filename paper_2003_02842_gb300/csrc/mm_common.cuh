@@ -122,9 +122,12 @@ struct AssetFft {
   int split;    // CTAs per asset: 1, 2 (radix-2 step on load), 3 (radix-3 step on load)
   int pair;     // split 2 as a cluster of two CTAs (decimation in time by 2)
   int pre_perm; // split 1: the spread kernel stored the grid in digit-reversed order
+  int dif;      // decimation in frequency (natural-order input); else in time
   int N;
   int npass;
   int tw_rows;  // anchor rows over all passes
+  int rev_lo;   // decimation in frequency: rev(k) = T_lo[k mod rev_lo] + T_hi[k / rev_lo]
+  int rev_hi;   // (tables of rev_lo and rev_hi ints after the anchors; rev_lo * rev_hi = nl)
   int rad[kMaxAssetPasses];
   int stride[kMaxAssetPasses];
   int tw_off[kMaxAssetPasses];

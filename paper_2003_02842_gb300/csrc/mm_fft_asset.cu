@@ -19,16 +19,22 @@
 // of fewer assets than SMs thus spreads each asset's FFT over two or three
 // SMs.
 //
-// The local transform of L = R_1 R_2 ... R_s points (every R_p <= 32) is an
-// in-place decimation-in-time FFT: the input is stored in mixed-radix
-// digit-reversed order, then pass p = s..1 (blocks of length L_p =
-// R_p m_p, stride m_p) multiplies each butterfly's points by the twiddles
-// w_{L_p}^{j r} as they are loaded, transforms them in registers with a fully
-// unrolled R_p-point DFT (a compile-time Cooley-Tukey split into 2-, 3-, 4-,
-// 5- and 8-point DFTs with its twiddles folded into immediates) and stores
-// them back in place; the output comes out in natural order. With
-// k = q_1 + R_1 (q_2 + R_2 (q_3 + ...)), input k goes to position
-// sum_p q_p m_p.
+// The local transform of L = R_1 R_2 ... R_s points (every R_p <= 32) runs in
+// place in shared memory, pass p working on blocks of length L_p = R_p m_p
+// with stride m_p = L / (R_1 ... R_p): each butterfly's R_p points are
+// transformed in registers by a fully unrolled R_p-point DFT (a compile-time
+// Cooley-Tukey split into 2-, 3-, 4-, 5- and 8-point DFTs with its twiddles
+// folded into immediates) and stored back. With k = q_1 + R_1 (q_2 + R_2 (q_3
+// + ...)) and rev(k) = sum_p q_p m_p, two orders are used:
+//  - decimation in frequency (the default): natural-order input, so the grid
+//    row lands in shared memory by bulk asynchronous copies (or, with a split,
+//    in coalesced order); passes p = 1..s multiply output q of butterfly j by
+//    w_{L_p}^{j q} after the DFT; output k ends up at position rev(k), which
+//    the unpacking step reads;
+//  - decimation in time: input k stored at position rev(k) (as the polynomial
+//    scatter can write it, or by per-point asynchronous copies), passes p =
+//    s..1 multiplying input r by w_{L_p}^{j r} before the DFT, output in
+//    natural order.
 #include <algorithm>
 #include <utility>
 
@@ -156,12 +162,35 @@ template <> struct Codelet<4> { static __device__ __forceinline__ void run(Cplx<
 template <> struct Codelet<5> { static __device__ __forceinline__ void run(Cplx<float>* v) { Dft<float, 5>::run(v); } };
 template <> struct Codelet<8> { static __device__ __forceinline__ void run(Cplx<float>* v) { Dft<float, 8>::run(v); } };
 
-// One decimation-in-time pass of radix R over L points in place. The
-// twiddles w^r (w = w_{L_p}^j), r = 1..R-1, are built from the four anchors
-// w, w^2, w^3, w^4 of row j (shared memory) as (w^4)^(r/4) w^(r mod 4): at
-// most R/4 + 1 rounded complex products per twiddle.
+// The twiddles w^r (w = w_{L_p}^j, row j of the pass's anchors), r = 1..R-1,
+// applied to v[r]: built from the four anchors w, w^2, w^3, w^4 of row j
+// (shared memory) as (w^4)^(r/4) w^(r mod 4), at most R/4 + 1 rounded
+// complex products per twiddle.
 template <int R>
-__device__ __forceinline__ void dit_pass(Cplx<float>* __restrict__ s, int L, int m, const float4* __restrict__ anc,
+__device__ __forceinline__ void apply_twiddles(Cplx<float>* v, const float4* __restrict__ anc, int j) {
+  const float4 a01 = anc[2 * j], a23 = anc[2 * j + 1];
+  const Cplx<float> w1{a01.x, a01.y}, w2{a01.z, a01.w}, w3{a23.x, a23.y}, w4{a23.z, a23.w};
+  Cplx<float> pw = w4;  // (w^4)^(q4) for q4 >= 1
+#pragma unroll
+  for (int q4 = 0; 4 * q4 < R; ++q4) {
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int r = 4 * q4 + rr;
+      if (r == 0 || r >= R) continue;
+      Cplx<float> t;
+      if (q4 == 0) t = rr == 1 ? w1 : (rr == 2 ? w2 : w3);
+      else if (rr == 0) t = pw;
+      else t = cmul(pw, rr == 1 ? w1 : (rr == 2 ? w2 : w3));
+      v[r] = cmul(v[r], t);
+    }
+    if (q4 >= 1) pw = cmul(pw, w4);
+  }
+}
+
+// One pass of radix R and stride m over L points in place: decimation in
+// time twiddles the inputs, decimation in frequency the outputs.
+template <int R, bool DIF>
+__device__ __forceinline__ void fft_pass(Cplx<float>* __restrict__ s, int L, int m, const float4* __restrict__ anc,
                                          int nth) {
   const int nbf = L / R;
   const unsigned mm = magic_of((unsigned)m);
@@ -172,52 +201,55 @@ __device__ __forceinline__ void dit_pass(Cplx<float>* __restrict__ s, int L, int
     Cplx<float> v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = s[base + r * m];
-    if (m > 1) {
-      const float4 a01 = anc[2 * j], a23 = anc[2 * j + 1];
-      const Cplx<float> w1{a01.x, a01.y}, w2{a01.z, a01.w}, w3{a23.x, a23.y}, w4{a23.z, a23.w};
-      Cplx<float> pw = w4;  // (w^4)^(q4) for q4 >= 1
-#pragma unroll
-      for (int q4 = 0; 4 * q4 < R; ++q4) {
-#pragma unroll
-        for (int rr = 0; rr < 4; ++rr) {
-          const int r = 4 * q4 + rr;
-          if (r == 0 || r >= R) continue;
-          Cplx<float> t;
-          if (q4 == 0) t = rr == 1 ? w1 : (rr == 2 ? w2 : w3);
-          else if (rr == 0) t = pw;
-          else t = cmul(pw, rr == 1 ? w1 : (rr == 2 ? w2 : w3));
-          v[r] = cmul(v[r], t);
-        }
-        if (q4 >= 1) pw = cmul(pw, w4);
-      }
-    }
+    if (!DIF && m > 1) apply_twiddles<R>(v, anc, j);
     Codelet<R>::run(v);
+    if (DIF && m > 1) apply_twiddles<R>(v, anc, j);
 #pragma unroll
     for (int q = 0; q < R; ++q) s[base + q * m] = v[q];
   }
 }
 
-__device__ __forceinline__ void run_pass(int R, Cplx<float>* s, int L, int m, const float4* anc, int nth) {
+template <bool DIF>
+__device__ __forceinline__ void run_pass_t(int R, Cplx<float>* s, int L, int m, const float4* anc, int nth) {
   switch (R) {
-    case 2: dit_pass<2>(s, L, m, anc, nth); break;
-    case 3: dit_pass<3>(s, L, m, anc, nth); break;
-    case 4: dit_pass<4>(s, L, m, anc, nth); break;
-    case 5: dit_pass<5>(s, L, m, anc, nth); break;
-    case 6: dit_pass<6>(s, L, m, anc, nth); break;
-    case 8: dit_pass<8>(s, L, m, anc, nth); break;
-    case 9: dit_pass<9>(s, L, m, anc, nth); break;
-    case 10: dit_pass<10>(s, L, m, anc, nth); break;
-    case 12: dit_pass<12>(s, L, m, anc, nth); break;
-    case 15: dit_pass<15>(s, L, m, anc, nth); break;
-    case 16: dit_pass<16>(s, L, m, anc, nth); break;
-    case 18: dit_pass<18>(s, L, m, anc, nth); break;
-    case 20: dit_pass<20>(s, L, m, anc, nth); break;
-    case 24: dit_pass<24>(s, L, m, anc, nth); break;
-    case 25: dit_pass<25>(s, L, m, anc, nth); break;
-    case 27: dit_pass<27>(s, L, m, anc, nth); break;
-    case 30: dit_pass<30>(s, L, m, anc, nth); break;
-    case 32: dit_pass<32>(s, L, m, anc, nth); break;
+    case 2: fft_pass<2, DIF>(s, L, m, anc, nth); break;
+    case 3: fft_pass<3, DIF>(s, L, m, anc, nth); break;
+    case 4: fft_pass<4, DIF>(s, L, m, anc, nth); break;
+    case 5: fft_pass<5, DIF>(s, L, m, anc, nth); break;
+    case 6: fft_pass<6, DIF>(s, L, m, anc, nth); break;
+    case 8: fft_pass<8, DIF>(s, L, m, anc, nth); break;
+    case 9: fft_pass<9, DIF>(s, L, m, anc, nth); break;
+    case 10: fft_pass<10, DIF>(s, L, m, anc, nth); break;
+    case 12: fft_pass<12, DIF>(s, L, m, anc, nth); break;
+    case 15: fft_pass<15, DIF>(s, L, m, anc, nth); break;
+    case 16: fft_pass<16, DIF>(s, L, m, anc, nth); break;
+    case 18: fft_pass<18, DIF>(s, L, m, anc, nth); break;
+    case 20: fft_pass<20, DIF>(s, L, m, anc, nth); break;
+    case 24: fft_pass<24, DIF>(s, L, m, anc, nth); break;
+    case 25: fft_pass<25, DIF>(s, L, m, anc, nth); break;
+    case 27: fft_pass<27, DIF>(s, L, m, anc, nth); break;
+    case 30: fft_pass<30, DIF>(s, L, m, anc, nth); break;
+    case 32: fft_pass<32, DIF>(s, L, m, anc, nth); break;
     default: break;  // the host plans only the radices above
+  }
+}
+
+// Entry p of a per-pass array, selected without indexing it at run time (a
+// run-time index would move the kernel parameter into local memory).
+__device__ __forceinline__ int pick(const int (&a)[kMaxAssetPasses], int p) {
+  static_assert(kMaxAssetPasses == 4, "pick() selects among four entries");
+  return p == 0 ? a[0] : p == 1 ? a[1] : p == 2 ? a[2] : a[3];
+}
+
+// All passes of the local transform in the plan's order for its direction.
+__device__ __forceinline__ void run_passes(const AssetFft& f, Cplx<float>* s, const float4* anc, int nth) {
+  for (int i = 0; i < f.npass; ++i) {
+    const int p = f.dif ? i : f.npass - 1 - i;
+    const int R = pick(f.rad, p), m = pick(f.stride, p);
+    const float4* a = anc + 2 * pick(f.tw_off, p);
+    if (f.dif) run_pass_t<true>(R, s, f.nl, m, a, nth);
+    else run_pass_t<false>(R, s, f.nl, m, a, nth);
+    __syncthreads();
   }
 }
 
@@ -234,6 +266,22 @@ __device__ __forceinline__ int digit_rev(int j, const AssetFft& f, const unsigne
     }
   }
   return pos;
+}
+
+// Shared-memory position of local output k: rev(k) after decimation in
+// frequency (from the two digit-reversal tables: k = x + rev_lo y has
+// rev(k) = T_lo[x] + T_hi[y], T_lo holding the first two digits' terms and
+// T_hi the rest), k after decimation in time.
+struct RevTab {
+  const int* lo;
+  const int* hi;
+  int B;
+  unsigned mB;
+};
+__device__ __forceinline__ int out_pos(int k, const AssetFft& f, const RevTab& t) {
+  if (!f.dif) return k;
+  const int y = fast_div(k, t.B, t.mB);
+  return t.lo[k - y * t.B] + t.hi[y];
 }
 
 // Byte offset of the anchor rows in shared memory: after the nl complex
@@ -271,9 +319,9 @@ constexpr int kPairBatch = 4;     // the same for the cluster variant (more valu
 // terms to the stored ones and clears both words for the next launch. The
 // sum of two rounded terms is the same whichever CTA comes first.
 template <int NTH>
-__device__ __forceinline__ void pair_terms(Cplx<float>* s, const AssetFft& f, int c, const Cplx<float>* __restrict__ U,
-                                           const float* __restrict__ decon, Cplx<float>* oa, int* sync,
-                                           int* status) {
+__device__ __forceinline__ void pair_terms(Cplx<float>* s, const AssetFft& f, const RevTab& rt, int c,
+                                           const Cplx<float>* __restrict__ U, const float* __restrict__ decon,
+                                           Cplx<float>* oa, int* sync, int* status) {
   const int L = f.nl;
   const int cp = 3 - c;
   const int Qc = c <= f.N ? (f.N - c) / 3 + 1 : 0;
@@ -281,7 +329,7 @@ __device__ __forceinline__ void pair_terms(Cplx<float>* s, const AssetFft& f, in
   for (int q = threadIdx.x; q < Qc + Qp; q += NTH) {
     const bool own = q < Qc;
     const int k = own ? c + 3 * q : cp + 3 * (q - Qc);
-    const int slot = own ? q : L - 1 - (q - Qc);
+    const int slot = out_pos(own ? q : L - 1 - (q - Qc), f, rt);
     const float dk = __ldg(decon + k);
     const Cplx<float> u = U[k];
     const Cplx<float> z = own ? s[slot] : cconj(s[slot]);
@@ -298,7 +346,7 @@ __device__ __forceinline__ void pair_terms(Cplx<float>* s, const AssetFft& f, in
   if (s_role == 0) {
     for (int q = threadIdx.x; q < Qc + Qp; q += NTH) {
       const bool own = q < Qc;
-      oa[own ? c + 3 * q : cp + 3 * (q - Qc)] = s[own ? q : L - 1 - (q - Qc)];
+      oa[own ? c + 3 * q : cp + 3 * (q - Qc)] = s[out_pos(own ? q : L - 1 - (q - Qc), f, rt)];
     }
     __threadfence();
     __syncthreads();
@@ -330,7 +378,7 @@ __device__ __forceinline__ void pair_terms(Cplx<float>* s, const AssetFft& f, in
   for (int q = threadIdx.x; q < Qc + Qp; q += NTH) {
     const bool own = q < Qc;
     const int k = own ? c + 3 * q : cp + 3 * (q - Qc);
-    const Cplx<float> t = s[own ? q : L - 1 - (q - Qc)];
+    const Cplx<float> t = s[out_pos(own ? q : L - 1 - (q - Qc), f, rt)];
     const float2 o = __ldcg(reinterpret_cast<const float2*>(oa + k));
     oa[k] = Cplx<float>{t.x + o.x, t.y + o.y};
   }
@@ -361,12 +409,13 @@ __global__ void __launch_bounds__(NTH, 512 / NTH)
 #pragma unroll
   for (int p = 0; p < kMaxAssetPasses; ++p) mr[p] = magic_of((unsigned)f.rad[p]);
 
-  // load into digit-reversed order (with the first radix-2 step when S = 2)
+  // load in the order of the transform's direction (with the first radix-S
+  // step when S > 1)
   const Cplx<float>* z = reinterpret_cast<const Cplx<float>*>(grid) + (size_t)a * f.n;
-  if (f.pre_perm) {
-    // the spread kernel already stored the row in digit-reversed order: one
-    // bulk asynchronous copy of the whole row (the anchors' cp.async copies
-    // are waited for below)
+  if (f.pre_perm || (f.dif && f.split == 1)) {
+    // the row as stored (natural order, or digit-reversed by the polynomial
+    // scatter): bulk asynchronous copies of the whole row, 16-byte aligned
+    // since n is even (the anchors' cp.async copies are waited for below)
     __shared__ __align__(8) uint64_t bar;
     const uint32_t bytes = (uint32_t)f.n * 8u;
     if (threadIdx.x == 0) {
@@ -430,7 +479,7 @@ __global__ void __launch_bounds__(NTH, 512 / NTH)
             y = Cplx<float>{fmaf(hs, df.y, fmaf(-0.5f, sm.x, z0[u].x)), fmaf(-hs, df.x, fmaf(-0.5f, sm.y, z0[u].y))};
             y = cmul(y, w[u]);
           }
-          s[digit_rev(j, f, mr)] = y;
+          s[f.dif ? j : digit_rev(j, f, mr)] = y;
         }
       }
     }
@@ -449,17 +498,42 @@ __global__ void __launch_bounds__(NTH, 512 / NTH)
 #pragma unroll
       for (int u = 0; u < kLoadBatch; ++u) {
         const int j = j0 + u * NTH;
-        if (j < L) s[digit_rev(j, f, mr)] = c == 0 ? cadd(y[u], z1[u]) : cmul(csub(y[u], z1[u]), w[u]);
+        if (j < L)
+          s[f.dif ? j : digit_rev(j, f, mr)] = c == 0 ? cadd(y[u], z1[u]) : cmul(csub(y[u], z1[u]), w[u]);
       }
     }
   }
+  // digit-reversal tables for the unpacking step (decimation in frequency)
+  RevTab rt{};
+  if (f.dif) {
+    int* tlo = reinterpret_cast<int*>(smem_raw + anchor_offset(f.nl) + (size_t)f.tw_rows * 32);
+    int* thi = tlo + f.rev_lo;
+    const int R0 = f.rad[0], R1 = f.npass >= 2 ? f.rad[1] : 1;
+    for (int x = threadIdx.x; x < f.rev_lo; x += NTH) {
+      const int q1 = fast_div(x, R0, mr[0]);
+      tlo[x] = (x - q1 * R0) * f.stride[0] + (R1 > 1 ? q1 * f.stride[1] : 0);
+    }
+    for (int y = threadIdx.x; y < f.rev_hi; y += NTH) {
+      int pos = 0, r = y;
+#pragma unroll
+      for (int p = 2; p < kMaxAssetPasses; ++p) {
+        if (p < f.npass) {
+          const int R = f.rad[p];
+          const int q = fast_div(r, R, mr[p]);
+          pos += (r - q * R) * f.stride[p];
+          r = q;
+        }
+      }
+      thi[y] = pos;
+    }
+    rt.lo = tlo;
+    rt.hi = thi;
+    rt.B = f.rev_lo;
+    rt.mB = magic_of((unsigned)f.rev_lo);
+  }
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
   __syncthreads();
-
-  for (int p = f.npass - 1; p >= 0; --p) {
-    run_pass(f.rad[p], s, L, f.stride[p], anc + 2 * f.tw_off[p], NTH);
-    __syncthreads();
-  }
+  run_passes(f, s, anc, NTH);
 
   // unpack the real-input transform and deconvolve (Eq. (14)):
   // G(k) = (Z_k + conj Z_{n-k}) / 2 + w_{2n}^k (Z_k - conj Z_{n-k}) / (2i)
@@ -472,7 +546,7 @@ __global__ void __launch_bounds__(NTH, 512 / NTH)
   const int S = f.split;
   Cplx<float>* oa = out + (size_t)a * (f.N + 1);
   if (S == 3 && c != 0) {
-    pair_terms<NTH>(s, f, c, U, decon, oa, sync + 2 * a, status);
+    pair_terms<NTH>(s, f, rt, c, U, decon, oa, sync + 2 * a, status);
     return;
   }
   for (int q0 = threadIdx.x; c + S * q0 <= f.N; q0 += NTH * kUnpackBatch) {
@@ -492,8 +566,8 @@ __global__ void __launch_bounds__(NTH, 512 / NTH)
       const int k = c + S * q;
       if (k <= f.N) {
         const int qn = c == 0 ? (q == 0 ? 0 : L - q) : L - 1 - q;
-        const Cplx<float> Zk = s[q];
-        const Cplx<float> Zc = cconj(s[qn]);
+        const Cplx<float> Zk = s[out_pos(q, f, rt)];
+        const Cplx<float> Zc = cconj(s[out_pos(qn, f, rt)]);
         const Cplx<float> E = {0.5f * (Zk.x + Zc.x), 0.5f * (Zk.y + Zc.y)};
         const Cplx<float> dlt = csub(Zk, Zc);
         const Cplx<float> O = {0.5f * dlt.y, -0.5f * dlt.x};  // (Z_k - conj Z_{n-k}) / (2i)
@@ -541,10 +615,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 512 / NTH)
   }
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
   __syncthreads();
-  for (int p = f.npass - 1; p >= 0; --p) {
-    run_pass(f.rad[p], s, L, f.stride[p], anc + 2 * f.tw_off[p], NTH);
-    __syncthreads();
-  }
+  run_passes(f, s, anc, NTH);  // decimation in time (f.dif = 0)
   cluster_sync_all();  // both halves transformed and visible to the partner
   const uint32_t peer = peer_addr(s, c ^ 1u);
   Cplx<float>* oa = out + (size_t)a * (f.N + 1);
@@ -616,7 +687,9 @@ bool asset_fft_radix_ok(int R) {
   }
 }
 
-size_t asset_fft_smem(const AssetFft& f) { return anchor_offset(f.nl) + (size_t)f.tw_rows * 32; }
+size_t asset_fft_smem(const AssetFft& f) {
+  return anchor_offset(f.nl) + (size_t)f.tw_rows * 32 + (f.dif ? (size_t)(f.rev_lo + f.rev_hi) * 4 : 0);
+}
 
 int asset_fft_threads(int split) { return split >= 2 ? 256 : 512; }
 

@@ -142,7 +142,8 @@ def test_per_asset_fft_radix_plans(N, variant, split):
         out = run(dict(tol=tl["tol"], kernel=kernel, basis="dirichlet", prec="bf16x3", fft_algo=variant), ev, N)
         info = out["info"]
         n = info["Mr"] // 2
-        want = split if split else 3  # D = 3 < SMs: a pair by default
+        # by default one CTA per asset; the largest grid only as a cluster pair
+        want = split if split else (3 if N == 14399 else 1)
         if (N == 14399 and split == 1) or (want == 4 and n % 3):
             # n = 28800: the whole grid does not fit one CTA's shared memory;
             # a three-way split needs 3 | n
