@@ -620,9 +620,19 @@ mm_status coeffs_impl(mm_plan p, const int64_t* off, const double* t, const doub
                       double t1, void* coeffs, int32_t* N_used, cudaStream_t st) {
   const int D = p->D;
   p->last = st;
+  // with a given cutoff the grid is configured first, so that k_bounds also
+  // computes the call's cell scales
+  int64_t Mr_known = 0;
+  if (N > 0) {
+    if (N > p->desc.N_max) return MM_ERR_CUTOFF;
+    if (p->desc.basis == MM_BASIS_FEJER && N < 1) return MM_ERR_CUTOFF;
+    const mm_status rc = configure(p, N);
+    if (rc != MM_OK) return rc;
+    Mr_known = p->Mr;
+  }
   {
     StageScope sc(p, MM_STAGE_PREP, st);
-    MM_CUDA(launch_bounds(off, t, D, p->gsize, p->desc.max_events, t0, t1, p->bounds, p->status, st));
+    MM_CUDA(launch_bounds(off, t, D, p->gsize, p->desc.max_events, t0, t1, Mr_known, p->bounds, p->status, st));
   }
   if (N <= 0 && p->G > 1) return MM_ERR_CUTOFF;  // a batch sweeps given cutoffs
   if (N <= 0) {
@@ -1162,7 +1172,7 @@ mm_status mm_nyquist(mm_plan p, const int64_t* d_offsets, const double* d_t, dou
   p->last = st;
   {
     StageScope sc(p, MM_STAGE_PREP, st);
-    MM_CUDA(launch_bounds(d_offsets, d_t, p->D, p->gsize, p->desc.max_events, t0, t1, p->bounds, p->status, st));
+    MM_CUDA(launch_bounds(d_offsets, d_t, p->D, p->gsize, p->desc.max_events, t0, t1, 0, p->bounds, p->status, st));
   }
   {
     StageScope sc(p, MM_STAGE_PREP, st, 2);

@@ -92,9 +92,11 @@ struct KernelPoly {
 struct Rescale {
   double t0, t1;             // window used (data minimum / maximum or caller's)
   long long t0_fix;          // t0 in units of 2^-F
-  unsigned long long S;      // 64-bit multiplier, in [2^63, 2^64)
+  unsigned long long S;      // cell scale of grid scale_Mr: 64-bit multiplier, in [2^63, 2^64)
   int F;                     // fractional bits of the time fixed point
   int sh;                    // right shift of the 128-bit product, 0..127
+  float s_hi, s_lo;          // the float-pair cell scale of the same grid
+  long long scale_Mr;        // grid size the cell scales belong to (0: not computed)
 };
 constexpr int kUFrac = 40;   // fractional bits of u_fix
 
@@ -155,8 +157,10 @@ constexpr int kMaxEppsAssets = 12;
 
 // ---------------------------------------------------------------- launchers
 // Each returns cudaGetLastError() of its launch.
+// Mr > 0: also the cell scales of grid Mr (so later kernels do no float64
+// arithmetic for them); 0 when the grid is not known yet.
 cudaError_t launch_bounds(const int64_t* off, const double* t, int D, int gsize, int64_t max_events,
-                          double w0, double w1, Rescale* rs, int* status, cudaStream_t s);
+                          double w0, double w1, int64_t Mr, Rescale* rs, int* status, cudaStream_t s);
 cudaError_t launch_group_scales(const Rescale* rs, int G, int64_t Mr, GroupScale* out, const int* status,
                                 cudaStream_t s);
 size_t group_scale_bytes();

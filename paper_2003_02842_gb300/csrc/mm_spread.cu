@@ -39,8 +39,8 @@ namespace mmgpu {
 // non-decreasing and lie in [0, max_events], so a malformed offsets array
 // anywhere leaves every read in bounds.
 __global__ void k_bounds(const int64_t* __restrict__ off, const double* __restrict__ t, int D, int gsize,
-                         int64_t max_events, double w0, double w1, Rescale* rs, int* status) {
-  __shared__ double s_lo[256], s_hi[256];
+                         int64_t max_events, double w0, double w1, int64_t Mr, Rescale* rs, int* status) {
+  __shared__ double s_lo[8], s_hi[8];
   __shared__ int s_bad;
   int* gate = status + 1;
   const int g = blockIdx.x;
@@ -78,17 +78,23 @@ __global__ void k_bounds(const int64_t* __restrict__ off, const double* __restri
     }
   }
   if (outwin) atomicOr(&s_bad, 2);
-  s_lo[threadIdx.x] = lo;
-  s_hi[threadIdx.x] = hi;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      s_lo[threadIdx.x] = fmin(s_lo[threadIdx.x], s_lo[threadIdx.x + w]);
-      s_hi[threadIdx.x] = fmax(s_hi[threadIdx.x], s_hi[threadIdx.x + w]);
-    }
-    __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
   }
+  if ((threadIdx.x & 31) == 0) {
+    s_lo[threadIdx.x >> 5] = lo;
+    s_hi[threadIdx.x >> 5] = hi;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      lo = fmin(lo, s_lo[w]);
+      hi = fmax(hi, s_hi[w]);
+    }
+    s_lo[0] = lo;
+    s_hi[0] = hi;
     const double t0 = window ? w0 : s_lo[0];
     const double t1 = window ? w1 : s_hi[0];
     int gt = 0;
@@ -106,6 +112,16 @@ __global__ void k_bounds(const int64_t* __restrict__ off, const double* __restri
       frexp(fmax(fabs(t0), fabs(t1)), &ex);  // max |t| < 2^ex
       r.F = 62 - (ex + 1);                   // |t_fix| < 2^61
       r.t0_fix = to_fix(t0, r.F);
+      if (Mr > 0) {
+        // the cell scales of this call's grid, once (float64 is slow here)
+        const UScale us = make_uscale(r, Mr);
+        const UScaleF usf = make_uscale_f(r, Mr);
+        r.S = us.S;
+        r.sh = us.sh;
+        r.s_hi = usf.s_hi;
+        r.s_lo = usf.s_lo;
+        r.scale_Mr = Mr;
+      }
     }
     rs[g] = r;
     if (gridDim.x == 1) *gate = gt;  // one problem: this call's gate
@@ -114,13 +130,13 @@ __global__ void k_bounds(const int64_t* __restrict__ off, const double* __restri
 }
 
 cudaError_t launch_bounds(const int64_t* off, const double* t, int D, int gsize, int64_t max_events, double w0,
-                          double w1, Rescale* rs, int* status, cudaStream_t s) {
+                          double w1, int64_t Mr, Rescale* rs, int* status, cudaStream_t s) {
   const int G = (D + gsize - 1) / gsize;
   if (G > 1) {
     cudaError_t e = cudaMemsetAsync(status + 1, 0, sizeof(int), s);  // the gate of this call
     if (e != cudaSuccess) return e;
   }
-  k_bounds<<<G, 256, 0, s>>>(off, t, D, gsize, max_events, w0, w1, rs, status);
+  k_bounds<<<G, 256, 0, s>>>(off, t, D, gsize, max_events, w0, w1, Mr, rs, status);
   return cudaGetLastError();
 }
 
@@ -215,20 +231,33 @@ __global__ void __launch_bounds__(256) k_prep(const int64_t* __restrict__ off, c
                                               T* __restrict__ rd, T* __restrict__ rv, int* status) {
   __shared__ UScale s_us;
   __shared__ UScaleF s_usf;
-  __shared__ Rescale s_rs;
   __shared__ int s_flags;
-  if (*gate) return;  // uniform
+  // one round of loads: the gate, the event count and the call's rescaling
+  // (with its cell scales when k_bounds knew the grid); then each thread's
+  // event loads are in flight while warp 0 finds the block's asset
+  const int gated = *gate;
+  const int64_t ntot = off[D];
+  Rescale rs0{};
+  if (!gsc) rs0 = *rsp;
+  if (gated) return;  // uniform
+  const bool scales = gsc || rs0.scale_Mr == Mr;  // uniform
+  const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double th = 0.0, tn = 0.0, p0 = 0.0, p1 = 0.0;
+  if (h < ntot) {
+    th = t[h];
+    p0 = logp[h];
+    if (h + 1 < ntot) {
+      tn = t[h + 1];
+      p1 = logp[h + 1];
+    }
+  }
   if (threadIdx.x == 0) {
-    if (!gsc) {
-      s_rs = *rsp;
-      if (sizeof(T) == 8) s_us = make_uscale(s_rs, Mr);
-      else s_usf = make_uscale_f(s_rs, Mr);
+    if (!scales) {
+      if (sizeof(T) == 8) s_us = make_uscale(rs0, Mr);
+      else s_usf = make_uscale_f(rs0, Mr);
     }
     s_flags = 0;
   }
-  __syncthreads();
-  const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t ntot = off[D];
   // asset of the block's first event (a 32-ary search by warp 0, a couple of
   // dependent loads), then each thread walks forward to its own asset
   __shared__ int s_a0;
@@ -262,18 +291,24 @@ __global__ void __launch_bounds__(256) k_prep(const int64_t* __restrict__ off, c
     if (h + 1 < off[lo + 1]) {
       // this event's problem: its fixed-point scale (batched form) or the
       // call's single one
-      Rescale rs = s_rs;
-      UScale us = s_us;
-      UScaleF usf = s_usf;
+      Rescale rs = rs0;
+      UScale us;
+      UScaleF usf;
       if (gsc) {
         const GroupScale q = gsc[lo / gsize];
         rs.t0_fix = q.t0_fix;
         rs.F = q.F;
         us = q.us;
         usf = q.usf;
+      } else if (scales) {
+        us.S = rs0.S;
+        us.sh = rs0.sh;
+        usf.s_hi = rs0.s_hi;
+        usf.s_lo = rs0.s_lo;
+      } else {
+        us = s_us;
+        usf = s_usf;
       }
-      const double th = t[h], tn = t[h + 1];
-      const double p0 = logp[h], p1 = logp[h + 1];
       const long long kh = order_key(th), kn = order_key(tn);
       if (!(kh < kn)) flags |= (kh == kn) ? ST_DUPLICATE : ST_UNSORTED;
       int b0 = kNoCell;
