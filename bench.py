@@ -36,10 +36,10 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # dram bytes (read + write) per launch of the dominant kernel, from the ncu
 # capture summarised in profiles/ (None until a capture of the current kernel)
 NCU_TRAFFIC = {
-    # profiles/c3_block_D100_N10000_kernels_ncu.md (default configuration)
+    # from the ncu capture of the block workload in its default configuration
     ("spread", "c3", "bf16x3", "es"): 9225216,
-    ("fft", "c3", "bf16x3", "es"): 16520448,
-    ("prep", "c3", "bf16x3", "es"): 12272896,
+    ("fft", "c3", "bf16x3", "es"): 16451328,
+    ("prep", "c3", "bf16x3", "es"): 12273408,
     ("gram", "c3", "bf16x3", "es"): 8143360,
 }
 
