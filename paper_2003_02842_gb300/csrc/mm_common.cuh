@@ -232,4 +232,30 @@ mm_status plan_flags_to_status(int flags);
 cudaError_t launch_epps(int Dg, bool fejer, const void* coef, int ld, const int* cut, int ncut, int G, float* sigma,
                         float* R, int* status, int grid, cudaStream_t s);
 
+// ------------------------------------------------- programmatic launches
+// The hot path's kernels are launched with programmatic stream
+// serialization: a kernel may be scheduled before its predecessor in the
+// stream has finished, runs only set-up that touches neither global memory
+// written by earlier kernels nor memory they read, then waits at pdl_wait()
+// until the predecessor has completed and its writes are visible (a no-op
+// when launched normally). pdl_trigger() lets the successor be scheduled.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 }  // namespace mmgpu

@@ -391,9 +391,42 @@ __global__ void __launch_bounds__(NTH, 512 / NTH)
                 const float* __restrict__ decon, Cplx<float>* __restrict__ out, const int* __restrict__ gate,
                 int* status, int* __restrict__ sync) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (*gate) return;  // uniform: the whole block leaves
   Cplx<float>* s = reinterpret_cast<Cplx<float>*>(smem_raw);
   float4* anc = reinterpret_cast<float4*>(smem_raw + anchor_offset(f.nl));  // twiddle anchors, 32 B per row
+  unsigned mr[kMaxAssetPasses];
+#pragma unroll
+  for (int p = 0; p < kMaxAssetPasses; ++p) mr[p] = magic_of((unsigned)f.rad[p]);
+  // digit-reversal tables for the unpacking step (decimation in frequency)
+  RevTab rt{};
+  if (f.dif) {
+    int* tlo = reinterpret_cast<int*>(smem_raw + anchor_offset(f.nl) + (size_t)f.tw_rows * 32);
+    int* thi = tlo + f.rev_lo;
+    const int R0 = f.rad[0], R1 = f.npass >= 2 ? f.rad[1] : 1;
+    for (int x = threadIdx.x; x < f.rev_lo; x += NTH) {
+      const int q1 = fast_div(x, R0, mr[0]);
+      tlo[x] = (x - q1 * R0) * f.stride[0] + (R1 > 1 ? q1 * f.stride[1] : 0);
+    }
+    for (int y = threadIdx.x; y < f.rev_hi; y += NTH) {
+      int pos = 0, r = y;
+#pragma unroll
+      for (int p = 2; p < kMaxAssetPasses; ++p) {
+        if (p < f.npass) {
+          const int R = f.rad[p];
+          const int q = fast_div(r, R, mr[p]);
+          pos += (r - q * R) * f.stride[p];
+          r = q;
+        }
+      }
+      thi[y] = pos;
+    }
+    rt.lo = tlo;
+    rt.hi = thi;
+    rt.B = f.rev_lo;
+    rt.mB = magic_of((unsigned)f.rev_lo);
+  }
+  pdl_wait();         // the grid comes from the spreading kernel
+  if (*gate) return;  // uniform: the whole block leaves
+  pdl_trigger();      // the contraction may take the SMs this launch leaves free
   {
     // anchor rows: 16-byte asynchronous copies, waited for with the grid
     const float4* src = reinterpret_cast<const float4*>(tw);
@@ -405,9 +438,6 @@ __global__ void __launch_bounds__(NTH, 512 / NTH)
   const int c = blockIdx.x;  // which half of the modes (S = 2), else 0
   const int a = blockIdx.y;
   const int L = f.nl;
-  unsigned mr[kMaxAssetPasses];
-#pragma unroll
-  for (int p = 0; p < kMaxAssetPasses; ++p) mr[p] = magic_of((unsigned)f.rad[p]);
 
   // load in the order of the transform's direction (with the first radix-S
   // step when S > 1)
@@ -502,34 +532,6 @@ __global__ void __launch_bounds__(NTH, 512 / NTH)
           s[f.dif ? j : digit_rev(j, f, mr)] = c == 0 ? cadd(y[u], z1[u]) : cmul(csub(y[u], z1[u]), w[u]);
       }
     }
-  }
-  // digit-reversal tables for the unpacking step (decimation in frequency)
-  RevTab rt{};
-  if (f.dif) {
-    int* tlo = reinterpret_cast<int*>(smem_raw + anchor_offset(f.nl) + (size_t)f.tw_rows * 32);
-    int* thi = tlo + f.rev_lo;
-    const int R0 = f.rad[0], R1 = f.npass >= 2 ? f.rad[1] : 1;
-    for (int x = threadIdx.x; x < f.rev_lo; x += NTH) {
-      const int q1 = fast_div(x, R0, mr[0]);
-      tlo[x] = (x - q1 * R0) * f.stride[0] + (R1 > 1 ? q1 * f.stride[1] : 0);
-    }
-    for (int y = threadIdx.x; y < f.rev_hi; y += NTH) {
-      int pos = 0, r = y;
-#pragma unroll
-      for (int p = 2; p < kMaxAssetPasses; ++p) {
-        if (p < f.npass) {
-          const int R = f.rad[p];
-          const int q = fast_div(r, R, mr[p]);
-          pos += (r - q * R) * f.stride[p];
-          r = q;
-        }
-      }
-      thi[y] = pos;
-    }
-    rt.lo = tlo;
-    rt.hi = thi;
-    rt.B = f.rev_lo;
-    rt.mB = magic_of((unsigned)f.rev_lo);
   }
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
   __syncthreads();
@@ -715,14 +717,14 @@ cudaError_t launch_fft_asset(const float* grid, const AssetFft& f, int D, const 
                                                  status + 1);
   } else if (asset_fft_threads(f.split) == 256) {
     if ((e = set(k_fft_asset<256>)) != cudaSuccess) return e;
-    k_fft_asset<256><<<grd, 256, smem, s>>>(grid, f, (const Cplx<float>*)W, (const Cplx<float>*)tw,
-                                            (const Cplx<float>*)U, (const float*)decon, (Cplx<float>*)coeffs,
-                                            status + 1, status, sync);
+    return launch_pdl(k_fft_asset<256>, grd, dim3(256), smem, s, grid, f, (const Cplx<float>*)W,
+                      (const Cplx<float>*)tw, (const Cplx<float>*)U, (const float*)decon, (Cplx<float>*)coeffs,
+                      (const int*)(status + 1), status, sync);
   } else {
     if ((e = set(k_fft_asset<512>)) != cudaSuccess) return e;
-    k_fft_asset<512><<<grd, 512, smem, s>>>(grid, f, (const Cplx<float>*)W, (const Cplx<float>*)tw,
-                                            (const Cplx<float>*)U, (const float*)decon, (Cplx<float>*)coeffs,
-                                            status + 1, status, sync);
+    return launch_pdl(k_fft_asset<512>, grd, dim3(512), smem, s, grid, f, (const Cplx<float>*)W,
+                      (const Cplx<float>*)tw, (const Cplx<float>*)U, (const float*)decon, (Cplx<float>*)coeffs,
+                      (const int*)(status + 1), status, sync);
   }
   return cudaGetLastError();
 }

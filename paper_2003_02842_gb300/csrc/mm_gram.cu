@@ -329,6 +329,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restr
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
+  pdl_wait();     // the coefficients come from the FFT kernel
+  pdl_trigger();  // the correlation epilogue may be scheduled
 
   const int chunk = g.chunk;
   Chunk<MODE> ca, cb;
@@ -428,15 +430,13 @@ cudaError_t launch_gram_tc(int mode, const void* coeffs, const GramParams& g, co
   if (mode == 0) {
     e = cudaFuncSetAttribute(k_gram_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_gram_tc<0><<<grd, kTcThreads, smem, s>>>((const float2*)coeffs, g, wsq, acc, status, done, sigma, R,
-                                                zero_next);
-  } else {
-    e = cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_gram_tc<1><<<grd, kTcThreads, smem, s>>>((const float2*)coeffs, g, wsq, acc, status, done, sigma, R,
-                                                zero_next);
+    return launch_pdl(k_gram_tc<0>, grd, dim3(kTcThreads), smem, s, (const float2*)coeffs, g, wsq, acc, status, done,
+                      sigma, R, zero_next);
   }
-  return cudaGetLastError();
+  e = cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(k_gram_tc<1>, grd, dim3(kTcThreads), smem, s, (const float2*)coeffs, g, wsq, acc, status, done,
+                    sigma, R, zero_next);
 }
 
 // Sigma and R from the FP32 accumulator of k_gram_tc (upper tile pairs only:
@@ -448,6 +448,8 @@ cudaError_t launch_gram_tc(int mode, const void* coeffs, const GramParams& g, co
 __global__ void __launch_bounds__(256) k_corr_acc(const float* __restrict__ acc, GramParams g, float* __restrict__ sigma,
                                                   float* __restrict__ R, float* __restrict__ zero_next, int* status) {
   __shared__ double s_inv_i[16], s_inv_j[16];
+  pdl_wait();  // the accumulator comes from the contraction kernel
+  pdl_trigger();
   const int li = threadIdx.x >> 4, lj = threadIdx.x & 15;
   const int j = blockIdx.x * 16 + lj;
   const int i = blockIdx.y * 16 + li;
@@ -483,8 +485,7 @@ __global__ void __launch_bounds__(256) k_corr_acc(const float* __restrict__ acc,
 cudaError_t launch_corr_acc(const float* acc, const GramParams& g, float* sigma, float* R, float* zero_next,
                             int* status, cudaStream_t s) {
   dim3 grd((g.Dp + 15) / 16, (g.D + 15) / 16);
-  k_corr_acc<<<grd, 256, 0, s>>>(acc, g, sigma, R, zero_next, status);
-  return cudaGetLastError();
+  return launch_pdl(k_corr_acc, grd, dim3(256), 0, s, acc, g, sigma, R, zero_next, status);
 }
 
 // ------------------------------------------------------------ reduce + R

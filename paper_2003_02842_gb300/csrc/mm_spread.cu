@@ -42,6 +42,8 @@ __global__ void k_bounds(const int64_t* __restrict__ off, const double* __restri
                          int64_t max_events, double w0, double w1, int64_t Mr, Rescale* rs, int* status) {
   __shared__ double s_lo[8], s_hi[8];
   __shared__ int s_bad;
+  pdl_wait();     // the previous call's kernels may still read the gate
+  pdl_trigger();  // prep may be scheduled (it waits for this kernel)
   int* gate = status + 1;
   const int g = blockIdx.x;
   const int i0 = g * gsize, i1 = min(i0 + gsize, D);
@@ -136,8 +138,7 @@ cudaError_t launch_bounds(const int64_t* off, const double* t, int D, int gsize,
     cudaError_t e = cudaMemsetAsync(status + 1, 0, sizeof(int), s);  // the gate of this call
     if (e != cudaSuccess) return e;
   }
-  k_bounds<<<G, 256, 0, s>>>(off, t, D, gsize, max_events, w0, w1, Mr, rs, status);
-  return cudaGetLastError();
+  return launch_pdl(k_bounds, dim3(G), dim3(256), 0, s, off, t, D, gsize, max_events, w0, w1, Mr, rs, status);
 }
 
 // Per-problem fixed-point cell scales for the grid size of this call.
@@ -234,7 +235,9 @@ __global__ void __launch_bounds__(256) k_prep(const int64_t* __restrict__ off, c
   __shared__ int s_flags;
   // one round of loads: the gate, the event count and the call's rescaling
   // (with its cell scales when k_bounds knew the grid); then each thread's
-  // event loads are in flight while warp 0 finds the block's asset
+  // event loads are in flight while warp 0 finds the block's asset. No event
+  // is read before the gate (k_bounds' validation of the offsets) is known.
+  pdl_wait();
   const int gated = *gate;
   const int64_t ntot = off[D];
   Rescale rs0{};
@@ -344,6 +347,7 @@ __global__ void __launch_bounds__(256) k_prep(const int64_t* __restrict__ off, c
   if (flags) atomicOr(&s_flags, flags);
   __syncthreads();
   if (threadIdx.x == 0 && s_flags) atomicOr(status, s_flags);
+  pdl_trigger();
 }
 
 template <typename T>
@@ -352,8 +356,8 @@ static cudaError_t launch_prep_t(const int64_t* off, const double* t, const doub
                                  T* rd, T* rv, int* status, cudaStream_t s) {
   if (max_events <= 0) return cudaSuccess;
   const int64_t blocks = (max_events + 255) / 256;
-  k_prep<T><<<(unsigned)blocks, 256, 0, s>>>(off, t, logp, rs, gsc, gsize, status + 1, D, Mr, rb0, rd, rv, status);
-  return cudaGetLastError();
+  return launch_pdl(k_prep<T>, dim3((unsigned)blocks), dim3(256), 0, s, off, t, logp, rs, gsc, gsize, status + 1, D,
+                    Mr, rb0, rd, rv, status);
 }
 
 cudaError_t launch_prep_f32(const int64_t* off, const double* t, const double* logp, const Rescale* rs,
@@ -599,7 +603,6 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_poly(const int64_t* _
   int* tile = reinterpret_cast<int*>(ev_v + EC);
   const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile);
   __shared__ float s_part[kSpreadThreads / 32];
-  if (*gate) return;  // uniform: the whole block leaves
   const int a = blockIdx.y;
   const int64_t L = (int64_t)blockIdx.x * p.tile;
   const int Tlen = (int)min((int64_t)p.tile, p.Mr - L);
@@ -608,6 +611,8 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_poly(const int64_t* _
     const int n4 = (Tlen + 3) / 4;
     for (int c = threadIdx.x; c < n4; c += kSpreadThreads) t4[c] = make_int4(0, 0, 0, 0);
   }
+  pdl_wait();         // the records come from the prep kernel
+  if (*gate) return;  // uniform: the whole block leaves
   TileRanges tr;
   tile_ranges(off, rb0, p, a, L, Tlen, tr);
   const int64_t ntot = tr.n2 + tr.n1 + tr.n0;
@@ -693,6 +698,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_poly(const int64_t* _
       const int2 v = t2[c2];
       gz[pos] = make_float2((float)v.x * inv, (float)v.y * inv);
     }
+    pdl_trigger();
     return;
   }
   float* g = grid + (int64_t)a * p.Mr + L;
@@ -706,6 +712,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_poly(const int64_t* _
   } else {
     for (int c = threadIdx.x; c < Tlen; c += kSpreadThreads) g[c] = (float)tile[c] * inv;
   }
+  pdl_trigger();
 }
 
 bool spread_poly_supported(int ntaps) {
@@ -722,8 +729,8 @@ cudaError_t launch_spread_poly(const int64_t* off, const int* rb0, const void* r
   auto go = [&](auto fn) -> cudaError_t {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fn<<<grd, kSpreadThreads, smem, s>>>(off, rb0, (const float*)rd, (const float*)rv, status + 1, p, poly, grid);
-    return cudaGetLastError();
+    return launch_pdl(fn, grd, dim3(kSpreadThreads), smem, s, off, rb0, (const float*)rd, (const float*)rv,
+                      (const int*)(status + 1), p, poly, grid);
   };
   switch (nt) {
     case 9: return go(k_spread_poly<9>);
