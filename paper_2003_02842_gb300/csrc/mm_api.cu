@@ -542,7 +542,9 @@ mm_status configure(mm_plan p, int N) {
     }
   }
   // decimation in frequency (natural-order input) except where the input
-  // arrives digit-reversed: the scatter's permuted grid, the cluster pair
+  // arrives digit-reversed (the scatter's permuted grid) and for the cluster
+  // pair, whose joining step reads half its values from the partner's shared
+  // memory: those reads must be contiguous (natural output order)
   af.dif = !af.pre_perm && !af.pair;
   p->afft = af;
   p->use_afft = afft && !s.fused;

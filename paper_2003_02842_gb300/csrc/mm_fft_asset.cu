@@ -288,6 +288,39 @@ __device__ __forceinline__ int out_pos(int k, const AssetFft& f, const RevTab& t
 // points, rounded up to 16 bytes (nl may be odd) for the float4 accesses.
 __host__ __device__ __forceinline__ size_t anchor_offset(int nl) { return ((size_t)nl * 8 + 15) & ~(size_t)15; }
 
+// The two digit-reversal tables of a decimation-in-frequency plan, built in
+// shared memory after the anchor rows (from the plan alone: no global reads).
+template <int NTH>
+__device__ __forceinline__ RevTab build_rev_tables(const AssetFft& f, unsigned char* smem_raw, const unsigned* mr) {
+  RevTab rt{};
+  if (!f.dif) return rt;
+  int* tlo = reinterpret_cast<int*>(smem_raw + anchor_offset(f.nl) + (size_t)f.tw_rows * 32);
+  int* thi = tlo + f.rev_lo;
+  const int R0 = f.rad[0], R1 = f.npass >= 2 ? f.rad[1] : 1;
+  for (int x = threadIdx.x; x < f.rev_lo; x += NTH) {
+    const int q1 = fast_div(x, R0, mr[0]);
+    tlo[x] = (x - q1 * R0) * f.stride[0] + (R1 > 1 ? q1 * f.stride[1] : 0);
+  }
+  for (int y = threadIdx.x; y < f.rev_hi; y += NTH) {
+    int pos = 0, r = y;
+#pragma unroll
+    for (int p = 2; p < kMaxAssetPasses; ++p) {
+      if (p < f.npass) {
+        const int R = f.rad[p];
+        const int q = fast_div(r, R, mr[p]);
+        pos += (r - q * R) * f.stride[p];
+        r = q;
+      }
+    }
+    thi[y] = pos;
+  }
+  rt.lo = tlo;
+  rt.hi = thi;
+  rt.B = f.rev_lo;
+  rt.mB = magic_of((unsigned)f.rev_lo);
+  return rt;
+}
+
 // Distributed shared memory of a thread-block cluster.
 __device__ __forceinline__ uint32_t peer_addr(const void* p, unsigned rank) {
   uint32_t a = (uint32_t)__cvta_generic_to_shared(p), r;
@@ -307,6 +340,7 @@ constexpr int kLoadBatch = 8;     // global loads in flight per thread (split lo
 constexpr uint32_t kBulkChunk = 32768;  // bytes per bulk copy instruction
 constexpr int kUnpackBatch = 8;   // table reads in flight per thread in the unpacking step
 constexpr int kPairBatch = 4;     // the same for the cluster variant (more values per mode)
+constexpr int kPairThreads = 512; // one CTA of a pair per SM (each holds half an asset's grid)
 
 // Classes c and 3 - c (c = 1, 2) of a three-CTA split complete each other's
 // modes: mode k of class c is d_k (alpha_k Z_k + beta_k conj Z_{n-k}) with
@@ -396,34 +430,7 @@ __global__ void __launch_bounds__(NTH, 512 / NTH)
   unsigned mr[kMaxAssetPasses];
 #pragma unroll
   for (int p = 0; p < kMaxAssetPasses; ++p) mr[p] = magic_of((unsigned)f.rad[p]);
-  // digit-reversal tables for the unpacking step (decimation in frequency)
-  RevTab rt{};
-  if (f.dif) {
-    int* tlo = reinterpret_cast<int*>(smem_raw + anchor_offset(f.nl) + (size_t)f.tw_rows * 32);
-    int* thi = tlo + f.rev_lo;
-    const int R0 = f.rad[0], R1 = f.npass >= 2 ? f.rad[1] : 1;
-    for (int x = threadIdx.x; x < f.rev_lo; x += NTH) {
-      const int q1 = fast_div(x, R0, mr[0]);
-      tlo[x] = (x - q1 * R0) * f.stride[0] + (R1 > 1 ? q1 * f.stride[1] : 0);
-    }
-    for (int y = threadIdx.x; y < f.rev_hi; y += NTH) {
-      int pos = 0, r = y;
-#pragma unroll
-      for (int p = 2; p < kMaxAssetPasses; ++p) {
-        if (p < f.npass) {
-          const int R = f.rad[p];
-          const int q = fast_div(r, R, mr[p]);
-          pos += (r - q * R) * f.stride[p];
-          r = q;
-        }
-      }
-      thi[y] = pos;
-    }
-    rt.lo = tlo;
-    rt.hi = thi;
-    rt.B = f.rev_lo;
-    rt.mB = magic_of((unsigned)f.rev_lo);
-  }
+  const RevTab rt = build_rev_tables<NTH>(f, smem_raw, mr);
   pdl_wait();         // the grid comes from the spreading kernel
   if (*gate) return;  // uniform: the whole block leaves
   pdl_trigger();      // the contraction may take the SMs this launch leaves free
@@ -587,13 +594,11 @@ __global__ void __launch_bounds__(NTH, 512 / NTH)
 // joins the halves, each CTA reading its partner's X through distributed
 // shared memory while it unpacks and deconvolves every other mode.
 template <int NTH>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 512 / NTH)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
     k_fft_asset_pair(const float* __restrict__ grid, AssetFft f, const Cplx<float>* __restrict__ W,
                      const Cplx<float>* __restrict__ tw, const Cplx<float>* __restrict__ U,
                      const float* __restrict__ decon, Cplx<float>* __restrict__ out, const int* __restrict__ gate) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // every CTA of the cluster reads the same gate word: both leave or neither
-  if (*gate) return;
   Cplx<float>* s = reinterpret_cast<Cplx<float>*>(smem_raw);
   float4* anc = reinterpret_cast<float4*>(smem_raw + anchor_offset(f.nl));
   unsigned c;
@@ -603,6 +608,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 512 / NTH)
   unsigned mr[kMaxAssetPasses];
 #pragma unroll
   for (int p = 0; p < kMaxAssetPasses; ++p) mr[p] = magic_of((unsigned)f.rad[p]);
+  const RevTab rt = build_rev_tables<NTH>(f, smem_raw, mr);
+  pdl_wait();  // the grid comes from the spreading kernel
+  // every CTA of the cluster reads the same gate word: both leave or neither
+  if (*gate) return;
+  pdl_trigger();
   {
     const float4* src = reinterpret_cast<const float4*>(tw);
     for (int i = threadIdx.x; i < 2 * f.tw_rows; i += NTH) {
@@ -612,12 +622,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 512 / NTH)
   }
   const Cplx<float>* z = reinterpret_cast<const Cplx<float>*>(grid) + (size_t)a * f.n + c;
   for (int m = threadIdx.x; m < L; m += NTH) {
-    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s + digit_rev(m, f, mr));
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s + (f.dif ? m : digit_rev(m, f, mr)));
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(z + 2 * (size_t)m) : "memory");
   }
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
   __syncthreads();
-  run_passes(f, s, anc, NTH);  // decimation in time (f.dif = 0)
+  run_passes(f, s, anc, NTH);
   cluster_sync_all();  // both halves transformed and visible to the partner
   const uint32_t peer = peer_addr(s, c ^ 1u);
   Cplx<float>* oa = out + (size_t)a * (f.N + 1);
@@ -633,8 +643,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 512 / NTH)
         dk[u] = __ldg(decon + k);
         Uk[u] = U[k];
         Wk[u] = W[k];
-        const Cplx<float> lk = s[k], lj = s[j];
-        const Cplx<float> rk = ld_cluster(peer + 8u * (uint32_t)k), rj = ld_cluster(peer + 8u * (uint32_t)j);
+        const int pk = out_pos(k, f, rt), pj = out_pos(j, f, rt);  // the same layout in both CTAs
+        const Cplx<float> lk = s[pk], lj = s[pj];
+        const Cplx<float> rk = ld_cluster(peer + 8u * (uint32_t)pk), rj = ld_cluster(peer + 8u * (uint32_t)pj);
         A0[u] = c == 0 ? lk : rk;  // X_0[k]
         A1[u] = c == 0 ? rk : lk;  // X_1[k]
         B0[u] = c == 0 ? lj : rj;  // X_0[(n-k) mod L]
@@ -711,10 +722,10 @@ cudaError_t launch_fft_asset(const float* grid, const AssetFft& f, int D, const 
   auto set = [&](auto fn) { return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); };
   cudaError_t e;
   if (f.pair) {
-    if ((e = set(k_fft_asset_pair<256>)) != cudaSuccess) return e;
-    k_fft_asset_pair<256><<<grd, 256, smem, s>>>(grid, f, (const Cplx<float>*)W, (const Cplx<float>*)tw,
-                                                 (const Cplx<float>*)U, (const float*)decon, (Cplx<float>*)coeffs,
-                                                 status + 1);
+    if ((e = set(k_fft_asset_pair<kPairThreads>)) != cudaSuccess) return e;
+    return launch_pdl(k_fft_asset_pair<kPairThreads>, grd, dim3(kPairThreads), smem, s, grid, f,
+                      (const Cplx<float>*)W, (const Cplx<float>*)tw, (const Cplx<float>*)U, (const float*)decon,
+                      (Cplx<float>*)coeffs, (const int*)(status + 1));
   } else if (asset_fft_threads(f.split) == 256) {
     if ((e = set(k_fft_asset<256>)) != cudaSuccess) return e;
     return launch_pdl(k_fft_asset<256>, grd, dim3(256), smem, s, grid, f, (const Cplx<float>*)W,
