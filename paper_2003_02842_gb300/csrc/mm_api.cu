@@ -444,8 +444,9 @@ mm_status configure(mm_plan p, int N) {
   s.kernel = p->desc.kernel;
   s.max_events = p->desc.max_events;
   const int tmax = spread_max_tile(p->fp64);
-  // default tile: half the largest in float32 (measured faster on GB300), the largest in float64
-  int tile = p->desc.spread_tile > 0 ? std::min(p->desc.spread_tile, tmax) : (p->fp64 ? tmax : tmax / 2);
+  // default tile: the largest (measured on GB300 with the polynomial scatter:
+  // 4096 cells beat 2048 on both the block and the batched workloads)
+  int tile = p->desc.spread_tile > 0 ? std::min(p->desc.spread_tile, tmax) : tmax;
   if (p->tune_tile > 0) tile = std::min(p->tune_tile, tmax);
   if (Mr <= (int64_t)tile) {
     tile = (int)Mr;
@@ -504,9 +505,11 @@ mm_status configure(mm_plan p, int N) {
   // radices up to 16 by default: the fully unrolled codelets of 25 to 32
   // points stall on instruction fetch, so four small passes beat three large
   // ones; radices up to 32 where the small ones need too many passes or
-  // twiddle rows
+  // twiddle rows. The cluster pair (decimation in time, 512 threads per CTA)
+  // measured the other way round: up to 32 first.
   auto fits_split = [&](int sp_) {
-    for (int maxr : {16, 32}) {
+    const bool pair_first = sp_ == 2 && pair;
+    for (int maxr : {pair_first ? 32 : 16, pair_first ? 16 : 32}) {
       if (p->tune_maxr > 0 && maxr != p->tune_maxr) continue;
       if (plan_asset_fft(n, sp_, N, maxr, &af) && asset_fft_smem(af) + 2048 <= (size_t)p->smem_optin &&
           asset_twiddle_count(af) <= p->atw_cap)
