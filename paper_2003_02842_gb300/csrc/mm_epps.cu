@@ -7,12 +7,17 @@
 // pair k, -k folded into a factor 2 for k >= 1, no factor for k = 0) and
 // Q_k = Re(F(k) F(k)^H) (a Dg x Dg matrix),
 //   Dirichlet  Sigma(N) = (2 pi)^2 / (2N + 1) * P(N),
-//   Fejer      Sigma(N) = (2 pi)^2 / (N + 1) * (P(N) - P1(N) / N),
-//   P(N) = sum_{k<=N} d_k Q_k,  P1(N) = sum_{k<=N} d_k k Q_k,  d_0 = 1, d_k = 2,
-// so one pass over k accumulating the segments (N_{j-1}, N_j] followed by a
-// prefix sum over segments gives every cutoff: the work is that of a single
-// contraction at N_max plus O(#cutoffs Dg^2) additions, not one contraction
-// per cutoff.
+//   Fejer      Sigma(N) = (2 pi)^2 / ((N + 1) N) * sum_{k<=N} d_k (N - k) Q_k,
+//   P(N) = sum_{k<=N} d_k Q_k,  d_0 = 1, d_k = 2.
+// One pass over k accumulates, for each segment s = (e_{s-1}, e_s] of the
+// cutoff list, S_s = sum d_k Q_k and T_s = sum d_k (e_s - k) Q_k; then
+//   sum_{k<=N_j} d_k (N_j - k) Q_k = sum_{s<=j} ((N_j - e_s) S_s + T_s)
+//                                  = A_j + sum_{s<=j} T_s,
+//   A_j = A_{j-1} + (e_j - e_{j-1}) P_{j-1},  P_j = P_{j-1} + S_j,
+// every cutoff from one contraction at N_max plus O(#cutoffs Dg^2) additions.
+// All weights here are non-negative, so a diagonal entry is a sum of
+// non-negative terms: the form P(N) - sum d_k k Q_k / N, which cancels when
+// Q_0 dominates (a small total return at N = 1), is not used.
 //
 // One CTA per problem (grid-stride over problems). The modes are cut into
 // chunks of at most 512 that never cross a cutoff; each warp takes whole
@@ -48,7 +53,7 @@ __global__ void __launch_bounds__(kEppsThreads) k_epps(const float2* __restrict_
   double* ssig = reinterpret_cast<double*>(smem_raw + (((size_t)NS * ncut * NP * 4 + 15) & ~(size_t)15));  // [ncut][NP]
   __shared__ int scut[kMaxCutoffs];
   __shared__ int cstart[kMaxCutoffs + 1];                  // first chunk of each segment
-  __shared__ double swt[kMaxCutoffs], swt1[kMaxCutoffs];  // basis weights per cutoff
+  __shared__ double swt[kMaxCutoffs];                      // basis weight per cutoff
   __shared__ float sinv[kMaxCutoffs * DG];                 // 1 / sqrt(Sigma_aa(N_j))
   if (*gate) return;  // uniform
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -56,8 +61,7 @@ __global__ void __launch_bounds__(kEppsThreads) k_epps(const float2* __restrict_
     const int c = cut_g[i];
     scut[i] = c;
     const double four_pi2 = 4.0 * kPi * kPi;
-    swt[i] = FEJER ? four_pi2 / ((double)c + 1.0) : four_pi2 / (2.0 * (double)c + 1.0);
-    swt1[i] = FEJER ? 1.0 / (double)c : 0.0;
+    swt[i] = FEJER ? four_pi2 / (((double)c + 1.0) * (double)c) : four_pi2 / (2.0 * (double)c + 1.0);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -93,6 +97,7 @@ __global__ void __launch_bounds__(kEppsThreads) k_epps(const float2* __restrict_
       }
       const int kb = (sj ? scut[sj - 1] + 1 : 0) + (ch - cstart[sj]) * kChunkModes;
       const int ke = min(kb + kChunkModes, scut[sj] + 1);
+      const int es = scut[sj];  // the segment's end cutoff: weights e_s - k >= 0
       float acc[NP], acc1[FEJER ? NP : 1];
 #pragma unroll
       for (int p = 0; p < NP; ++p) acc[p] = 0.f;
@@ -106,7 +111,7 @@ __global__ void __launch_bounds__(kEppsThreads) k_epps(const float2* __restrict_
           const float2 v = __ldg(cg + (size_t)i * ld + k);
           c[i] = make_float2(v.x * sc, v.y * sc);
         }
-        const float kf = (float)k;
+        const float kf = (float)(es - k);
         int p = 0;
 #pragma unroll
         for (int i = 0; i < DG; ++i)
@@ -136,11 +141,12 @@ __global__ void __launch_bounds__(kEppsThreads) k_epps(const float2* __restrict_
     // diagonal normalisation: 1/sqrt(Sigma_aa) in float64 once per asset and
     // cutoff, the off-diagonal products in float32
     for (int p = threadIdx.x; p < NP; p += kEppsThreads) {
-      double P = 0.0, P1 = 0.0;
+      double P = 0.0, A = 0.0, Ts = 0.0;
       for (int j = 0; j < ncut; ++j) {
+        if (FEJER && j > 0) A += (double)(scut[j] - scut[j - 1]) * P;
         P += (double)sacc[j * NP + p];
-        if (FEJER) P1 += (double)sacc[(ncut + j) * NP + p];
-        ssig[j * NP + p] = FEJER ? swt[j] * (P - P1 * swt1[j]) : swt[j] * P;
+        if (FEJER) Ts += (double)sacc[(ncut + j) * NP + p];
+        ssig[j * NP + p] = FEJER ? swt[j] * (A + Ts) : swt[j] * P;
       }
     }
     __syncthreads();

@@ -117,6 +117,50 @@ def c2_async(seed=0, T=28800, rates=(1 / 15, 1 / 20)):
     return ev
 
 
+def epps_replications(seed, reps, T=28800, rate=1 / 5, rho=0.35, var=(0.1, 0.2)):
+    """The arrival-time Epps experiment (Sec. 4.1): per replication a
+    bivariate GBM (mu = 0.01, variances `var`, correlation rho) on a 1-s grid
+    of T seconds, each asset observed at its own Poisson arrivals of the same
+    rate on that grid (exponential inter-arrival times moved up to the next
+    second, repeats merged). Returns the replications stacked as one Events
+    (reps problems of 2 assets each)."""
+    ts, ps = [], []
+    cov = bivariate_cov(var[0], var[1], rho)
+    for r in range(reps):
+        rng = rng_for(6, seed, r)
+        lp = gbm_grid(T, 0.01, cov, rng)
+        for j in range(2):
+            idx = poisson_grid_sample(T, rate, rng)
+            ts.append(idx.astype(np.float64))
+            ps.append(lp[idx, j])
+    ev = from_lists(ts, ps)
+    ev.meta = {"workload": f"epps_R{reps}_T{T}", "reps": reps, "T": T, "rate": rate, "rho": rho}
+    return ev
+
+
+def mse_bias_replications(seed, reps, n=100, rho=0.35, var=(0.1, 0.2), mu=0.01):
+    """The accuracy experiment (Sec. 3.2): per replication a bivariate GBM of n
+    synchronous points spanning one day (times 0..n-1, step 1/n day), the
+    first asset observed at every point, the second at every second point
+    (regular non-synchronous trading). Returns the replications stacked as
+    one Events (reps problems of 2 assets each); meta holds the per-step
+    covariance and mean of the log-price increments."""
+    cov = bivariate_cov(var[0], var[1], rho)
+    dt = 1.0 / n
+    ts, ps = [], []
+    t1 = np.arange(n, dtype=np.float64)
+    t2 = np.arange(0, n, 2, dtype=np.float64)
+    for r in range(reps):
+        rng = rng_for(7, seed, r)
+        lp = gbm_grid(n, mu, cov, rng, dt_days=dt)
+        ts += [t1, t2]
+        ps += [lp[:, 0], lp[::2, 1]]
+    ev = from_lists(ts, ps)
+    ev.meta = {"workload": f"mse_bias_R{reps}_n{n}", "reps": reps, "n": n, "step_cov": cov * dt,
+               "step_mean": (mu - 0.5 * np.diag(cov)) * dt}
+    return ev
+
+
 def _continuous_poisson(T, rate, rng):
     n = rng.poisson(rate * T)
     return np.sort(rng.uniform(0.0, T, size=n))

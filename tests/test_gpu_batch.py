@@ -151,3 +151,42 @@ def test_batch_rejects_bad_requests():
     for bad in ([0, 5], [5, 5], [3, 2], [10, 51]):
         with pytest.raises(mm.MMError):
             mm.mm_batch_epps(b, off, t, p, bad)
+
+
+@pytest.mark.parametrize("basis", ["dirichlet", "fejer"])
+def test_sweep_contraction_relative_to_sigma_itself(basis):
+    # the sweep against Eqs. (2) / (3) evaluated in float64 on the sweep's own
+    # coefficients, each entry relative to sqrt(Sigma_ii Sigma_jj) at its own
+    # cutoff (no NUFFT error enters). One replication has a tiny total return
+    # in its first asset, so that at N = 1 its diagonal (a single k = 0 term)
+    # is small against the k = 1 term: a sweep that forms the Fejer weights as
+    # a difference of two prefix sums loses it.
+    import paper_2003_02842_gb300 as mm
+    reps, D = 3, 2
+    evs = _split(synth.concat_events([synth.random_events(40 + r, D=D, n_range=(80, 200), T=3000.0)
+                                      for r in range(reps)]), reps, D)
+    e = evs[1]
+    a0, a1 = int(e.offsets[0]), int(e.offsets[1])
+    lp = e.logp.copy()
+    lp[a1 - 1] = lp[a0] + 1e-7  # total return of asset 0 in replication 1
+    evs[1] = synth.Events(e.offsets, e.t, lp)
+    ev = synth.concat_events(evs)
+    cutoffs = [1, 2, 3, 8, 40]
+    b = mm.mm_batch_create(reps=reps, D=D, N_max=max(cutoffs), max_events=ev.n_events, tol=1e-6, kernel="es",
+                           basis=basis)
+    off, t, p = to_dev(ev)
+    S, _ = mm.mm_batch_epps(b, off, t, p, cutoffs)
+    assert mm.mm_batch_sync(b) == 0
+    F = mm.mm_batch_coeffs(b).cpu().numpy().astype(np.complex128)  # [reps * D, N_max + 1]
+    S = S.cpu().numpy().astype(np.float64)
+    mm.mm_batch_destroy(b)
+    for r in range(reps):
+        c = F[r * D:(r + 1) * D] * 2 * np.pi  # c-convention
+        for j, N in enumerate(cutoffs):
+            k = np.arange(N + 1)
+            w = np.full(N + 1, 1.0 / (2 * N + 1)) if basis == "dirichlet" else (1.0 - k / N) / (N + 1)
+            w = w * np.where(k == 0, 1.0, 2.0)  # the -k half folded in
+            ref = np.real((c[:, None, :N + 1] * np.conj(c[None, :, :N + 1]) * w).sum(axis=2))
+            scale = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
+            assert np.all(np.diag(ref) > 0)
+            assert np.max(np.abs(S[r, j] - ref) / scale) <= 2e-5, (r, N, S[r, j], ref)
