@@ -191,6 +191,28 @@ mm_status mm_cov(mm_plan plan, const void* d_coeffs, int32_t N, void* d_sigma, v
 mm_status mm_corr(mm_plan plan, const void* d_coeffs, int32_t N, void* d_sigma_or_null,
                   void* d_R, void* stream);
 
+/* Covariance with a cutoff per pair of assets (Sec. 3.1: assets with their
+ * own cutoffs, e.g. their own Nyquist cutoffs in the arrival-time
+ * representation, give D(D-1)/2 pairwise estimates): Sigma_ij is Eq. (2)
+ * (Dirichlet) or Eq. (3) (Fejer), the plan's basis, at
+ * N_ij = min(h_N[i], h_N[j]), from d_coeffs as mm_coeffs writes them at
+ * N_coeffs ([D][N_coeffs + 1], the plan's precision); R_ij = Sigma_ij /
+ * sqrt(Sigma_ii Sigma_jj), R_ii = 1. Such a matrix need not be positive
+ * semi-definite; psd_repair = 1 replaces Sigma (before R is formed) by the
+ * positive semi-definite matrix closest to it in the Frobenius norm,
+ * V max(Lambda, 0) V^T from its eigendecomposition (float64 Jacobi
+ * iteration, D <= 256, else MM_ERR_UNSUPPORTED), leaving it unchanged when
+ * no eigenvalue is negative; *d_clipped_or_null (device int) receives the
+ * number of negative eigenvalues clipped (0 without repair).
+ * h_N: host array of D cutoffs, each in [0, N_coeffs] ([1, N_coeffs] for
+ * Fejer), else MM_ERR_CUTOFF; read before the call returns. Outputs D x D
+ * row-major float32 (mixed plans) or float64 (FP64 plans), caller owned; a
+ * non-positive variance gives NaN entries and MM_ERR_ZERO_VARIANCE at the
+ * next mm_plan_sync. Asynchronous on stream; not available on batch plans. */
+mm_status mm_corr_pairwise(mm_plan plan, const void* d_coeffs, int32_t N_coeffs, const int32_t* h_N,
+                           int32_t psd_repair, void* d_sigma_or_null, void* d_R, int32_t* d_clipped_or_null,
+                           void* stream);
+
 /* mm_corr without a plan and without allocating anything, for callers that
  * cannot call cudaMalloc (their device memory is owned by a pool or an
  * allocator they must not bypass, or an allocation may not fail at that

@@ -273,6 +273,39 @@ def estimate(offsets, t, logp, N=None, basis="dirichlet", window=None, ks=None):
             "imag_worst": worst, "roff": roff, "rt": rt, "rd": rd}
 
 
+def cov_pairwise_cutoffs(offsets, t, logp, Ns, basis="dirichlet", window=None):
+    """Sec. 3.1, per-asset cutoffs: Sigma_ij by Eq. (2) or (3) at
+    N_ij = min(Ns[i], Ns[j]), every asset rescaled with the problem's common
+    window (data min/max unless given). Each distinct pairwise cutoff is one
+    evaluation of Algorithm 3 at that N; its entries (i, j) with N_ij = N are
+    kept. Returns (Sigma, R)."""
+    off = _i64a(offsets)
+    D = len(off) - 1
+    Ns = np.asarray(Ns, dtype=np.int64)
+    t0, t1 = window if window is not None else bounds(off, t)
+    Nij = np.minimum(Ns[:, None], Ns[None, :])
+    S = np.zeros((D, D))
+    for N in np.unique(Nij):
+        est = estimate(off, t, logp, N=int(N), basis=basis, window=(t0, t1))
+        sel = Nij == N
+        S[sel] = est["Sigma"][sel]
+    return S, corr(S)
+
+
+def nearest_psd(S):
+    """The positive semi-definite matrix nearest to the symmetric S in the
+    Frobenius norm (the eigenvalue method the paper cites for repairing a
+    pairwise estimate, Sec. 3.1): V max(Lambda, 0) V^T from S = V Lambda V^T
+    (numpy's symmetric eigendecomposition). Returns (matrix, number of
+    negative eigenvalues); S itself when none is negative."""
+    S = 0.5 * (np.asarray(S, dtype=np.float64) + np.asarray(S, dtype=np.float64).T)
+    lam, V = np.linalg.eigh(S)
+    neg = int(np.sum(lam < 0.0))
+    if neg == 0:
+        return S, 0
+    return (V * np.maximum(lam, 0.0)) @ V.T, neg
+
+
 def coeffs_F(offsets, t, logp, N, window=None, assets=None, ks=None):
     """F(dp_i)(k) = c_k / (2 pi) (Eq. (4)) for k = 0..N (or the modes ks) of the
     selected assets; rescale bounds from the data unless a window is given."""

@@ -22,6 +22,7 @@ from ._lib import BASES, KERNELS, PRECISIONS, STAGES, STATUS_NAMES
 __all__ = [
     "MMError", "Plan", "mm_plan_create", "mm_destroy", "mm_coeffs", "mm_cov", "mm_corr", "mm_estimate",
     "mm_estimate_host", "mm_nyquist", "mm_plan_sync", "mm_plan_get_info", "mm_profile_enable", "mm_plan_set_graphs",
+    "mm_corr_pairwise",
     "mm_profile_read", "mm_status_string", "mm_version", "mm_corr_noalloc", "mm_autotune", "KERNELS", "BASES", "PRECISIONS", "STAGES",
     "Batch", "mm_batch_create", "mm_batch_destroy", "mm_batch_epps", "mm_batch_autotune", "mm_batch_coeffs",
     "mm_batch_sync", "mm_batch_get_info", "mm_batch_profile_enable", "mm_batch_profile_read",
@@ -193,6 +194,34 @@ def mm_corr(plan, coeffs, N, sigma=True, R=None, stream=None):
     _check(_lib.load().mm_corr(plan.handle, _dptr(coeffs, _coef_dtype(plan), "coeffs"), int(N), ps,
                                _dptr(R, dt, "R"), _stream(stream)), "mm_corr")
     return S, R
+
+
+def mm_corr_pairwise(plan, coeffs, N_coeffs, N_per_asset, psd_repair=False, sigma=True, R=None, stream=None):
+    """Sigma and R with a cutoff per pair of assets, N_ij = min(N_i, N_j)
+    (Sec. 3.1), from coefficients computed at N_coeffs; psd_repair replaces
+    Sigma by the nearest positive semi-definite matrix (Frobenius norm)
+    before R is formed. Returns (Sigma or None, R, clipped), clipped a device
+    int32 tensor holding the number of negative eigenvalues removed."""
+    torch = _torch()
+    D = plan.desc["D"]
+    dt = _real_dtype(plan)
+    if R is None:
+        R = torch.empty((D, D), dtype=dt, device=coeffs.device)
+    S = None
+    if sigma is True:
+        S = torch.empty((D, D), dtype=dt, device=coeffs.device)
+    elif sigma is not None and sigma is not False:
+        S = sigma
+    Ns = [int(x) for x in N_per_asset]
+    if len(Ns) != D:
+        raise ValueError(f"mm_corr_pairwise: {len(Ns)} cutoffs for {D} assets")
+    hN = (ctypes.c_int32 * D)(*Ns)
+    clipped = torch.zeros(1, dtype=torch.int32, device=coeffs.device)
+    ps = _dptr(S, dt, "sigma") if S is not None else ctypes.c_void_p(0)
+    _check(_lib.load().mm_corr_pairwise(plan.handle, _dptr(coeffs, _coef_dtype(plan), "coeffs"), int(N_coeffs), hN,
+                                        1 if psd_repair else 0, ps, _dptr(R, dt, "R"),
+                                        ctypes.c_void_p(clipped.data_ptr()), _stream(stream)), "mm_corr_pairwise")
+    return S, R, clipped
 
 
 def mm_corr_noalloc(coeffs, N, basis="dirichlet", prec="bf16x3", sigma=True, R=None, stream=None):

@@ -177,6 +177,7 @@ def load():
         "mm_corr": ([p, p, i32, p, p, p], st),
         "mm_estimate": ([p, p, p, p, i32, d, d, p, p, p, ctypes.POINTER(i32), p], st),
         "mm_corr_noalloc": ([i32, i32, st, st, p, p, p, p], st),
+        "mm_corr_pairwise": ([p, p, i32, p, i32, p, p, p, p], st),
         "mm_estimate_host": ([p, p, p, p, i32, d, d, p, p, p, ctypes.POINTER(i32), p], st),
         "mm_nyquist": ([p, p, p, d, d, ctypes.POINTER(i32), p], st),
         "mm_autotune": ([p, p, p, p, i32, d, d, p, i32, p], st),

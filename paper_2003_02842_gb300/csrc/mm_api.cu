@@ -262,6 +262,11 @@ struct mm_plan_s {
   float* acc[2] = {nullptr, nullptr};  // mixed path: FP32 accumulators, used alternately
   int* gram_done = nullptr;       // contraction CTAs finished (the last one runs the epilogue)
   int* fft_sync = nullptr;        // per asset: arrival counter and flag of the three-CTA FFT split
+  int* pw_N = nullptr;            // pairwise-cutoff covariance: per-asset cutoffs,
+  double* pw_sig = nullptr;       // the float64 estimate,
+  double* pw_A = nullptr;         // the repair's working matrix and eigenvectors
+  double* pw_V = nullptr;         // (allocated on first use)
+  int* pw_clip = nullptr;
   int acc_sel = 0;
   bool acc_dirty = true;          // clear both before the next contraction
   int acc_D = -1;                 // D whose D x Dp region the last epilogue cleared
@@ -340,7 +345,8 @@ mm_status dalloc(mm_plan p, void** ptr, size_t bytes) {
 
 void free_all(mm_plan p) {
   void* ptrs[] = {p->grid, p->rec_b0, p->rec_d, p->rec_v, p->W, p->atw, p->U, p->decon, p->glx, p->glw, p->bounds, p->gscale, p->status, p->gapbits, p->wsq,
-                  p->partial, p->acc[0], p->acc[1], p->gram_done, p->fft_sync, p->s_off, p->s_t, p->s_p, p->s_coef,
+                  p->partial, p->acc[0], p->acc[1], p->gram_done, p->fft_sync, p->pw_N, p->pw_sig, p->pw_A,
+                  p->pw_V, p->pw_clip, p->s_off, p->s_t, p->s_p, p->s_coef,
                   p->s_sigma, p->s_R};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -1014,6 +1020,44 @@ mm_status mm_coeffs(mm_plan p, const int64_t* d_offsets, const double* d_t, cons
   if (!d_offsets || !d_t || !d_logp || !d_coeffs) return MM_ERR_INVALID_ARG;
   if (!(isfinite(t0) && isfinite(t1))) return MM_ERR_INVALID_ARG;
   return coeffs_impl(p, d_offsets, d_t, d_logp, N, t0, t1, d_coeffs, N_used, (cudaStream_t)stream);
+}
+
+mm_status mm_corr_pairwise(mm_plan p, const void* d_coeffs, int32_t N_coeffs, const int32_t* h_N,
+                           int32_t psd_repair, void* d_sigma_or_null, void* d_R, int32_t* d_clipped_or_null,
+                           void* stream) {
+  mm_status r = check_plan(p);
+  if (r != MM_OK) return r;
+  if (p->batch) return MM_ERR_UNSUPPORTED;
+  if (!d_coeffs || !h_N || !d_R || (psd_repair != 0 && psd_repair != 1)) return MM_ERR_INVALID_ARG;
+  if (N_coeffs < 0 || N_coeffs > p->desc.N_max) return MM_ERR_CUTOFF;
+  const int D = p->D;
+  if (psd_repair && D > pairwise_psd_max_assets()) return MM_ERR_UNSUPPORTED;
+  const int lo = p->desc.basis == MM_BASIS_FEJER ? 1 : 0;
+  for (int i = 0; i < D; ++i)
+    if (h_N[i] < lo || h_N[i] > N_coeffs) return MM_ERR_CUTOFF;
+  if (!p->pw_N) {
+    const size_t dd = (size_t)p->desc.D * p->desc.D * sizeof(double);
+    mm_status a = dalloc(p, (void**)&p->pw_N, (size_t)p->desc.D * sizeof(int));
+    if (a == MM_OK) a = dalloc(p, (void**)&p->pw_sig, dd);
+    if (a == MM_OK && p->desc.D <= pairwise_psd_max_assets()) a = dalloc(p, (void**)&p->pw_A, dd);
+    if (a == MM_OK && p->desc.D <= pairwise_psd_max_assets()) a = dalloc(p, (void**)&p->pw_V, dd);
+    if (a == MM_OK) a = dalloc(p, (void**)&p->pw_clip, sizeof(int));
+    if (a != MM_OK) return a;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  p->last = st;
+  MM_CUDA(cudaMemcpyAsync(p->pw_N, h_N, (size_t)D * sizeof(int), cudaMemcpyHostToDevice, st));
+  {
+    StageScope sc(p, MM_STAGE_GRAM, st);
+    MM_CUDA(launch_pairwise(p->fp64, p->desc.basis == MM_BASIS_FEJER, d_coeffs, N_coeffs + 1, p->pw_N, D,
+                            p->pw_sig, st));
+  }
+  StageScope sc(p, MM_STAGE_REDUCE, st, psd_repair ? 2 : 1);
+  int* clip = d_clipped_or_null ? (int*)d_clipped_or_null : p->pw_clip;
+  if (psd_repair) MM_CUDA(launch_psd_repair(p->pw_sig, p->pw_A, p->pw_V, D, clip, st));
+  else MM_CUDA(cudaMemsetAsync(clip, 0, sizeof(int), st));
+  MM_CUDA(launch_pairwise_out(p->fp64, p->pw_sig, D, d_sigma_or_null, d_R, p->status, st));
+  return MM_OK;
 }
 
 mm_status mm_cov(mm_plan p, const void* d_coeffs, int32_t N, void* d_sigma, void* stream) {

@@ -232,6 +232,15 @@ mm_status plan_flags_to_status(int flags);
 cudaError_t launch_epps(int Dg, bool fejer, const void* coef, int ld, const int* cut, int ncut, int G, float* sigma,
                         float* R, int* status, int grid, cudaStream_t s);
 
+// Pairwise-cutoff covariance (float64 D x D into sig) and its repair to the
+// nearest positive semi-definite matrix (one CTA, D <= pairwise_psd_max_assets()).
+int pairwise_psd_max_assets();
+cudaError_t launch_pairwise(bool fp64, bool fejer, const void* coeffs, int ld, const int* Nv, int D,
+                            double* sig, cudaStream_t s);
+cudaError_t launch_psd_repair(double* sig, double* A, double* V, int D, int* clipped, cudaStream_t s);
+cudaError_t launch_pairwise_out(bool fp64, const double* sig, int D, void* sigma, void* R, int* status,
+                                cudaStream_t s);
+
 // ------------------------------------------------- programmatic launches
 // The hot path's kernels are launched with programmatic stream
 // serialization: a kernel may be scheduled before its predecessor in the

@@ -1,0 +1,279 @@
+// mm_pairwise.cu -- covariance with a cutoff per pair of assets and the
+// repair to the nearest positive semi-definite matrix (Sec. 3.1: when each
+// asset has its own cutoff, e.g. its own Nyquist cutoff in the arrival-time
+// representation, each entry is a pairwise estimate, and neither basis then
+// guarantees a positive semi-definite matrix).
+//
+// Sigma_ij is Eq. (2) (Dirichlet) or Eq. (3) (Fejer) at N_ij = min(N_i, N_j)
+// from coefficients computed once at max_i N_i:
+//   Dirichlet  (2 pi)^2 / (2N + 1)      * sum_{k<=N} d_k Re(F_i(k) conj F_j(k)),
+//   Fejer      (2 pi)^2 / ((N + 1) N)   * sum_{k<=N} d_k (N - k) Re(F_i(k) conj F_j(k)),
+// d_0 = 1, d_k = 2 (the -k half folded in); every weight is non-negative.
+// One CTA per 16 x 16 tile of pairs (upper tiles), the two tiles' coefficient
+// rows staged in shared memory 128 modes at a time; a thread owns one pair,
+// sums a chunk in the coefficients' precision and adds it to a float64 sum.
+//
+// Repair: the matrix closest to Sigma in the Frobenius norm among the positive
+// semi-definite ones is V max(Lambda, 0) V^T (Sigma = V Lambda V^T), the
+// eigenvalue method the paper points to. The eigendecomposition is a cyclic
+// Jacobi iteration in float64 in one CTA: each step applies D/2 disjoint
+// rotations in parallel (round-robin pairing), a sweep is D - 1 steps, and
+// the sweeps stop when the off-diagonal norm is below 1e-14 of the matrix
+// norm or after kJacobiSweeps.
+#include <math.h>
+
+#include "mm_common.cuh"
+
+namespace mmgpu {
+
+namespace {
+
+constexpr int kPT = 16;        // tile edge (pairs per tile: 16 x 16)
+constexpr int kPChunk = 128;   // modes staged per chunk
+constexpr int kJacobiThreads = 1024;
+constexpr int kJacobiSweeps = 40;
+constexpr int kPsdMaxD = 256;  // largest matrix the one-CTA repair takes
+
+__device__ __forceinline__ void tile_of(int p, int nt, int& I, int& J) {
+  int i = 0;
+  while (p >= nt - i) {
+    p -= nt - i;
+    ++i;
+  }
+  I = i;
+  J = i + p;
+}
+
+template <typename T2>
+__device__ __forceinline__ T2 zero2() {
+  T2 z;
+  z.x = 0;
+  z.y = 0;
+  return z;
+}
+
+template <typename T2, typename T, bool FEJER>
+__global__ void __launch_bounds__(256) k_pairwise(const T2* __restrict__ F, int ld, const int* __restrict__ Nv,
+                                                  int D, int nt, double* __restrict__ sig) {
+  __shared__ T2 a[kPT][kPChunk + 1], b[kPT][kPChunk + 1];
+  __shared__ int s_nmax;
+  int I, J;
+  tile_of(blockIdx.x, nt, I, J);
+  const int ti = threadIdx.x / kPT, tj = threadIdx.x % kPT;
+  const int i = I * kPT + ti, j = J * kPT + tj;
+  const bool valid = i < D && j < D && (I < J || ti <= tj);
+  const int Nij = valid ? min(Nv[i], Nv[j]) : -1;
+  if (threadIdx.x == 0) s_nmax = -1;
+  __syncthreads();
+  if (valid) atomicMax(&s_nmax, Nij);
+  __syncthreads();
+  const int nmax = s_nmax;  // the tile's largest pairwise cutoff
+  double acc = 0.0;
+  for (int k0 = 0; k0 <= nmax; k0 += kPChunk) {
+    for (int e = threadIdx.x; e < kPT * kPChunk; e += blockDim.x) {
+      const int r = e / kPChunk, c = e - r * kPChunk;
+      const int k = k0 + c;
+      const int ra = I * kPT + r, rb = J * kPT + r;
+      a[r][c] = (k <= nmax && ra < D) ? F[(size_t)ra * ld + k] : zero2<T2>();
+      b[r][c] = (k <= nmax && rb < D) ? F[(size_t)rb * ld + k] : zero2<T2>();
+    }
+    __syncthreads();
+    T part = 0;
+    const int cend = min(kPChunk - 1, Nij - k0);  // last mode of this pair in the chunk
+    for (int c = 0; c <= cend; ++c) {
+      const int k = k0 + c;
+      T w = k == 0 ? (T)1 : (T)2;
+      if (FEJER) w *= (T)(Nij - k);
+      part += w * (a[ti][c].x * b[tj][c].x + a[ti][c].y * b[tj][c].y);
+    }
+    acc += (double)part;
+    __syncthreads();
+  }
+  if (valid) {
+    const double fp2 = 4.0 * kPi * kPi;
+    const double v = acc * (FEJER ? fp2 / (((double)Nij + 1.0) * (double)Nij) : fp2 / (2.0 * Nij + 1.0));
+    sig[(size_t)i * D + j] = v;
+    sig[(size_t)j * D + i] = v;
+  }
+}
+
+// The Jacobi iteration (Golub and Van Loan, the cyclic Jacobi algorithm with
+// a parallel ordering): rotation (p, q) with tau = (a_qq - a_pp) / (2 a_pq),
+// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c
+// zeroes a_pq in J^T A J, J = [[c, s], [-s, c]] on rows and columns p, q;
+// V accumulates V J. A is a float64 copy of Sigma (global scratch), V the
+// eigenvectors; sig is replaced by V max(Lambda, 0) V^T only when an
+// eigenvalue is negative.
+__global__ void __launch_bounds__(kJacobiThreads) k_psd_repair(double* __restrict__ sig, double* __restrict__ A,
+                                                               double* __restrict__ V, int D, int* clipped) {
+  __shared__ int sp[kPsdMaxD / 2], sq[kPsdMaxD / 2];
+  __shared__ double sc[kPsdMaxD / 2], ss[kPsdMaxD / 2];
+  __shared__ double s_lam[kPsdMaxD];
+  __shared__ double s_red[kJacobiThreads / 32];
+  __shared__ int s_neg;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int m = (D + 1) & ~1;  // players of the round-robin (one idle when D is odd)
+  const int nh = m / 2;
+  for (int e = tid; e < D * D; e += nth) {
+    A[e] = sig[e];
+    const int r = e / D;
+    V[e] = (r == e - r * D) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  auto block_sum = [&](double v) -> double {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) s_red[tid >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < (nth >> 5); ++w) t += s_red[w];
+    __syncthreads();
+    return t;
+  };
+  double nrm = 0.0;
+  for (int e = tid; e < D * D; e += nth) nrm += A[e] * A[e];
+  const double norm2 = block_sum(nrm);
+  for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
+    double off = 0.0;
+    for (int e = tid; e < D * D; e += nth) {
+      const int r = e / D;
+      if (r != e - r * D) off += A[e] * A[e];
+    }
+    if (!(block_sum(off) > 1e-28 * norm2)) break;  // uniform
+    for (int step = 0; step < m - 1; ++step) {
+      // round-robin: player m-1 meets player `step`; the others pair up
+      // symmetrically around it
+      if (tid < nh) {
+        int p, q;
+        if (tid == 0) {
+          p = step;
+          q = m - 1;
+        } else {
+          p = (step + tid) % (m - 1);
+          q = (step - tid + (m - 1)) % (m - 1);
+        }
+        if (p > q) {
+          const int x = p;
+          p = q;
+          q = x;
+        }
+        double c = 1.0, sn = 0.0;
+        if (q < D) {
+          const double apq = A[(size_t)p * D + q];
+          if (apq != 0.0) {
+            const double tau = (A[(size_t)q * D + q] - A[(size_t)p * D + p]) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = t * c;
+          }
+        }
+        sp[tid] = p;
+        sq[tid] = q;
+        sc[tid] = c;
+        ss[tid] = sn;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int e = tid; e < nh * D; e += nth) {
+        const int r = e / D, x = e - r * D;
+        const int p = sp[r], q = sq[r];
+        if (q >= D) continue;
+        const double c = sc[r], sn = ss[r];
+        const double ap = A[(size_t)p * D + x], aq = A[(size_t)q * D + x];
+        A[(size_t)p * D + x] = c * ap - sn * aq;
+        A[(size_t)q * D + x] = sn * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int e = tid; e < nh * D; e += nth) {
+        const int r = e / D, x = e - r * D;
+        const int p = sp[r], q = sq[r];
+        if (q >= D) continue;
+        const double c = sc[r], sn = ss[r];
+        const double ap = A[(size_t)x * D + p], aq = A[(size_t)x * D + q];
+        A[(size_t)x * D + p] = c * ap - sn * aq;
+        A[(size_t)x * D + q] = sn * ap + c * aq;
+        const double vp = V[(size_t)x * D + p], vq = V[(size_t)x * D + q];
+        V[(size_t)x * D + p] = c * vp - sn * vq;
+        V[(size_t)x * D + q] = sn * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) s_neg = 0;
+  __syncthreads();
+  for (int i = tid; i < D; i += nth) {
+    const double l = A[(size_t)i * D + i];
+    s_lam[i] = l > 0.0 ? l : 0.0;
+    if (l < 0.0) atomicAdd(&s_neg, 1);
+  }
+  __syncthreads();
+  if (tid == 0 && clipped) *clipped = s_neg;
+  if (s_neg == 0) return;  // already positive semi-definite: Sigma unchanged
+  for (int e = tid; e < D * D; e += nth) {
+    const int i = e / D, j = e - i * D;
+    if (j < i) continue;
+    double v = 0.0;
+    for (int k = 0; k < D; ++k) v += V[(size_t)i * D + k] * s_lam[k] * V[(size_t)j * D + k];
+    sig[(size_t)i * D + j] = v;
+    sig[(size_t)j * D + i] = v;
+  }
+}
+
+// Sigma and R in the output precision: R_ij = Sigma_ij / sqrt(Sigma_ii Sigma_jj)
+// (float64), R_ii = 1; a non-positive variance gives NaN and ST_ZERO_VAR.
+template <typename T>
+__global__ void k_pairwise_out(const double* __restrict__ sig, int D, T* __restrict__ sigma, T* __restrict__ R,
+                               int* status) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= D * D) return;
+  const int i = e / D, j = e - i * D;
+  const double v = sig[e], a = sig[(size_t)i * D + i], b = sig[(size_t)j * D + j];
+  if (sigma) sigma[e] = (T)v;
+  double r;
+  if (a > 0.0 && b > 0.0) {
+    r = (i == j) ? 1.0 : v / (sqrt(a) * sqrt(b));
+  } else {
+    r = __longlong_as_double(0x7ff8000000000000ll);
+    if (i == j) atomicOr(status, ST_ZERO_VAR);
+  }
+  R[e] = (T)r;
+}
+
+}  // namespace
+
+}  // namespace mmgpu
+
+namespace mmgpu {
+
+int pairwise_psd_max_assets() { return kPsdMaxD; }
+
+cudaError_t launch_pairwise(bool fp64, bool fejer, const void* coeffs, int ld, const int* Nv, int D,
+                            double* sig, cudaStream_t s) {
+  const int nt = (D + kPT - 1) / kPT;
+  const int grid = nt * (nt + 1) / 2;
+  if (fp64) {
+    if (fejer) k_pairwise<double2, double, true><<<grid, 256, 0, s>>>((const double2*)coeffs, ld, Nv, D, nt, sig);
+    else k_pairwise<double2, double, false><<<grid, 256, 0, s>>>((const double2*)coeffs, ld, Nv, D, nt, sig);
+  } else {
+    if (fejer) k_pairwise<float2, float, true><<<grid, 256, 0, s>>>((const float2*)coeffs, ld, Nv, D, nt, sig);
+    else k_pairwise<float2, float, false><<<grid, 256, 0, s>>>((const float2*)coeffs, ld, Nv, D, nt, sig);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_psd_repair(double* sig, double* A, double* V, int D, int* clipped, cudaStream_t s) {
+  if (D > kPsdMaxD) return cudaErrorInvalidValue;
+  k_psd_repair<<<1, kJacobiThreads, 0, s>>>(sig, A, V, D, clipped);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pairwise_out(bool fp64, const double* sig, int D, void* sigma, void* R, int* status,
+                                cudaStream_t s) {
+  const int n = D * D, grid = (n + 255) / 256;
+  if (fp64) k_pairwise_out<double><<<grid, 256, 0, s>>>(sig, D, (double*)sigma, (double*)R, status);
+  else k_pairwise_out<float><<<grid, 256, 0, s>>>(sig, D, (float*)sigma, (float*)R, status);
+  return cudaGetLastError();
+}
+
+}  // namespace mmgpu
