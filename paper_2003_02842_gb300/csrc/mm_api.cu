@@ -1054,7 +1054,7 @@ mm_status mm_corr_pairwise(mm_plan p, const void* d_coeffs, int32_t N_coeffs, co
   }
   StageScope sc(p, MM_STAGE_REDUCE, st, psd_repair ? 2 : 1);
   int* clip = d_clipped_or_null ? (int*)d_clipped_or_null : p->pw_clip;
-  if (psd_repair) MM_CUDA(launch_psd_repair(p->pw_sig, p->pw_A, p->pw_V, D, clip, st));
+  if (psd_repair) MM_CUDA(launch_psd_repair(p->fp64, p->pw_sig, p->pw_A, p->pw_V, D, clip, st));
   else MM_CUDA(cudaMemsetAsync(clip, 0, sizeof(int), st));
   MM_CUDA(launch_pairwise_out(p->fp64, p->pw_sig, D, d_sigma_or_null, d_R, p->status, st));
   return MM_OK;

@@ -237,7 +237,7 @@ cudaError_t launch_epps(int Dg, bool fejer, const void* coef, int ld, const int*
 int pairwise_psd_max_assets();
 cudaError_t launch_pairwise(bool fp64, bool fejer, const void* coeffs, int ld, const int* Nv, int D,
                             double* sig, cudaStream_t s);
-cudaError_t launch_psd_repair(double* sig, double* A, double* V, int D, int* clipped, cudaStream_t s);
+cudaError_t launch_psd_repair(bool fp64, double* sig, double* A, double* V, int D, int* clipped, cudaStream_t s);
 cudaError_t launch_pairwise_out(bool fp64, const double* sig, int D, void* sigma, void* R, int* status,
                                 cudaStream_t s);
 

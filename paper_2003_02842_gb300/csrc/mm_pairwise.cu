@@ -16,10 +16,13 @@
 // Repair: the matrix closest to Sigma in the Frobenius norm among the positive
 // semi-definite ones is V max(Lambda, 0) V^T (Sigma = V Lambda V^T), the
 // eigenvalue method the paper points to. The eigendecomposition is a cyclic
-// Jacobi iteration in float64 in one CTA: each step applies D/2 disjoint
+// Jacobi iteration in one CTA: each step applies D/2 disjoint
 // rotations in parallel (round-robin pairing), a sweep is D - 1 steps, and
-// the sweeps stop when the off-diagonal norm is below 1e-14 of the matrix
-// norm or after kJacobiSweeps.
+// the sweeps stop when the off-diagonal norm is below 2 D eps of the matrix
+// norm (eps of the working type: float64 for FP64 plans, float32 for the
+// mixed precisions' float32 Sigma) or after kJacobiSweeps. GB300 issues
+// float64 at a small fraction of the float32 rate, so the mixed path works
+// in float32.
 #include <math.h>
 
 #include "mm_common.cuh"
@@ -33,6 +36,7 @@ constexpr int kPChunk = 128;   // modes staged per chunk
 constexpr int kJacobiThreads = 1024;
 constexpr int kJacobiSweeps = 40;
 constexpr int kPsdMaxD = 256;  // largest matrix the one-CTA repair takes
+constexpr size_t kPsdSmemBytes = 200 * 1024;  // the working matrix and eigenvectors in shared memory up to this
 
 __device__ __forceinline__ void tile_of(int p, int nt, int& I, int& J) {
   int i = 0;
@@ -101,13 +105,20 @@ __global__ void __launch_bounds__(256) k_pairwise(const T2* __restrict__ F, int 
 // a parallel ordering): rotation (p, q) with tau = (a_qq - a_pp) / (2 a_pq),
 // t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c
 // zeroes a_pq in J^T A J, J = [[c, s], [-s, c]] on rows and columns p, q;
-// V accumulates V J. A is a float64 copy of Sigma (global scratch), V the
-// eigenvectors; sig is replaced by V max(Lambda, 0) V^T only when an
-// eigenvalue is negative.
-__global__ void __launch_bounds__(kJacobiThreads) k_psd_repair(double* __restrict__ sig, double* __restrict__ A,
-                                                               double* __restrict__ V, int D, int* clipped) {
+// V accumulates V J. A is a float64 copy of Sigma, V the eigenvectors (both
+// in shared memory up to D = 112, else in global scratch); sig is replaced by
+// V max(Lambda, 0) V^T only when an eigenvalue is negative.
+template <typename W>
+__global__ void __launch_bounds__(kJacobiThreads) k_psd_repair(double* __restrict__ sig, W* Ag, W* Vg, int D,
+                                                               int* clipped) {
+  // the working matrix and the eigenvectors in shared memory when both fit,
+  // else in the global scratch
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const bool in_smem = (size_t)2 * D * D * sizeof(W) <= kPsdSmemBytes;
+  W* A = in_smem ? reinterpret_cast<W*>(smem_raw) : Ag;
+  W* V = in_smem ? reinterpret_cast<W*>(smem_raw) + (size_t)D * D : Vg;
   __shared__ int sp[kPsdMaxD / 2], sq[kPsdMaxD / 2];
-  __shared__ double sc[kPsdMaxD / 2], ss[kPsdMaxD / 2];
+  __shared__ W sc[kPsdMaxD / 2], ss[kPsdMaxD / 2];
   __shared__ double s_lam[kPsdMaxD];
   __shared__ double s_red[kJacobiThreads / 32];
   __shared__ int s_neg;
@@ -115,9 +126,9 @@ __global__ void __launch_bounds__(kJacobiThreads) k_psd_repair(double* __restric
   const int m = (D + 1) & ~1;  // players of the round-robin (one idle when D is odd)
   const int nh = m / 2;
   for (int e = tid; e < D * D; e += nth) {
-    A[e] = sig[e];
+    A[e] = (W)sig[e];
     const int r = e / D;
-    V[e] = (r == e - r * D) ? 1.0 : 0.0;
+    V[e] = (r == e - r * D) ? (W)1 : (W)0;
   }
   __syncthreads();
   auto block_sum = [&](double v) -> double {
@@ -131,15 +142,19 @@ __global__ void __launch_bounds__(kJacobiThreads) k_psd_repair(double* __restric
     return t;
   };
   double nrm = 0.0;
-  for (int e = tid; e < D * D; e += nth) nrm += A[e] * A[e];
+  for (int e = tid; e < D * D; e += nth) nrm += (double)A[e] * (double)A[e];
   const double norm2 = block_sum(nrm);
+  // converged when the off-diagonal norm reaches the level rounding leaves in
+  // a D x D rotation sequence, 2 D eps of the norm (eps of the working type)
+  const double eps = sizeof(W) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-8;
+  const double rel2 = (2.0 * D * eps) * (2.0 * D * eps);
   for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
     double off = 0.0;
     for (int e = tid; e < D * D; e += nth) {
       const int r = e / D;
-      if (r != e - r * D) off += A[e] * A[e];
+      if (r != e - r * D) off += (double)A[e] * (double)A[e];
     }
-    if (!(block_sum(off) > 1e-28 * norm2)) break;  // uniform
+    if (!(block_sum(off) > rel2 * norm2)) break;  // uniform
     for (int step = 0; step < m - 1; ++step) {
       // round-robin: player m-1 meets player `step`; the others pair up
       // symmetrically around it
@@ -157,13 +172,13 @@ __global__ void __launch_bounds__(kJacobiThreads) k_psd_repair(double* __restric
           p = q;
           q = x;
         }
-        double c = 1.0, sn = 0.0;
+        W c = 1, sn = 0;
         if (q < D) {
-          const double apq = A[(size_t)p * D + q];
-          if (apq != 0.0) {
-            const double tau = (A[(size_t)q * D + q] - A[(size_t)p * D + p]) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
+          const W apq = A[(size_t)p * D + q];
+          if (apq != (W)0) {
+            const W tau = (A[(size_t)q * D + q] - A[(size_t)p * D + p]) / ((W)2 * apq);
+            const W t = (tau >= (W)0 ? (W)1 : (W)-1) / (fabs(tau) + sqrt((W)1 + tau * tau));
+            c = (W)1 / sqrt((W)1 + t * t);
             sn = t * c;
           }
         }
@@ -178,8 +193,8 @@ __global__ void __launch_bounds__(kJacobiThreads) k_psd_repair(double* __restric
         const int r = e / D, x = e - r * D;
         const int p = sp[r], q = sq[r];
         if (q >= D) continue;
-        const double c = sc[r], sn = ss[r];
-        const double ap = A[(size_t)p * D + x], aq = A[(size_t)q * D + x];
+        const W c = sc[r], sn = ss[r];
+        const W ap = A[(size_t)p * D + x], aq = A[(size_t)q * D + x];
         A[(size_t)p * D + x] = c * ap - sn * aq;
         A[(size_t)q * D + x] = sn * ap + c * aq;
       }
@@ -189,11 +204,11 @@ __global__ void __launch_bounds__(kJacobiThreads) k_psd_repair(double* __restric
         const int r = e / D, x = e - r * D;
         const int p = sp[r], q = sq[r];
         if (q >= D) continue;
-        const double c = sc[r], sn = ss[r];
-        const double ap = A[(size_t)x * D + p], aq = A[(size_t)x * D + q];
+        const W c = sc[r], sn = ss[r];
+        const W ap = A[(size_t)x * D + p], aq = A[(size_t)x * D + q];
         A[(size_t)x * D + p] = c * ap - sn * aq;
         A[(size_t)x * D + q] = sn * ap + c * aq;
-        const double vp = V[(size_t)x * D + p], vq = V[(size_t)x * D + q];
+        const W vp = V[(size_t)x * D + p], vq = V[(size_t)x * D + q];
         V[(size_t)x * D + p] = c * vp - sn * vq;
         V[(size_t)x * D + q] = sn * vp + c * vq;
       }
@@ -203,7 +218,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_psd_repair(double* __restric
   if (tid == 0) s_neg = 0;
   __syncthreads();
   for (int i = tid; i < D; i += nth) {
-    const double l = A[(size_t)i * D + i];
+    const double l = (double)A[(size_t)i * D + i];
     s_lam[i] = l > 0.0 ? l : 0.0;
     if (l < 0.0) atomicAdd(&s_neg, 1);
   }
@@ -213,8 +228,8 @@ __global__ void __launch_bounds__(kJacobiThreads) k_psd_repair(double* __restric
   for (int e = tid; e < D * D; e += nth) {
     const int i = e / D, j = e - i * D;
     if (j < i) continue;
-    double v = 0.0;
-    for (int k = 0; k < D; ++k) v += V[(size_t)i * D + k] * s_lam[k] * V[(size_t)j * D + k];
+    W v = 0;
+    for (int k = 0; k < D; ++k) v += V[(size_t)i * D + k] * (W)s_lam[k] * V[(size_t)j * D + k];
     sig[(size_t)i * D + j] = v;
     sig[(size_t)j * D + i] = v;
   }
@@ -262,9 +277,28 @@ cudaError_t launch_pairwise(bool fp64, bool fejer, const void* coeffs, int ld, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_psd_repair(double* sig, double* A, double* V, int D, int* clipped, cudaStream_t s) {
+cudaError_t launch_psd_repair(bool fp64, double* sig, double* A, double* V, int D, int* clipped, cudaStream_t s) {
   if (D > kPsdMaxD) return cudaErrorInvalidValue;
-  k_psd_repair<<<1, kJacobiThreads, 0, s>>>(sig, A, V, D, clipped);
+  auto go = [&](auto kern, size_t wbytes) -> cudaError_t {
+    const size_t need = 2 * (size_t)D * D * wbytes;
+    const size_t smem = need <= kPsdSmemBytes ? need : 0;
+    if (smem) {
+      const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  cudaError_t e;
+  if (fp64) {
+    if ((e = go(k_psd_repair<double>, 8)) != cudaSuccess) return e;
+    const size_t need = 2 * (size_t)D * D * 8;
+    k_psd_repair<double><<<1, kJacobiThreads, need <= kPsdSmemBytes ? need : 0, s>>>(sig, A, V, D, clipped);
+  } else {
+    if ((e = go(k_psd_repair<float>, 4)) != cudaSuccess) return e;
+    const size_t need = 2 * (size_t)D * D * 4;
+    k_psd_repair<float><<<1, kJacobiThreads, need <= kPsdSmemBytes ? need : 0, s>>>(sig, (float*)A, (float*)V, D,
+                                                                                     clipped);
+  }
   return cudaGetLastError();
 }
 

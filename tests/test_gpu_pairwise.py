@@ -5,8 +5,10 @@ Tolerances: Sigma, max |dSigma_ij| / sqrt(Sigma_ii Sigma_jj) <= 1e-4 (mixed)
 and 1e-9 (FP64), R <= 1e-4 / 1e-9, as for the common cutoff. The repair maps
 a symmetric matrix to its nearest positive semi-definite one, a map that
 moves no two inputs further apart in the Frobenius norm than they were: the
-repaired matrices may differ by at most the input matrices' difference (times
-2, for the float64 Jacobi iteration's own rounding) plus 1e-12 of the norm.
+repaired matrices may differ by at most twice the input matrices' difference
+plus the eigensolver's own rounding, 1e-12 of the norm for the float64
+Jacobi iteration (FP64 plans) and 1e-5 for the float32 one (mixed
+precisions, whose Sigma is itself correct to about 1e-5 of its scale).
 """
 import numpy as np
 import pytest
@@ -18,7 +20,7 @@ from gpu_helpers import sigma_err, to_dev
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": dict(tol=1e-12, sig=1e-9, R=1e-9), "bf16x3": dict(tol=1e-6, sig=1e-4, R=1e-4)}
+TOL = {"fp64": dict(tol=1e-12, sig=1e-9, R=1e-9, eig=1e-12), "bf16x3": dict(tol=1e-6, sig=1e-4, R=1e-4, eig=1e-5)}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -74,7 +76,7 @@ def test_psd_repair_matches_oracle(prec, basis, seed):
     assert neg >= 1  # the pairwise estimate is not positive semi-definite here
     assert out["status"] == 0 and out["clipped"] == neg
     d_in = np.linalg.norm(raw["S"] - S_ref)
-    assert np.linalg.norm(out["S"] - P_ref) <= 2.0 * d_in + 1e-12 * np.linalg.norm(S_ref)
+    assert np.linalg.norm(out["S"] - P_ref) <= 2.0 * d_in + TOL[prec]["eig"] * np.linalg.norm(S_ref)
     assert np.linalg.eigvalsh(out["S"]).min() >= -1e-5 * np.abs(np.linalg.eigvalsh(S_ref)).max()
     assert np.max(np.abs(out["R"] - oracle.corr(P_ref))) <= 10 * TOL[prec]["R"]
 
