@@ -161,6 +161,41 @@ def mse_bias_replications(seed, reps, n=100, rho=0.35, var=(0.1, 0.2), mu=0.01):
     return ev
 
 
+def sensitivity_covariances(seed, count, var=(0.1, 0.3), cov=(-0.1, 0.1), max_corr=0.9):
+    """Daily 2x2 covariance matrices for the sensitivity test (App. B): both
+    variances uniform on `var`, the covariance uniform on `cov` and clipped to
+    a correlation of at most max_corr (a definite matrix)."""
+    rng = rng_for(9, seed)
+    out = []
+    for _ in range(count):
+        v1, v2 = rng.uniform(*var, size=2)
+        lim = max_corr * np.sqrt(v1 * v2)
+        c = float(np.clip(rng.uniform(*cov), -lim, lim))
+        out.append(np.array([[v1, c], [c, v2]]))
+    return out
+
+
+def sensitivity_replications(seed, covs, reps=1, n=10000, mu=0.01):
+    """The sensitivity test (App. B): synchronous bivariate GBMs of n points
+    over one day (step 1/n day), `reps` replications of each daily 2x2
+    covariance in covs; all stacked as one Events (2 assets per problem).
+    meta["truth"] holds each problem's integrated covariance over the path,
+    (n - 1)/n times the daily one."""
+    ts, ps, truth = [], [], []
+    t = np.arange(n, dtype=np.float64)
+    for i, cov in enumerate(covs):
+        cov = np.asarray(cov, np.float64)
+        for r in range(reps):
+            rng = rng_for(8, seed, i, r)
+            lp = gbm_grid(n, mu, cov, rng, dt_days=1.0 / n)
+            ts += [t, t]
+            ps += [lp[:, 0], lp[:, 1]]
+            truth.append(cov * (n - 1) / n)
+    ev = from_lists(ts, ps)
+    ev.meta = {"workload": f"sensitivity_n{n}", "truth": np.array(truth), "n": n}
+    return ev
+
+
 def _continuous_poisson(T, rate, rng):
     n = rng.poisson(rate * T)
     return np.sort(rng.uniform(0.0, T, size=n))
