@@ -268,11 +268,14 @@ __device__ void corr_epilogue_block(const float* __restrict__ acc, const GramPar
     const int i = e / g.Dp, j = e - i * g.Dp;
     if (zero_next) zero_next[e] = 0.0f;
     if (j >= g.D) continue;
-    const bool up = (i / kTile) <= (j / kTile);
-    const double v = up ? (double)__ldcg(acc + (int64_t)i * g.Dp + j) : (double)__ldcg(acc + (int64_t)j * g.Dp + i);
+    // (min, max) is in an accumulated tile pair; reading it for both (i, j)
+    // and (j, i), with the commuting product a * b, makes Sigma and R exactly
+    // symmetric (the split-K sums of acc[i][j] and acc[j][i] within a
+    // diagonal tile round in different orders)
+    const double v = (double)__ldcg(acc + (int64_t)min(i, j) * g.Dp + max(i, j));
     const double a = s_inv[i], b = s_inv[j];
     double r;
-    if (a > 0.0 && b > 0.0) r = (i == j) ? 1.0 : v * a * b;
+    if (a > 0.0 && b > 0.0) r = (i == j) ? 1.0 : v * (a * b);
     else {
       r = __longlong_as_double(0x7ff8000000000000ll);
       if (i == j) zero = true;
@@ -296,9 +299,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restr
   int I, J;
   pair_of(blockIdx.y, g.ntiles, I, J);
   const bool two = I != J;
+  // the K-chunks spread evenly over the splits (at most chunks_per_split each)
   const int s = blockIdx.x;
-  const int c0 = s * g.chunks_per_split;
-  const int c1 = min(c0 + g.chunks_per_split, g.nchunks);
+  const int c0 = (int)((int64_t)s * g.nchunks / g.splits);
+  const int c1 = (int)((int64_t)(s + 1) * g.nchunks / g.splits);
   const int nit = c1 - c0;
 
   // 1024-byte aligned staging area: per stage [A_hi][A_lo]([B_hi][B_lo])
@@ -440,7 +444,8 @@ cudaError_t launch_gram_tc(int mode, const void* coeffs, const GramParams& g, co
 }
 
 // Sigma and R from the FP32 accumulator of k_gram_tc (upper tile pairs only:
-// entry (i, j) lives at acc[i][j] when tile(i) <= tile(j), else acc[j][i]).
+// entry (i, j) lives at acc[i][j] when tile(i) <= tile(j), else acc[j][i];
+// both triangles read acc[min(i, j)][max(i, j)]).
 // The normalisation R_ij = Sigma_ij / (sqrt(Sigma_ii) sqrt(Sigma_jj)) is in
 // FP64; R_ii = 1 exactly; zero variance gives NaN and a status. The block
 // also clears the matching entries of zero_next, the accumulator the next
@@ -469,11 +474,11 @@ __global__ void __launch_bounds__(256) k_corr_acc(const float* __restrict__ acc,
   if (i >= g.D || j >= g.Dp) return;
   if (zero_next) zero_next[(int64_t)i * g.Dp + j] = 0.0f;
   if (j >= g.D) return;
-  const bool up = (i / kTile) <= (j / kTile);
-  const double v = up ? (double)acc[(int64_t)i * g.Dp + j] : (double)acc[(int64_t)j * g.Dp + i];
+  // read (min, max) for both triangles: exactly symmetric Sigma and R
+  const double v = (double)acc[(int64_t)min(i, j) * g.Dp + max(i, j)];
   const double a = s_inv_i[li], b = s_inv_j[lj];
   double r;
-  if (a > 0.0 && b > 0.0) r = (i == j) ? 1.0 : v * a * b;
+  if (a > 0.0 && b > 0.0) r = (i == j) ? 1.0 : v * (a * b);
   else {
     r = __longlong_as_double(0x7ff8000000000000ll);
     if (i == j) atomicOr(status, ST_ZERO_VAR);

@@ -217,22 +217,47 @@ constexpr int kSpreadThreads = 256;
 constexpr int kNoCell = -0x40000000;  // cell of a skipped event (outside every window)
 
 // ------------------------------------------------------------------ prep
-// Steps a0 / a1 of the hot path, one thread per event h: the rescaled cell
+// Steps a0 / a1 of the hot path: for each event h, the rescaled cell
 // coordinate in exact fixed point (Algorithm 4), split into the cell b0 and
 // the offset d in [0, 1), and the return delta = logp[h+1] - logp[h]
 // (Algorithm 3 step F.3), written once as a compact record (b0, d, delta) in
 // event order. Since each asset's times are sorted, its records are sorted
 // by cell: that order is the bin sort the spreading kernels search. The
-// last event of an asset carries no return and its record is not read.
+// last event of an asset carries no return and its record is never read
+// (it holds kNoCell or is left as it was).
+//
+// Each thread takes kPrepE consecutive events: it loads kPrepE + 1 times and
+// log-prices, orders, checks and splits each value once (every value but the
+// last serves two returns), and writes its records with vector stores.
+constexpr int kPrepE = 4;
+constexpr int kPrepThreads = 256;
+
+template <typename T> struct Rec4;
+template <> struct Rec4<float> {
+  static __device__ __forceinline__ void store(float* p, const float* v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <> struct Rec4<double> {
+  static __device__ __forceinline__ void store(double* p, const double* v) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+};
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_prep(const int64_t* __restrict__ off, const double* __restrict__ t,
-                                              const double* __restrict__ logp, const Rescale* __restrict__ rsp,
-                                              const GroupScale* __restrict__ gsc, int gsize,
-                                              const int* __restrict__ gate, int D, int64_t Mr, int* __restrict__ rb0,
-                                              T* __restrict__ rd, T* __restrict__ rv, int* status) {
+__global__ void __launch_bounds__(kPrepThreads, 5) k_prep(const int64_t* __restrict__ off, const double* __restrict__ t,
+                                                       const double* __restrict__ logp,
+                                                       const Rescale* __restrict__ rsp,
+                                                       const GroupScale* __restrict__ gsc, int gsize,
+                                                       const int* __restrict__ gate, int D, int64_t Mr,
+                                                       int* __restrict__ rb0, T* __restrict__ rd,
+                                                       T* __restrict__ rv, int* status) {
+  static_assert(kPrepE == 4, "records are stored as 4-vectors");
   __shared__ UScale s_us;
   __shared__ UScaleF s_usf;
   __shared__ int s_flags;
+  __shared__ int s_a0;
   // one round of loads: the gate, the event count and the call's rescaling
   // (with its cell scales when k_bounds knew the grid); then each thread's
   // event loads are in flight while warp 0 finds the block's asset. No event
@@ -244,14 +269,16 @@ __global__ void __launch_bounds__(256) k_prep(const int64_t* __restrict__ off, c
   if (!gsc) rs0 = *rsp;
   if (gated) return;  // uniform
   const bool scales = gsc || rs0.scale_Mr == Mr;  // uniform
-  const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double th = 0.0, tn = 0.0, p0 = 0.0, p1 = 0.0;
-  if (h < ntot) {
-    th = t[h];
-    p0 = logp[h];
-    if (h + 1 < ntot) {
-      tn = t[h + 1];
-      p1 = logp[h + 1];
+  const int64_t hb = (int64_t)blockIdx.x * (kPrepThreads * kPrepE);
+  const int64_t h0 = hb + (int64_t)threadIdx.x * kPrepE;
+  double tv[kPrepE + 1], pv[kPrepE + 1];
+#pragma unroll
+  for (int j = 0; j <= kPrepE; ++j) {
+    tv[j] = 0.0;
+    pv[j] = 0.0;
+    if (h0 + j < ntot) {
+      tv[j] = t[h0 + j];
+      pv[j] = logp[h0 + j];
     }
   }
   if (threadIdx.x == 0) {
@@ -262,18 +289,17 @@ __global__ void __launch_bounds__(256) k_prep(const int64_t* __restrict__ off, c
     s_flags = 0;
   }
   // asset of the block's first event (a 32-ary search by warp 0, a couple of
-  // dependent loads), then each thread walks forward to its own asset
-  __shared__ int s_a0;
+  // dependent loads), then each thread walks forward to its own events' assets
   if (threadIdx.x < 32) {
-    const int64_t hb = min((int64_t)blockIdx.x * blockDim.x, ntot > 0 ? ntot - 1 : 0);
-    // first index in [1, D] with off[idx] > hb (D when none): the asset is idx - 1
+    const int64_t hs = min(hb, ntot > 0 ? ntot - 1 : 0);
+    // first index in [1, D] with off[idx] > hs (D when none): the asset is idx - 1
     const int lane = threadIdx.x;
     int64_t lo = 1, hi = D;
     for (int it = 0; it < 16 && hi > lo; ++it) {
       const int64_t len = hi - lo;
       const int64_t stride = (len + 31) / 32;
       const int64_t o = (int64_t)lane * stride;
-      const bool below = o < len && off[lo + o] <= hb;
+      const bool below = o < len && off[lo + o] <= hs;
       const int cnt = __popc(__ballot_sync(0xffffffffu, below));
       if (cnt == 0) {
         hi = lo;
@@ -286,62 +312,92 @@ __global__ void __launch_bounds__(256) k_prep(const int64_t* __restrict__ off, c
     }
     if (lane == 0) s_a0 = (int)lo - 1;
   }
+  // per value, once: order key, finiteness and (float32 path) the exact
+  // hi + lo split of the log-price
+  long long key[kPrepE + 1];
+  bool fin_t[kPrepE + 1], fin_p[kPrepE + 1];
+  float ph[kPrepE + 1], pl[kPrepE + 1];
+#pragma unroll
+  for (int j = 0; j <= kPrepE; ++j) {
+    key[j] = order_key(tv[j]);
+    fin_t[j] = finite_bits(tv[j]);
+    fin_p[j] = finite_bits(pv[j]);
+    if (sizeof(T) == 4) split_f64(pv[j], ph[j], pl[j]);
+  }
   __syncthreads();
   int flags = 0;
-  if (h < ntot) {
-    int lo = s_a0;
+  int b0v[kPrepE];
+  T dv[kPrepE], vv[kPrepE];
+  int lo = s_a0;
+#pragma unroll
+  for (int j = 0; j < kPrepE; ++j) {
+    const int64_t h = h0 + j;
+    b0v[j] = kNoCell;
+    dv[j] = (T)0;
+    vv[j] = (T)0;
+    if (h >= ntot) continue;
     while (lo + 1 < D && off[lo + 1] <= h) ++lo;
-    if (h + 1 < off[lo + 1]) {
-      // this event's problem: its fixed-point scale (batched form) or the
-      // call's single one
-      Rescale rs = rs0;
-      UScale us;
-      UScaleF usf;
-      if (gsc) {
-        const GroupScale q = gsc[lo / gsize];
-        rs.t0_fix = q.t0_fix;
-        rs.F = q.F;
-        us = q.us;
-        usf = q.usf;
-      } else if (scales) {
-        us.S = rs0.S;
-        us.sh = rs0.sh;
-        usf.s_hi = rs0.s_hi;
-        usf.s_lo = rs0.s_lo;
-      } else {
-        us = s_us;
-        usf = s_usf;
+    if (!(h + 1 < off[lo + 1])) continue;  // the asset's last event: no return
+    // this event's problem: its fixed-point scale (batched form) or the
+    // call's single one
+    Rescale rs = rs0;
+    UScale us;
+    UScaleF usf;
+    if (gsc) {
+      const GroupScale q = gsc[lo / gsize];
+      rs.t0_fix = q.t0_fix;
+      rs.F = q.F;
+      us = q.us;
+      usf = q.usf;
+    } else if (scales) {
+      us.S = rs0.S;
+      us.sh = rs0.sh;
+      usf.s_hi = rs0.s_hi;
+      usf.s_lo = rs0.s_lo;
+    } else {
+      us = s_us;
+      usf = s_usf;
+    }
+    if (!(key[j] < key[j + 1])) flags |= (key[j] == key[j + 1]) ? ST_DUPLICATE : ST_UNSORTED;
+    if (!(fin_t[j] && fin_p[j] && fin_p[j + 1])) {
+      flags |= ST_NONFINITE;
+      continue;
+    }
+    const long long dt = to_fix(tv[j], rs.F) - rs.t0_fix;
+    int cb;
+    T cd;
+    if (sizeof(T) == 8) {
+      const unsigned long long uf = u_fix_of(tv[j], rs.t0_fix, rs.F, us);
+      cb = (int)(uf >> kUFrac);
+      cd = frac_to<T>(uf & ((1ull << kUFrac) - 1));
+    } else {
+      float fd;
+      cell_f32(dt, usf, cb, fd);
+      cd = (T)fd;
+    }
+    if (dt < 0 || cb > Mr || (cb == Mr && cd > (T)0)) {
+      flags |= ST_OUT_OF_WINDOW;
+      continue;
+    }
+    b0v[j] = cb;
+    dv[j] = cd;
+    if (sizeof(T) == 8) vv[j] = (T)(pv[j + 1] - pv[j]);
+    else vv[j] = (T)((ph[j + 1] - ph[j]) + (pl[j + 1] - pl[j]));
+  }
+  if (h0 + kPrepE <= ntot) {
+    // h0 is a multiple of 4 and the record arrays are the plan's own
+    // (256-byte aligned) allocations: 16-byte vector stores
+    *reinterpret_cast<int4*>(rb0 + h0) = make_int4(b0v[0], b0v[1], b0v[2], b0v[3]);
+    Rec4<T>::store(rd + h0, dv);
+    Rec4<T>::store(rv + h0, vv);
+  } else {
+#pragma unroll
+    for (int j = 0; j < kPrepE; ++j) {
+      if (h0 + j < ntot) {
+        rb0[h0 + j] = b0v[j];
+        rd[h0 + j] = dv[j];
+        rv[h0 + j] = vv[j];
       }
-      const long long kh = order_key(th), kn = order_key(tn);
-      if (!(kh < kn)) flags |= (kh == kn) ? ST_DUPLICATE : ST_UNSORTED;
-      int b0 = kNoCell;
-      T d = (T)0, v = (T)0;
-      if (!(finite_bits(th) && finite_bits(p0) && finite_bits(p1))) {
-        flags |= ST_NONFINITE;
-      } else {
-        const long long dt = to_fix(th, rs.F) - rs.t0_fix;
-        int cb;
-        T cd;
-        if (sizeof(T) == 8) {
-          const unsigned long long uf = u_fix_of(th, rs.t0_fix, rs.F, us);
-          cb = (int)(uf >> kUFrac);
-          cd = frac_to<T>(uf & ((1ull << kUFrac) - 1));
-        } else {
-          float fd;
-          cell_f32(dt, usf, cb, fd);
-          cd = (T)fd;
-        }
-        if (dt < 0 || cb > Mr || (cb == Mr && cd > (T)0)) {
-          flags |= ST_OUT_OF_WINDOW;
-        } else {
-          b0 = cb;
-          d = cd;
-          v = return_of<T>(p0, p1);
-        }
-      }
-      rb0[h] = b0;
-      rd[h] = d;
-      rv[h] = v;
     }
   }
   if (flags) atomicOr(&s_flags, flags);
@@ -355,9 +411,11 @@ static cudaError_t launch_prep_t(const int64_t* off, const double* t, const doub
                                  const GroupScale* gsc, int gsize, int D, int64_t Mr, int64_t max_events, int* rb0,
                                  T* rd, T* rv, int* status, cudaStream_t s) {
   if (max_events <= 0) return cudaSuccess;
-  const int64_t blocks = (max_events + 255) / 256;
-  return launch_pdl(k_prep<T>, dim3((unsigned)blocks), dim3(256), 0, s, off, t, logp, rs, gsc, gsize, status + 1, D,
-                    Mr, rb0, rd, rv, status);
+  if ((((uintptr_t)rb0) | ((uintptr_t)rd) | ((uintptr_t)rv)) & 15) return cudaErrorMisalignedAddress;
+  const int64_t per_block = (int64_t)kPrepThreads * kPrepE;
+  const int64_t blocks = (max_events + per_block - 1) / per_block;
+  return launch_pdl(k_prep<T>, dim3((unsigned)blocks), dim3(kPrepThreads), 0, s, off, t, logp, rs, gsc, gsize,
+                    status + 1, D, Mr, rb0, rd, rv, status);
 }
 
 cudaError_t launch_prep_f32(const int64_t* off, const double* t, const double* logp, const Rescale* rs,

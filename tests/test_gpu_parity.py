@@ -167,6 +167,36 @@ def test_many_assets_multi_tile_contraction(prec):
     assert np.max(np.abs(out["R"].astype(np.float64) - ref["R"])) <= tl["R"]
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "3xtf32"])
+@pytest.mark.parametrize("D", [40, 100, 128])
+def test_split_k_contraction_exactly_symmetric_over_repeated_calls(prec, D):
+    # one output tile split over many K-chunks: the split sums of acc[i][j]
+    # and acc[j][i] reduce in L2 in different orders, yet Sigma and R come out
+    # exactly symmetric; repeated calls alternate the two accumulators (one
+    # cleared while the other is read) and change the cutoff
+    import torch
+    import paper_2003_02842_gb300 as mm
+    ev = synth.random_events(33 + D, D=D, n_range=(50, 400), T=20000.0)
+    tl = TOL[prec]
+    plan = mm.mm_plan_create(D=D, N_max=2000, max_events=ev.n_events, tol=tl["tol"], kernel="es", basis="fejer",
+                             prec=prec)
+    off, t, p = to_dev(ev)
+    for N in (2000, 1500, 2000, 300):
+        F, S, R, _ = mm.mm_estimate(plan, off, t, p, N)
+        assert mm.mm_plan_sync(plan) == 0
+        if N >= 1500:
+            assert mm.mm_plan_get_info(plan)["gram_splits"] >= 16
+        ref = oracle.estimate(ev.offsets, ev.t, ev.logp, N=N, basis="fejer")
+        assert sigma_err(S.cpu().numpy(), ref["Sigma"]) <= tl["sig"], N
+        Rg = R.cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(Rg - ref["R"])) <= tl["R"], N
+        assert np.all(np.diag(Rg) == 1.0) and np.array_equal(Rg, Rg.T)
+        Sg = S.cpu().numpy()
+        assert np.array_equal(Sg, Sg.T)
+    torch.cuda.synchronize()
+    mm.mm_destroy(plan)
+
+
 def test_single_asset_and_tiny_problem():
     ev = synth.from_lists([[0.0, 1.0, 3.5]], [[4.6, 4.61, 4.59]])
     for prec in ("fp64", "bf16x3"):
