@@ -276,6 +276,7 @@ struct mm_plan_s {
   void* s_coef = nullptr;
   void* s_sigma = nullptr;
   void* s_R = nullptr;
+  int* h_status = nullptr;        // pinned: the host-buffer entry point's status read-back
   int64_t workspace = 0;
   // per-cutoff configuration
   int cfg_N = -1;
@@ -350,6 +351,7 @@ void free_all(mm_plan p) {
                   p->s_sigma, p->s_R};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  if (p->h_status) cudaFreeHost(p->h_status);
   for (auto& e : p->eg)
     if (e.exec) cudaGraphExecDestroy(e.exec);
   if (p->cap) cudaStreamDestroy(p->cap);
@@ -966,6 +968,7 @@ mm_status plan_create_impl(const mm_plan_desc* desc, int gsize, bool batch, mm_p
     A(&p->s_coef, D * Np1 * p->cs);
     A(&p->s_sigma, D * D * p->rs);
     A(&p->s_R, D * D * p->rs);
+    if (r == MM_OK && cudaMallocHost((void**)&p->h_status, sizeof(int)) != cudaSuccess) r = MM_ERR_OOM;
   }
   if (r == MM_OK) {
     if (cudaMemset(p->status, 0, 4 * sizeof(int)) != cudaSuccess) r = MM_ERR_CUDA;
@@ -1112,7 +1115,18 @@ mm_status mm_estimate_host(mm_plan p, const int64_t* h_offsets, const double* h_
   if (h_coeffs_or_null)
     MM_CUDA(cudaMemcpyAsync(h_coeffs_or_null, p->s_coef, (size_t)D * (Nu + 1) * p->cs, cudaMemcpyDeviceToHost, st));
   if (N_used) *N_used = Nu;
-  return mm_plan_sync(p);
+  // the status word comes back with the results: one synchronisation
+  MM_CUDA(cudaMemcpyAsync(p->h_status, p->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  MM_CUDA(cudaStreamSynchronize(st));
+  const int f = *p->h_status;
+  if (f) {
+    // as mm_plan_sync: clear the status, and a split FFT's pair words after a timed-out wait
+    MM_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), st));
+    if ((f & ST_TIMEOUT) && p->fft_sync)
+      MM_CUDA(cudaMemsetAsync(p->fft_sync, 0, 2 * (size_t)p->desc.D * sizeof(int), st));
+    MM_CUDA(cudaStreamSynchronize(st));
+  }
+  return flags_to_status(f);
 }
 
 mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, const double* d_logp, int32_t N,
