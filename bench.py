@@ -479,12 +479,14 @@ def bench_serve(args):
     for r in reqs[:16]:
         mm.mm_server_submit(srv, r["t0"], r["t1"], r["assets"], dt=r["dt"])
     drain(16)
+    launches0 = mm.mm_server_get_stats(srv)["launches"]
     with ClockSampler(dev.index) as clk:
         t0 = time.time()
         for r in reqs:
             mm.mm_server_submit(srv, r["t0"], r["t1"], r["assets"], dt=r["dt"])
         done = drain(len(reqs))
         wall = time.time() - t0
+        launches = mm.mm_server_get_stats(srv)["launches"] - launches0
         ok = [c for c in done if c["status"] in (0, 9)]
         thr = len(done) / wall
         # latency phase: open-loop Poisson arrivals at load x throughput
@@ -525,7 +527,7 @@ def bench_serve(args):
                        "service_p99": float(np.percentile(svc, 99))},
         "peak_inflight": stats["peak_inflight"],
         "clocks": clocks,
-        "gpu_launches": None,
+        "gpu_launches": int(launches),
     }
     print(json.dumps(line), flush=True)
 

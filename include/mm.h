@@ -439,6 +439,8 @@ typedef struct {
   int64_t slot_bytes;          /* device workspace per slot */
   int64_t resident_bytes;      /* the resident event store */
   int32_t slots, inflight, peak_inflight, queued;
+  int64_t launches;            /* kernels launched for requests since creation (the window
+                                  gather and the slot plans' own, graph replays included) */
 } mm_server_stats;
 
 typedef struct mm_server_s* mm_server;

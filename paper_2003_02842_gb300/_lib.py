@@ -151,6 +151,7 @@ class ServerStats(ctypes.Structure):
         ("inflight", ctypes.c_int32),
         ("peak_inflight", ctypes.c_int32),
         ("queued", ctypes.c_int32),
+        ("launches", ctypes.c_int64),
     ]
 
 

@@ -14,6 +14,7 @@
 // Requests complete out of order; the caller polls completions with their
 // submit / start / finish times (host clock), from which p50 / p99 latency
 // follow.
+#include <atomic>
 #include <math.h>
 #include <string.h>
 
@@ -153,6 +154,7 @@ struct mm_server_s {
   bool stop = false;
   int64_t next_ticket = 1;
   int64_t submitted = 0, completed = 0;
+  std::atomic<int64_t> launches{0};  // kernels launched for requests (start() runs outside mu)
   int inflight = 0, peak_inflight = 0;
   double t_origin = 0;
 };
@@ -225,6 +227,8 @@ void start(mm_server s, Slot& sl, Req&& rq) {
     cudaEventRecord(sl.done, st);
   };
   memcpy(sl.h_assets, sl.req.assets.data(), (size_t)n * 4);
+  mm_plan_info pi0{};
+  mm_plan_get_info(sl.p, &pi0);
   int* status = plan_status_word(sl.p);
   if (cudaMemcpyAsync(sl.d_assets, sl.h_assets, (size_t)n * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess)
@@ -233,6 +237,7 @@ void start(mm_server s, Slot& sl, Req&& rq) {
                                                   sl.req.t1, s->req_events, sl.d_lo, sl.d_off, status);
   k_window_copy<<<n, 256, 0, st>>>(sl.d_lo, sl.d_off, s->d_t_all, s->d_p_all, sl.d_t, sl.d_p);
   if (cudaGetLastError() != cudaSuccess) return fail(MM_ERR_CUDA);
+  s->launches.fetch_add(2);
   mm_status r = plan_set_active_assets(sl.p, n);
   if (r != MM_OK) return fail(r);
   int N = sl.req.N;
@@ -252,6 +257,8 @@ void start(mm_server s, Slot& sl, Req&& rq) {
   sl.N_used = Nu;
   r = mm_corr(sl.p, sl.d_coef, Nu, sl.req.h_S ? sl.d_S : nullptr, sl.d_R, st);
   if (r != MM_OK) return fail(r);
+  mm_plan_info pi1{};
+  if (mm_plan_get_info(sl.p, &pi1) == MM_OK) s->launches.fetch_add(pi1.launches - pi0.launches);
   const size_t bytes = (size_t)n * n * s->rs;
   if (cudaMemcpyAsync(sl.h_R, sl.d_R, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       (sl.req.h_S && cudaMemcpyAsync(sl.h_S, sl.d_S, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
@@ -450,6 +457,7 @@ mm_status mm_server_get_stats(mm_server s, mm_server_stats* st) {
   st->completed = s->completed;
   st->slot_bytes = s->slot_bytes;
   st->resident_bytes = (int64_t)(s->desc.D + 1) * 8 + 16 * s->desc.max_events;
+  st->launches = s->launches.load();
   return MM_OK;
 }
 

@@ -97,6 +97,9 @@ def test_same_result_alone_and_in_a_mix(day):
     assert sigma_err(inmix["Sigma"], alone["Sigma"].astype(np.float64)) <= 1e-6
     st = mm.mm_server_get_stats(srv)
     assert st["peak_inflight"] >= 2 and st["completed"] == 42
+    # every request: the window gather (two kernels) and the slot plan's
+    # coefficient and contraction kernels (at least four)
+    assert st["launches"] >= 6 * 42
     # the mix itself is right too
     for t, r in zip(tks[:5], mix[:5]):
         _check(day, r, done[t])
