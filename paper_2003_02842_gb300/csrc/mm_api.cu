@@ -277,6 +277,7 @@ struct mm_plan_s {
   void* s_sigma = nullptr;
   void* s_R = nullptr;
   int* h_status = nullptr;        // pinned: the host-buffer entry point's status read-back
+  int* asset_order = nullptr;     // spreading dispatch order (single problems of D <= kOrderMaxAssets)
   int64_t workspace = 0;
   // per-cutoff configuration
   int cfg_N = -1;
@@ -348,7 +349,7 @@ void free_all(mm_plan p) {
   void* ptrs[] = {p->grid, p->rec_b0, p->rec_d, p->rec_v, p->W, p->atw, p->U, p->decon, p->glx, p->glw, p->bounds, p->gscale, p->status, p->gapbits, p->wsq,
                   p->partial, p->acc[0], p->acc[1], p->gram_done, p->fft_sync, p->pw_N, p->pw_sig, p->pw_A,
                   p->pw_V, p->pw_clip, p->s_off, p->s_t, p->s_p, p->s_coef,
-                  p->s_sigma, p->s_R};
+                  p->s_sigma, p->s_R, p->asset_order};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->h_status) cudaFreeHost(p->h_status);
@@ -643,9 +644,13 @@ mm_status coeffs_impl(mm_plan p, const int64_t* off, const double* t, const doub
     if (rc != MM_OK) return rc;
     Mr_known = p->Mr;
   }
+  // one condition for both sides: k_bounds writes the order the spreading
+  // kernel then reads
+  const bool use_order = p->asset_order && p->G == 1 && D <= kOrderMaxAssets;
   {
     StageScope sc(p, MM_STAGE_PREP, st);
-    MM_CUDA(launch_bounds(off, t, D, p->gsize, p->desc.max_events, t0, t1, Mr_known, p->bounds, p->status, st));
+    MM_CUDA(launch_bounds(off, t, D, p->gsize, p->desc.max_events, t0, t1, Mr_known, p->bounds, p->status,
+                          use_order ? p->asset_order : nullptr, st));
   }
   if (N <= 0 && p->G > 1) return MM_ERR_CUTOFF;  // a batch sweeps given cutoffs
   if (N <= 0) {
@@ -689,6 +694,7 @@ mm_status coeffs_impl(mm_plan p, const int64_t* off, const double* t, const doub
     }
     {
       StageScope sc(p, MM_STAGE_SPREAD, st);
+      p->sp.order = use_order ? p->asset_order : nullptr;
       if (p->fp64)
         MM_CUDA(launch_spread_f64(off, p->rec_b0, p->rec_d, p->rec_v, p->sp, (double*)p->grid, p->status, st));
       else if (p->poly_ok)
@@ -945,6 +951,7 @@ mm_status plan_create_impl(const mm_plan_desc* desc, int gsize, bool batch, mm_p
   A((void**)&p->glx, kGlNodes * sizeof(double));
   A((void**)&p->glw, kGlNodes * sizeof(double));
   A((void**)&p->bounds, (size_t)p->G * sizeof(Rescale));
+  if (!batch && D <= (size_t)kOrderMaxAssets) A((void**)&p->asset_order, std::max<size_t>(D, 1) * sizeof(int));
   if (p->G > 1) A(&p->gscale, (size_t)p->G * group_scale_bytes());
   A((void**)&p->status, 4 * sizeof(int));
   A((void**)&p->gapbits, sizeof(unsigned long long));
@@ -1235,7 +1242,8 @@ mm_status mm_nyquist(mm_plan p, const int64_t* d_offsets, const double* d_t, dou
   p->last = st;
   {
     StageScope sc(p, MM_STAGE_PREP, st);
-    MM_CUDA(launch_bounds(d_offsets, d_t, p->D, p->gsize, p->desc.max_events, t0, t1, 0, p->bounds, p->status, st));
+    MM_CUDA(launch_bounds(d_offsets, d_t, p->D, p->gsize, p->desc.max_events, t0, t1, 0, p->bounds, p->status,
+                          nullptr, st));
   }
   {
     StageScope sc(p, MM_STAGE_PREP, st, 2);

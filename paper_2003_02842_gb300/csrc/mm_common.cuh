@@ -73,7 +73,13 @@ struct SpreadParams {
   double kb_b;       // KB: b = pi (2 - 1/sigma)
   double kb_inv_phi0;// KB: 1 / phi(0) (kernel normalised to peak 1)
   int64_t max_events;
+  // spreading tiles are dispatched asset by asset in this order (the assets
+  // ranked by event count, heaviest first, written by k_bounds), or in index
+  // order when null
+  const int* order;
 };
+
+constexpr int kOrderMaxAssets = 256;  // k_bounds ranks the assets of a single problem up to this D
 
 // Averaging kernel of the float32 path as one polynomial per stencil tap:
 // phi(k - d) ~ sum_i c[j][i] (d - 1/2)^i for tap k = klo + j and d in [0, 1),
@@ -159,8 +165,10 @@ constexpr int kMaxEppsAssets = 12;
 // Each returns cudaGetLastError() of its launch.
 // Mr > 0: also the cell scales of grid Mr (so later kernels do no float64
 // arithmetic for them); 0 when the grid is not known yet.
+// order != NULL (a single problem of D <= kOrderMaxAssets): also ranks the
+// assets by event count, heaviest first, into order[0..D-1].
 cudaError_t launch_bounds(const int64_t* off, const double* t, int D, int gsize, int64_t max_events,
-                          double w0, double w1, int64_t Mr, Rescale* rs, int* status, cudaStream_t s);
+                          double w0, double w1, int64_t Mr, Rescale* rs, int* status, int* order, cudaStream_t s);
 cudaError_t launch_group_scales(const Rescale* rs, int G, int64_t Mr, GroupScale* out, const int* status,
                                 cudaStream_t s);
 size_t group_scale_bytes();

@@ -39,7 +39,8 @@ namespace mmgpu {
 // non-decreasing and lie in [0, max_events], so a malformed offsets array
 // anywhere leaves every read in bounds.
 __global__ void k_bounds(const int64_t* __restrict__ off, const double* __restrict__ t, int D, int gsize,
-                         int64_t max_events, double w0, double w1, int64_t Mr, Rescale* rs, int* status) {
+                         int64_t max_events, double w0, double w1, int64_t Mr, Rescale* rs, int* status,
+                         int* __restrict__ order) {
   __shared__ double s_lo[8], s_hi[8];
   __shared__ int s_bad;
   pdl_wait();     // the previous call's kernels may still read the gate
@@ -65,6 +66,25 @@ __global__ void k_bounds(const int64_t* __restrict__ off, const double* __restri
       else atomicOr(gate, 1);
     }
     return;
+  }
+  // the spreading tiles' dispatch order: assets ranked by event count,
+  // heaviest first (ties by index), so that the longest tiles start first
+  if (order) {  // uniform: a single problem, D <= kOrderMaxAssets
+    __shared__ int s_cnt[kOrderMaxAssets];
+    for (int i = threadIdx.x; i < D; i += blockDim.x) {
+      const int64_t c = off[i + 1] - off[i];
+      s_cnt[i] = (int)min(c, (int64_t)0x7fffffff);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < D; i += blockDim.x) {
+      const int ci = s_cnt[i];
+      int r = 0;
+      for (int j = 0; j < D; ++j) {
+        const int cj = s_cnt[j];
+        r += (cj > ci || (cj == ci && j < i)) ? 1 : 0;
+      }
+      order[r] = i;
+    }
   }
   // 2) t_min / t_max from each asset's first and last event (Algorithm 4)
   const bool window = w1 > w0;
@@ -132,13 +152,15 @@ __global__ void k_bounds(const int64_t* __restrict__ off, const double* __restri
 }
 
 cudaError_t launch_bounds(const int64_t* off, const double* t, int D, int gsize, int64_t max_events, double w0,
-                          double w1, int64_t Mr, Rescale* rs, int* status, cudaStream_t s) {
+                          double w1, int64_t Mr, Rescale* rs, int* status, int* order, cudaStream_t s) {
   const int G = (D + gsize - 1) / gsize;
+  if (order && (G != 1 || D > kOrderMaxAssets)) return cudaErrorInvalidValue;
   if (G > 1) {
     cudaError_t e = cudaMemsetAsync(status + 1, 0, sizeof(int), s);  // the gate of this call
     if (e != cudaSuccess) return e;
   }
-  return launch_pdl(k_bounds, dim3(G), dim3(256), 0, s, off, t, D, gsize, max_events, w0, w1, Mr, rs, status);
+  return launch_pdl(k_bounds, dim3(G), dim3(256), 0, s, off, t, D, gsize, max_events, w0, w1, Mr, rs, status,
+                    order);
 }
 
 // Per-problem fixed-point cell scales for the grid size of this call.
@@ -661,7 +683,6 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_poly(const int64_t* _
   int* tile = reinterpret_cast<int*>(ev_v + EC);
   const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile);
   __shared__ float s_part[kSpreadThreads / 32];
-  const int a = blockIdx.y;
   const int64_t L = (int64_t)blockIdx.x * p.tile;
   const int Tlen = (int)min((int64_t)p.tile, p.Mr - L);
   {
@@ -671,6 +692,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_poly(const int64_t* _
   }
   pdl_wait();         // the records come from the prep kernel
   if (*gate) return;  // uniform: the whole block leaves
+  const int a = p.order ? p.order[blockIdx.y] : (int)blockIdx.y;
   TileRanges tr;
   tile_ranges(off, rb0, p, a, L, Tlen, tr);
   const int64_t ntot = tr.n2 + tr.n1 + tr.n0;
