@@ -455,7 +455,7 @@ cudaError_t launch_prep_f64(const int64_t* off, const double* t, const double* l
 }
 
 // ------------------------------------------------------------------ spread
-template <typename T> struct EvChunk { static constexpr int n = 2048; };
+template <typename T> struct EvChunk { static constexpr int n = 1536; };  // 6 spreading blocks per SM
 
 // Event ranges of a tile [L, L + Tlen): image m = r - 1 (r = 0, 1, 2) holds
 // the returns with b0 in [L - khi + m M_r, L + Tlen - klo + m M_r); taken in
