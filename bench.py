@@ -57,7 +57,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "c4", "c5"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "c4", "c5", "gram"])
+    ap.add_argument("--gram-d", type=int, default=500, help="gram: assets (the largest C5 request)")
+    ap.add_argument("--gram-n", type=int, default=14400, help="gram: cutoff (C5's N_max)")
     ap.add_argument("--reps", type=int, default=4096, help="c4: Monte Carlo replications per step")
     ap.add_argument("--cutoffs", type=int, default=64, help="c4: cutoffs of the Epps sweep")
     ap.add_argument("--requests", type=int, default=10000, help="c5: requests in the stream")
@@ -532,6 +534,115 @@ def bench_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_gram(args):
+    """The contraction alone (stage d: Sigma and R from coefficients) where it
+    is tensor-bound: D = 500 assets at N = 14400, the largest request of the
+    serving workload, on seeded synthetic coefficients."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_2003_02842_gb300 as mm
+    from paper_2003_02842_gb300 import synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    D, N = args.gram_d, args.gram_n
+    Fh = synth.gram_coefficients(0, D, N)
+    F = torch.from_numpy(Fh).to(dev)
+    plan = mm.mm_plan_create(D=D, N_max=N, max_events=0, tol=1e-6, kernel=args.kernel, basis="dirichlet",
+                             prec=args.prec)
+    S = torch.empty((D, D), dtype=torch.float32, device=dev)
+    R = torch.empty_like(S)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)  # inputs (57.6 MB) fit in L2
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        mm.mm_corr(plan, F, N, sigma=S, R=R)
+    assert mm.mm_plan_sync(plan) == 0
+    steps = max(1, min(args.steps, 200))
+    i0 = mm.mm_plan_get_info(plan)
+    ms = 0.0
+    with ClockSampler(dev.index) as clk:
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            mm.mm_corr(plan, F, N, sigma=S, R=R)
+            b.record()
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+    clocks = clk.summary()
+    i1 = mm.mm_plan_get_info(plan)
+    assert mm.mm_plan_sync(plan) == 0
+    # stage times (the contraction kernel and the correlation epilogue)
+    mm.mm_profile_read(plan, reset=True)
+    mm.mm_profile_enable(plan, True)
+    for _ in range(min(steps, 50)):
+        flush.zero_()
+        mm.mm_corr(plan, F, N, sigma=S, R=R)
+    torch.cuda.synchronize()
+    mm.mm_profile_enable(plan, False)
+    stages = mm.mm_profile_read(plan, reset=True)
+    gram_ms = stages["gram"][0] / max(stages["gram"][1], 1)
+    Rg = R.double().cpu().numpy()
+    mm.mm_destroy(plan)
+    # FP64 GPU path on the same coefficients
+    p64 = mm.mm_plan_create(D=D, N_max=N, max_events=0, tol=1e-12, kernel=args.kernel, basis="dirichlet",
+                            prec="fp64")
+    F64 = F.to(torch.complex128)
+    R64 = torch.empty((D, D), dtype=torch.float64, device=dev)
+    mm.mm_corr(p64, F64, N, sigma=None, R=R64)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    mm.mm_corr(p64, F64, N, sigma=None, R=R64)
+    e1.record()
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    dcorr = float(np.max(np.abs(R64.cpu().numpy() - Rg)))
+    mm.mm_destroy(p64)
+    # the oracle's contraction (c-convention over k = -N..N) on a sample of
+    # assets for about --cpu-budget seconds, scaled by (D / sample)^2
+    import oracle
+    ds, secs = 8, 0.0
+    while True:
+        c = np.zeros((ds, 2 * N + 1), dtype=np.complex128)
+        c[:, N:] = 2.0 * np.pi * Fh[:ds].astype(np.complex128)
+        c[:, :N] = np.conj(c[:, N + 1:][:, ::-1])
+        t0 = time.time()
+        oracle.cov_from_coeffs(c, N, "dirichlet")
+        secs = time.time() - t0
+        if secs >= 0.5 * args.cpu_budget or ds >= D:
+            break
+        ds = min(D, ds * 2)
+    cpu_rate = (ds / D) ** 2 / secs if secs > 0 else 0.0
+    peaks, src = load_peaks()
+    flops = 2.0 * D * D * 2.0 * (N + 1)  # the real product A A^T, A = D x 2(N + 1)
+    tiles = (D + 127) // 128
+    executed = 3.0 * (tiles * (tiles + 1) // 2) * 128 * 128 * 2.0 * (((N + 1 + 31) // 32) * 64)
+    achieved = flops / (gram_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": steps / (ms * 1e-3), "unit": "matrices/s", "n_gpus": 1, "steps": steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16" if args.prec == "bf16x3" else "tf32",
+        "data": "synthetic (seeded complex Gaussian coefficients at the scale of one day of GBM returns)",
+        "config": {"workload": f"gram_D{D}_N{N}", "D": D, "N": N, "contraction": args.prec, "basis": "dirichlet",
+                   "l2": "flushed between steps (256 MB write)", "gram_splits": i1["gram_splits"]},
+        "stage_ms": {"gram": gram_ms, "reduce": stages["reduce"][0] / max(stages["reduce"][1], 1)},
+        "roofline": {"kernel": "gram", "bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"],
+                     "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops"],
+                     "traffic": NCU_TRAFFIC.get(("gram", f"gram_D{D}_N{N}", args.prec, "es")),
+                     "peak_source": f"{src} bf16_tflops (burst)", "avg_launch_ms": gram_ms,
+                     "algorithmic_flops_per_launch": flops, "executed_tensor_flops_per_launch": executed},
+        "fp64_gpu_path": {"matrices_per_s": 1e3 / ms64, "max_abs_dcorr": dcorr},
+        "cpu_baseline": {"value": cpu_rate, "unit": "matrices/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"the oracle's contraction (Algorithm 3 step C) of {ds} of {D} assets at "
+                                   f"N={N} ({secs:.1f} s), scaled by (D/{ds})^2"},
+        "clocks": clocks,
+        "gpu_launches": int(i1["launches"] - i0["launches"]),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -543,6 +654,10 @@ def main():
     if args.workload == "c5":
         if int(os.environ.get("RANK", "0")) == 0:
             bench_serve(args)
+        return
+    if args.workload == "gram":
+        if int(os.environ.get("RANK", "0")) == 0:
+            bench_gram(args)
         return
     import torch
     import torch.distributed as dist

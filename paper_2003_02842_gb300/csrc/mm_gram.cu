@@ -163,7 +163,9 @@ __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
   return r;
 }
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;
+constexpr int kTcWarps = kTcThreads / 32;
+constexpr int kRowsPerWarp = 128 / kTcWarps;  // operand rows a warp converts
 constexpr int kTile = 128;                 // rows per operand tile
 constexpr int kTileBytes = kTile * 128;    // 128-byte rows
 constexpr uint32_t kTmemCols = 128;
@@ -181,11 +183,11 @@ __device__ __forceinline__ uint32_t sw128_off(int r, int cb) {
 // One K-chunk of the operand rows a thread owns, held in registers between
 // the global load and the conversion into shared memory, so that the loads
 // of chunk c+1 are in flight while chunk c is converted and multiplied.
-// MODE 0: 32 complex modes per chunk, one per lane, 32 rows per warp.
-// MODE 1: 16 complex modes per chunk, two rows per warp step, 32 rows per warp.
+// MODE 0: 32 complex modes per chunk, one per lane, kRowsPerWarp rows per warp.
+// MODE 1: 16 complex modes per chunk, two rows per warp step, kRowsPerWarp rows per warp.
 template <int MODE>
 struct Chunk {
-  static constexpr int R = MODE == 0 ? 32 : 16;
+  static constexpr int R = MODE == 0 ? kRowsPerWarp : kRowsPerWarp / 2;
   float2 v[R];
   float sc;
 };
@@ -201,7 +203,7 @@ __device__ __forceinline__ void load_chunk(const float2* __restrict__ F, const G
   c.sc = kin ? __ldg(wsq + k) : 0.0f;
 #pragma unroll
   for (int rr = 0; rr < Chunk<MODE>::R; ++rr) {
-    const int r = warp * 32 + (MODE == 0 ? rr : rr * 2 + half);
+    const int r = warp * kRowsPerWarp + (MODE == 0 ? rr : rr * 2 + half);
     const int row = row0 + r;
     c.v[rr] = (kin && row < g.D) ? __ldg(F + (int64_t)row * g.ld + k) : make_float2(0.f, 0.f);
   }
@@ -214,17 +216,12 @@ __device__ __forceinline__ void store_chunk(const Chunk<MODE>& c, uint8_t* hi, u
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (MODE == 0) {
 #pragma unroll
-    for (int rr = 0; rr < 32; ++rr) {
-      const int r = warp * 32 + rr;
+    for (int rr = 0; rr < kRowsPerWarp; ++rr) {
+      const int r = warp * kRowsPerWarp + rr;
       const float xr = c.v[rr].x * c.sc, xi = c.v[rr].y * c.sc;
-      const __nv_bfloat16 hr = __float2bfloat16_rn(xr), hi_ = __float2bfloat16_rn(xi);
-      const __nv_bfloat16 lr = __float2bfloat16_rn(xr - __bfloat162float(hr));
-      const __nv_bfloat16 li = __float2bfloat16_rn(xi - __bfloat162float(hi_));
-      __nv_bfloat162 H, L;
-      H.x = hr;
-      H.y = hi_;
-      L.x = lr;
-      L.y = li;
+      // (re, im) rounded as one packed pair, then the pair of residuals
+      const __nv_bfloat162 H = __floats2bfloat162_rn(xr, xi);
+      const __nv_bfloat162 L = __floats2bfloat162_rn(xr - __low2float(H), xi - __high2float(H));
       const uint32_t off = sw128_off(r, lane * 4);
       *reinterpret_cast<__nv_bfloat162*>(hi + off) = H;
       *reinterpret_cast<__nv_bfloat162*>(lo + off) = L;
@@ -232,8 +229,8 @@ __device__ __forceinline__ void store_chunk(const Chunk<MODE>& c, uint8_t* hi, u
   } else {
     const int half = lane >> 4, l = lane & 15;
 #pragma unroll
-    for (int rr = 0; rr < 16; ++rr) {
-      const int r = warp * 32 + rr * 2 + half;
+    for (int rr = 0; rr < kRowsPerWarp / 2; ++rr) {
+      const int r = warp * kRowsPerWarp + rr * 2 + half;
       const float xr = c.v[rr].x * c.sc, xi = c.v[rr].y * c.sc;
       const uint32_t hr = f32_to_tf32(xr), hi_ = f32_to_tf32(xi);
       const uint32_t lr = f32_to_tf32(xr - __uint_as_float(hr));
@@ -287,7 +284,7 @@ __device__ void corr_epilogue_block(const float* __restrict__ acc, const GramPar
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restrict__ F, GramParams g,
+__global__ void __launch_bounds__(kTcThreads, 2) k_gram_tc(const float2* __restrict__ F, GramParams g,
                                                            const float* __restrict__ wsq, float* __restrict__ acc,
                                                            int* status, int* done, float* sigma, float* Rout,
                                                            float* zero_next) {
@@ -386,13 +383,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restr
   tc_fence_after();
   __syncthreads();
 
+  // warp w reads TMEM lanes 32 (w mod 4) .. + 31 (its lane quadrant); the
+  // warps sharing a quadrant take alternate 16-column groups
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r = warp * 32 + lane;
+  const int quad = warp & 3;
+  const int r = quad * 32 + lane;
   if (!s_fail && nit > 0) {
     float* out = acc + (int64_t)(I * kTile + r) * g.Dp + J * kTile;
-    for (int c = 0; c < Nmma; c += 16) {
+    for (int c = 16 * (warp >> 2); c < Nmma; c += 16 * (kTcWarps / 4)) {
       uint32_t v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+      tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c, v);
       if (r < rowsI) {
 #pragma unroll
         for (int q = 0; q < 4; ++q)

@@ -311,6 +311,18 @@ def c4_batch(seed=0, reps=4096, D=10, T=28800, rho=0.35, sig2_range=(0.1, 0.2), 
     return ev
 
 
+def gram_coefficients(seed, D, N, day_var=0.1, T=28800):
+    """Synthetic Fourier coefficients for the contraction alone: D x (N + 1)
+    complex64, each mode complex Gaussian with the variance that one asset's
+    returns over T seconds of a GBM with daily variance day_var give every
+    mode, (day_var T / 86400) / (2 pi)^2 (returns summed against unit-modulus
+    phases), independent across assets and modes."""
+    rng = rng_for(10, seed, D, N)
+    sd = np.sqrt(day_var * T / SECONDS_PER_DAY / 2.0) / (2.0 * np.pi)  # per real and imaginary part
+    F = (rng.standard_normal((D, N + 1)) + 1j * rng.standard_normal((D, N + 1))) * sd
+    return F.astype(np.complex64)
+
+
 def c5_day(seed=0, D=500, T=28800, n_factors=3, load_sd=0.3, idio_var=0.1, mu=0.01, s0=100.0,
            lam_lo=0.01, lam_hi=1.0, shape=0.45):
     """Serving workload: one trading day of D assets on the 1-s grid. Arrival
