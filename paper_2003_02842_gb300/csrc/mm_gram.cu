@@ -163,7 +163,7 @@ __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
   return r;
 }
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;
 constexpr int kTcWarps = kTcThreads / 32;
 constexpr int kRowsPerWarp = 128 / kTcWarps;  // operand rows a warp converts
 constexpr int kTile = 128;                 // rows per operand tile
