@@ -37,10 +37,12 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # capture summarised in profiles/ (None until a capture of the current kernel)
 NCU_TRAFFIC = {
     # from the ncu capture of the block workload in its default configuration
-    ("spread", "c3", "bf16x3", "es"): 9224960,
+    ("spread", "c3", "bf16x3", "es"): 9225984,
     ("fft", "c3", "bf16x3", "es"): 16451584,
-    ("prep", "c3", "bf16x3", "es"): 12293120,
-    ("gram", "c3", "bf16x3", "es"): 8145152,
+    ("prep", "c3", "bf16x3", "es"): 12287488,
+    ("gram", "c3", "bf16x3", "es"): 8115712,
+    # the contraction alone at D = 500, N = 14400
+    ("gram", "gram_D500_N14400", "bf16x3", "es"): 59650560,
 }
 # the batched workload is too large for a full ncu capture: dram bytes per
 # grid row of its FFT from a capture of 256 replications (2560 rows of grid
