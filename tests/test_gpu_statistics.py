@@ -24,6 +24,13 @@ over the return pairs directly; the replication means of the GPU's Sigma lie
 within four standard errors of it at every cutoff, and the co-volatility
 shows the asynchrony bias growing with N that the paper reports.
 
+The same replications give the other curve of the accuracy figure, the MSE:
+the estimator is a Gaussian bilinear form in the step increments, so its
+variance has a closed form (2 tr(BVBV) + 4 mu^T BVB mu); the replication
+variance of every entry lies within four standard errors of it, and the
+replication MSE against the true integrated covariance within four standard
+errors of variance + bias^2.
+
 Third, the sensitivity test (App. B): synchronous bivariate GBMs of 10^4
 points over one day with integrated variances in 0.1-0.3 and covariances in
 -0.1-0.1; the estimates at the Nyquist cutoff lie on a line of slope 1
@@ -36,7 +43,7 @@ import oracle
 from paper_2003_02842_gb300 import synth
 
 from gpu_helpers import to_dev
-from stat_helpers import expected_sigma
+from stat_helpers import expected_sigma, sigma_moments, variance_se
 
 pytestmark = pytest.mark.gpu
 
@@ -135,6 +142,24 @@ def test_monte_carlo_mean_matches_the_estimators_expectation(accuracy_sweep, bas
             x = S[:, j, a, b]
             se = x.std(ddof=1) / np.sqrt(len(x))
             assert abs(x.mean() - E[a, b]) <= 4.0 * se, (basis, N, a, b, x.mean(), E[a, b], se)
+
+
+@pytest.mark.parametrize("basis", ["dirichlet", "fejer"])
+def test_monte_carlo_variance_and_mse_match_closed_form(accuracy_sweep, basis):
+    meta, out = accuracy_sweep
+    S = out[basis]
+    C = meta["step_cov"]
+    # the integrated (co)variance over the steps each pair of returns covers
+    truth = np.array([[(MB_N - 1) * C[0, 0], (MB_N - 2) * C[0, 1]], [(MB_N - 2) * C[1, 0], (MB_N - 2) * C[1, 1]]])
+    for j, N in enumerate(MB_CUTS):
+        E, Var = sigma_moments(meta, N, basis)
+        for a, b in [(0, 0), (1, 1), (0, 1)]:
+            x = S[:, j, a, b]
+            assert abs(x.var() - Var[a, b]) <= 4.0 * variance_se(x), (basis, N, a, b, x.var(), Var[a, b])
+            e2 = (x - truth[a, b]) ** 2
+            mse = Var[a, b] + (E[a, b] - truth[a, b]) ** 2
+            se = e2.std(ddof=1) / np.sqrt(len(e2))
+            assert abs(e2.mean() - mse) <= 4.0 * se, (basis, N, a, b, e2.mean(), mse, se)
 
 
 def test_covolatility_bias_grows_with_the_cutoff(accuracy_sweep):

@@ -5,14 +5,18 @@ E[Sigma_ab] = sum_{u,v} K_N(t_u - t_v) (Cov(d_u^a, d_v^b) + E d_u^a E d_v^b)
 for both bases (Eqs. (2), (3)) at small, middle and Nyquist cutoffs; and the
 closed form itself reproduces the paper's statements: no bias of the
 integrated volatility at any N (Dirichlet), a co-volatility bias that grows
-with N under asynchrony."""
+with N under asynchrony. The variance, for the MSE of the same experiment:
+the estimator is a Gaussian bilinear form in the step increments, whose mean
+(checked against the pair sum above) and variance are closed forms, and the
+oracle's Monte Carlo variance lies within four standard errors of the
+latter."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2003_02842_gb300 import synth
 
-from stat_helpers import expected_sigma
+from stat_helpers import expected_sigma, sigma_moments, variance_se
 
 REPS = 3000
 
@@ -52,3 +56,34 @@ def test_closed_form_volatility_unbiased_covolatility_epps():
         assert abs(E[0, 0] - 99 * C[0, 0]) <= 99 ** 2 * m[0] ** 2
     E = [expected_sigma(meta, N, "dirichlet")[0, 1] for N in (1, 10, 25, 50)]
     assert all(a > b for a, b in zip(E, E[1:]))
+
+
+@pytest.mark.parametrize("basis", ["dirichlet", "fejer"])
+@pytest.mark.parametrize("N", [1, 5, 50])
+def test_quadratic_form_mean_agrees_with_pair_sum(basis, N):
+    # two routes to E[Sigma]: the sum over return pairs and the trace of the
+    # bilinear form in the step increments
+    meta = synth.mse_bias_replications(0, 1).meta
+    E1 = expected_sigma(meta, N, basis)
+    E2, _ = sigma_moments(meta, N, basis)
+    assert np.allclose(E1, E2, rtol=1e-10, atol=1e-16)
+
+
+@pytest.mark.parametrize("basis", ["dirichlet", "fejer"])
+@pytest.mark.parametrize("N", [1, 5, 50])
+def test_oracle_variance_matches_closed_form(replications, basis, N):
+    meta, out = replications
+    v = out[(basis, N)]
+    _, Var = sigma_moments(meta, N, basis)
+    for a, b in [(0, 0), (1, 1), (0, 1)]:
+        x = v[:, a, b]
+        assert abs(x.var() - Var[a, b]) <= 4.0 * variance_se(x), (basis, N, a, b, x.var(), Var[a, b])
+
+
+def test_variance_closed_form_special_case():
+    # one step (n = 2), no drift: asset 1 has a single return d at time 0,
+    # the kernel there is K_N(0) = sum_k w_k = 1, so Sigma_11 = d^2 with d
+    # ~ N(0, C_11): mean C_11 and variance 2 C_11^2 (a centred Gaussian's square)
+    meta = {"n": 2, "step_cov": np.array([[0.3, 0.1], [0.1, 0.2]]), "step_mean": np.zeros(2)}
+    E, Var = sigma_moments(meta, 1, "dirichlet")
+    assert np.isclose(E[0, 0], 0.3) and np.isclose(Var[0, 0], 2 * 0.3 ** 2)
