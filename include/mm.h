@@ -399,6 +399,14 @@ mm_status mm_batch_get_info(mm_batch batch, mm_batch_info* info);
  * request_max_events events in the window, N_max) that fit in hbm_budget,
  * at least one and at most max_slots. Results are written to the caller's
  * host buffers; completions are polled, out of order, with host timestamps.
+ *
+ * Resident coefficients (cache_rows > 0): the coefficients of each requested
+ * asset over the request's window at its cutoff stay on the device (rows of
+ * N_max + 1, least recently used evicted first), and a later request with
+ * the same window and cutoff computes only its other assets. Requests whose
+ * cutoff is the window's Nyquist cutoff (known only on the device) are not
+ * cached; neither are rows of a request that failed. mm_server_load empties
+ * the cache.
  * ------------------------------------------------------------------------ */
 typedef struct {
   int32_t D;                   /* assets in the resident store, 1 .. 4096 */
@@ -407,7 +415,8 @@ typedef struct {
   int64_t request_max_events;  /* events a request's window may hold (0 = max_events) */
   int64_t hbm_budget;          /* bytes for the slots' workspace (0 = max_slots slots) */
   int32_t max_slots;           /* 1 .. 64 */
-  int32_t reserved0;           /* must be zero */
+  int32_t cache_rows;          /* >= 0: coefficient rows kept resident across requests, each
+                                  N_max + 1 coefficients of one (asset, window, cutoff); 0 = none */
   double tol;
   mm_kernel kernel;
   mm_basis basis;
@@ -441,6 +450,8 @@ typedef struct {
   int32_t slots, inflight, peak_inflight, queued;
   int64_t launches;            /* kernels launched for requests since creation (the window
                                   gather and the slot plans' own, graph replays included) */
+  int64_t cache_hits;          /* requested assets served from resident coefficient rows */
+  int64_t cache_misses;        /* requested assets whose coefficients were computed (cached requests) */
 } mm_server_stats;
 
 typedef struct mm_server_s* mm_server;

@@ -460,10 +460,13 @@ class Server:
 
 
 def mm_server_create(D, N_max, max_events, request_max_events=0, hbm_budget=0, max_slots=4, tol=1e-6,
-                     kernel="es", basis="fejer", prec="bf16x3") -> Server:
+                     kernel="es", basis="fejer", prec="bf16x3", cache_rows=0) -> Server:
+    """cache_rows > 0 keeps that many coefficient rows (one asset over one
+    window at one cutoff each) resident across requests."""
     d = _lib.ServerDesc()
     d.D, d.N_max, d.max_events, d.request_max_events = int(D), int(N_max), int(max_events), int(request_max_events)
     d.hbm_budget, d.max_slots, d.tol = int(hbm_budget), int(max_slots), float(tol)
+    d.cache_rows = int(cache_rows)
     d.kernel, d.basis, d.prec = KERNELS[kernel], BASES[basis], PRECISIONS[prec]
     h = ctypes.c_void_p()
     _check(_lib.load().mm_server_create(ctypes.byref(d), ctypes.byref(h)), "mm_server_create")

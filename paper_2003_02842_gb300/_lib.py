@@ -106,7 +106,7 @@ class ServerDesc(ctypes.Structure):
         ("request_max_events", ctypes.c_int64),
         ("hbm_budget", ctypes.c_int64),
         ("max_slots", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("cache_rows", ctypes.c_int32),
         ("tol", ctypes.c_double),
         ("kernel", ctypes.c_int),
         ("basis", ctypes.c_int),
@@ -152,6 +152,8 @@ class ServerStats(ctypes.Structure):
         ("peak_inflight", ctypes.c_int32),
         ("queued", ctypes.c_int32),
         ("launches", ctypes.c_int64),
+        ("cache_hits", ctypes.c_int64),
+        ("cache_misses", ctypes.c_int64),
     ]
 
 

@@ -14,6 +14,15 @@
 // Requests complete out of order; the caller polls completions with their
 // submit / start / finish times (host clock), from which p50 / p99 latency
 // follow.
+//
+// Resident coefficients: with a cache, each requested asset's coefficients
+// over the request's window at its cutoff are kept in a device row keyed by
+// (asset, t0, t1, N); a request computes only the assets it does not find,
+// writes them into fresh rows, and gathers all its rows for the contraction.
+// New rows become visible to other requests when their request has finished
+// (so no slot reads a row another slot is still writing); rows in use are
+// pinned; unpinned rows are evicted least recently used first. The index is
+// touched only by the scheduler thread.
 #include <atomic>
 #include <math.h>
 #include <string.h>
@@ -22,8 +31,10 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <list>
 #include <mutex>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "mm_common.cuh"
@@ -96,6 +107,57 @@ __global__ void k_window_copy(const int64_t* __restrict__ lo, const int64_t* __r
   }
 }
 
+// Coefficient rows between a dense [n][ld] matrix and the cache's rows
+// (8-byte units: complex64 or complex128 coefficients). Block i: row i.
+__global__ void k_rows_to_cache(const unsigned long long* __restrict__ src, int64_t src_ld,
+                                unsigned long long* __restrict__ cache, int64_t cache_ld,
+                                const int32_t* __restrict__ rows, int64_t width) {
+  const int i = blockIdx.x;
+  const unsigned long long* a = src + (int64_t)i * src_ld;
+  unsigned long long* b = cache + (int64_t)rows[i] * cache_ld;
+  for (int64_t j = threadIdx.x; j < width; j += blockDim.x) b[j] = a[j];
+}
+
+__global__ void k_rows_from_cache(const unsigned long long* __restrict__ cache, int64_t cache_ld,
+                                  const int32_t* __restrict__ rows, unsigned long long* __restrict__ dst,
+                                  int64_t dst_ld, int64_t width) {
+  const int i = blockIdx.x;
+  const unsigned long long* a = cache + (int64_t)rows[i] * cache_ld;
+  unsigned long long* b = dst + (int64_t)i * dst_ld;
+  for (int64_t j = threadIdx.x; j < width; j += blockDim.x) b[j] = a[j];
+}
+
+struct CacheKey {
+  int asset = 0;
+  int N = 0;
+  double t0 = 0, t1 = 0;
+  bool operator==(const CacheKey& o) const {
+    return asset == o.asset && N == o.N && memcmp(&t0, &o.t0, sizeof(double)) == 0 &&
+           memcmp(&t1, &o.t1, sizeof(double)) == 0;
+  }
+};
+
+struct CacheKeyHash {
+  size_t operator()(const CacheKey& k) const {
+    uint64_t a, b;
+    memcpy(&a, &k.t0, 8);
+    memcpy(&b, &k.t1, 8);
+    uint64_t h = (uint64_t)(uint32_t)k.asset * 0x9E3779B97F4A7C15ull;
+    h ^= (uint64_t)(uint32_t)k.N + 0x632BE59BD9B4E019ull + (h << 6) + (h >> 2);
+    h ^= a + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+    h ^= b + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+    return (size_t)h;
+  }
+};
+
+struct CacheRow {
+  CacheKey key;
+  int pins = 0;          // requests in flight that read or write this row
+  bool indexed = false;  // visible to lookups
+  bool in_lru = false;   // unpinned and indexed: evictable
+  std::list<int>::iterator lru;
+};
+
 double now_s() {
   using namespace std::chrono;
   return duration<double>(steady_clock::now().time_since_epoch()).count();
@@ -127,6 +189,10 @@ struct Slot {
   void* h_S = nullptr;          // pinned
   void* h_R = nullptr;          // pinned
   int* h_status = nullptr;      // pinned
+  int32_t* d_rows = nullptr;    // cache rows of the request's computed assets, then of all its assets
+  int32_t* h_rows = nullptr;    // pinned staging of d_rows
+  std::vector<int> pinned;      // cache rows this request reads (found in the index)
+  std::vector<int> reserved;    // cache rows this request writes (published when it finishes)
   bool busy = false;
   mm_status early = MM_OK;      // error found while enqueueing
   int N_used = 0;
@@ -157,16 +223,93 @@ struct mm_server_s {
   std::atomic<int64_t> launches{0};  // kernels launched for requests (start() runs outside mu)
   int inflight = 0, peak_inflight = 0;
   double t_origin = 0;
+  // resident coefficients (scheduler thread only, or under mu while idle)
+  void* d_cache = nullptr;  // cache_rows x (N_max + 1) coefficients
+  std::vector<CacheRow> rows;
+  std::unordered_map<CacheKey, int, CacheKeyHash> index;
+  std::list<int> lru;  // evictable rows, most recently used first
+  std::vector<int> free_rows;
+  std::atomic<int64_t> cache_hits{0}, cache_misses{0};
 };
 
 namespace {
 
+void cache_clear(mm_server s) {
+  s->index.clear();
+  s->lru.clear();
+  s->free_rows.clear();
+  for (int r = (int)s->rows.size() - 1; r >= 0; --r) {
+    s->rows[r] = CacheRow{};
+    s->free_rows.push_back(r);
+  }
+}
+
+void cache_pin(mm_server s, int r) {
+  CacheRow& c = s->rows[r];
+  if (c.in_lru) {
+    s->lru.erase(c.lru);
+    c.in_lru = false;
+  }
+  c.pins += 1;
+}
+
+void cache_unpin(mm_server s, int r) {
+  CacheRow& c = s->rows[r];
+  c.pins -= 1;
+  if (c.pins == 0 && c.indexed) {
+    s->lru.push_front(r);
+    c.lru = s->lru.begin();
+    c.in_lru = true;
+  }
+}
+
+// A row to write: a free one, else the least recently used unpinned one
+// (dropped from the index); -1 when every row is in use.
+int cache_take(mm_server s) {
+  if (!s->free_rows.empty()) {
+    const int r = s->free_rows.back();
+    s->free_rows.pop_back();
+    return r;
+  }
+  if (s->lru.empty()) return -1;
+  const int r = s->lru.back();
+  s->lru.pop_back();
+  CacheRow& c = s->rows[r];
+  s->index.erase(c.key);
+  c = CacheRow{};
+  return r;
+}
+
+void cache_free(mm_server s, int r) {
+  s->rows[r] = CacheRow{};
+  s->free_rows.push_back(r);
+}
+
+// A finished request's rows: the ones it read are unpinned; the ones it
+// wrote are published (unless the request failed, or the same key was
+// published meanwhile) or returned.
+void cache_release(mm_server s, Slot& sl, bool ok) {
+  for (int r : sl.pinned) cache_unpin(s, r);
+  for (int r : sl.reserved) {
+    CacheRow& c = s->rows[r];
+    if (ok && s->index.find(c.key) == s->index.end()) {
+      s->index.emplace(c.key, r);
+      c.indexed = true;
+      cache_unpin(s, r);
+    } else {
+      cache_free(s, r);
+    }
+  }
+  sl.pinned.clear();
+  sl.reserved.clear();
+}
+
 void free_slot(Slot& s) {
   if (s.p) mm_destroy(s.p);
-  void* dptrs[] = {s.d_assets, s.d_lo, s.d_off, s.d_t, s.d_p, s.d_coef, s.d_S, s.d_R};
+  void* dptrs[] = {s.d_assets, s.d_lo, s.d_off, s.d_t, s.d_p, s.d_coef, s.d_S, s.d_R, s.d_rows};
   for (void* q : dptrs)
     if (q) cudaFree(q);
-  void* hptrs[] = {s.h_assets, s.h_S, s.h_R, s.h_status};
+  void* hptrs[] = {s.h_assets, s.h_S, s.h_R, s.h_status, s.h_rows};
   for (void* q : hptrs)
     if (q) cudaFreeHost(q);
   if (s.done) cudaEventDestroy(s.done);
@@ -198,8 +341,10 @@ mm_status make_slot(mm_server s, Slot& sl, int64_t* bytes) {
   };
   bool ok = A((void**)&sl.d_assets, D * 4) && A((void**)&sl.d_lo, D * 8) && A((void**)&sl.d_off, (D + 1) * 8) &&
             A((void**)&sl.d_t, E * 8) && A((void**)&sl.d_p, E * 8) &&
-            A(&sl.d_coef, D * ((size_t)d.N_max + 1) * cs) && A(&sl.d_S, D * D * s->rs) && A(&sl.d_R, D * D * s->rs);
-  ok = ok && cudaMallocHost((void**)&sl.h_assets, D * 4) == cudaSuccess &&
+            A(&sl.d_coef, D * ((size_t)d.N_max + 1) * cs) && A(&sl.d_S, D * D * s->rs) && A(&sl.d_R, D * D * s->rs) &&
+            A((void**)&sl.d_rows, 2 * D * 4);
+  ok = ok && cudaMallocHost((void**)&sl.h_rows, 2 * D * 4) == cudaSuccess &&
+       cudaMallocHost((void**)&sl.h_assets, D * 4) == cudaSuccess &&
        cudaMallocHost(&sl.h_S, D * D * s->rs) == cudaSuccess && cudaMallocHost(&sl.h_R, D * D * s->rs) == cudaSuccess &&
        cudaMallocHost((void**)&sl.h_status, 16) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) == cudaSuccess &&
@@ -220,26 +365,14 @@ void start(mm_server s, Slot& sl, Req&& rq) {
   sl.busy = true;
   sl.early = MM_OK;
   sl.N_used = 0;
+  sl.pinned.clear();
+  sl.reserved.clear();
   const int n = (int)sl.req.assets.size();
   cudaStream_t st = sl.st;
   auto fail = [&](mm_status r) {
     sl.early = r;
     cudaEventRecord(sl.done, st);
   };
-  memcpy(sl.h_assets, sl.req.assets.data(), (size_t)n * 4);
-  mm_plan_info pi0{};
-  mm_plan_get_info(sl.p, &pi0);
-  int* status = plan_status_word(sl.p);
-  if (cudaMemcpyAsync(sl.d_assets, sl.h_assets, (size_t)n * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess)
-    return fail(MM_ERR_CUDA);
-  k_window_offsets<<<1, 512, (size_t)n * 8, st>>>(s->d_off_all, s->d_t_all, s->desc.D, sl.d_assets, n, sl.req.t0,
-                                                  sl.req.t1, s->req_events, sl.d_lo, sl.d_off, status);
-  k_window_copy<<<n, 256, 0, st>>>(sl.d_lo, sl.d_off, s->d_t_all, s->d_p_all, sl.d_t, sl.d_p);
-  if (cudaGetLastError() != cudaSuccess) return fail(MM_ERR_CUDA);
-  s->launches.fetch_add(2);
-  mm_status r = plan_set_active_assets(sl.p, n);
-  if (r != MM_OK) return fail(r);
   int N = sl.req.N;
   if (N <= 0 && sl.req.dt > 0.0) {
     // Eq. (19) for the sampling interval dt over the window length
@@ -247,13 +380,99 @@ void start(mm_server s, Slot& sl, Req&& rq) {
     if (N < 1) N = 1;
   }
   if (N > s->desc.N_max) N = s->desc.N_max;
-  int32_t Nu = 0;
-  r = mm_coeffs(sl.p, sl.d_off, sl.d_t, sl.d_p, N, sl.req.t0, sl.req.t1, sl.d_coef, &Nu, st);
-  if (r == MM_ERR_CUTOFF && N <= 0) {
-    // a window Nyquist cutoff above N_max: serve it at N_max
-    r = mm_coeffs(sl.p, sl.d_off, sl.d_t, sl.d_p, s->desc.N_max, sl.req.t0, sl.req.t1, sl.d_coef, &Nu, st);
+
+  // resident coefficients: with the cutoff known on the host, the assets
+  // found in the cache are read from their rows and only the others are
+  // computed (into rows reserved for them)
+  bool cached = !s->rows.empty() && N > 0;
+  std::vector<int> compute;  // positions in the request of the assets computed here
+  std::vector<int> row_of;
+  if (cached) {
+    row_of.assign(n, -1);
+    for (int i = 0; i < n; ++i) {
+      CacheKey k;
+      k.asset = sl.req.assets[i];
+      k.N = N;
+      k.t0 = sl.req.t0;
+      k.t1 = sl.req.t1;
+      const auto it = s->index.find(k);
+      if (it != s->index.end()) {
+        cache_pin(s, it->second);
+        sl.pinned.push_back(it->second);
+        row_of[i] = it->second;
+      } else {
+        compute.push_back(i);
+      }
+    }
+    for (int i : compute) {
+      const int r = cache_take(s);
+      if (r < 0) {  // every row in use: serve this request without the cache
+        cache_release(s, sl, false);
+        cached = false;
+        break;
+      }
+      CacheRow& c = s->rows[r];
+      c.key.asset = sl.req.assets[i];
+      c.key.N = N;
+      c.key.t0 = sl.req.t0;
+      c.key.t1 = sl.req.t1;
+      c.pins = 1;
+      sl.reserved.push_back(r);
+      row_of[i] = r;
+    }
   }
-  if (r != MM_OK) return fail(r);
+  if (!cached) {
+    compute.resize(n);
+    for (int i = 0; i < n; ++i) compute[i] = i;
+  }
+  const int nc = (int)compute.size();
+  for (int j = 0; j < nc; ++j) sl.h_assets[j] = sl.req.assets[compute[j]];
+
+  mm_plan_info pi0{};
+  mm_plan_get_info(sl.p, &pi0);
+  int* status = plan_status_word(sl.p);
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return fail(MM_ERR_CUDA);
+  int32_t Nu = N;
+  mm_status r = MM_OK;
+  if (nc > 0) {
+    if (cudaMemcpyAsync(sl.d_assets, sl.h_assets, (size_t)nc * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return fail(MM_ERR_CUDA);
+    k_window_offsets<<<1, 512, (size_t)nc * 8, st>>>(s->d_off_all, s->d_t_all, s->desc.D, sl.d_assets, nc,
+                                                     sl.req.t0, sl.req.t1, s->req_events, sl.d_lo, sl.d_off, status);
+    k_window_copy<<<nc, 256, 0, st>>>(sl.d_lo, sl.d_off, s->d_t_all, s->d_p_all, sl.d_t, sl.d_p);
+    if (cudaGetLastError() != cudaSuccess) return fail(MM_ERR_CUDA);
+    s->launches.fetch_add(2);
+    r = plan_set_active_assets(sl.p, nc);
+    if (r != MM_OK) return fail(r);
+    r = mm_coeffs(sl.p, sl.d_off, sl.d_t, sl.d_p, N, sl.req.t0, sl.req.t1, sl.d_coef, &Nu, st);
+    if (r == MM_ERR_CUTOFF && N <= 0) {
+      // a window Nyquist cutoff above N_max: serve it at N_max
+      r = mm_coeffs(sl.p, sl.d_off, sl.d_t, sl.d_p, s->desc.N_max, sl.req.t0, sl.req.t1, sl.d_coef, &Nu, st);
+    }
+    if (r != MM_OK) return fail(r);
+  }
+  if (cached) {
+    // computed rows into their cache rows, then every requested row (in
+    // request order) into the contraction's operand
+    const int D = s->desc.D;
+    for (int j = 0; j < nc; ++j) sl.h_rows[j] = row_of[compute[j]];
+    for (int i = 0; i < n; ++i) sl.h_rows[D + i] = row_of[i];
+    const int64_t u = (int64_t)(2 * s->rs) / 8;  // 8-byte units per coefficient
+    const int64_t width = (int64_t)(N + 1) * u, cld = (int64_t)(s->desc.N_max + 1) * u;
+    if (cudaMemcpyAsync(sl.d_rows, sl.h_rows, (size_t)2 * D * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return fail(MM_ERR_CUDA);
+    if (nc > 0)
+      k_rows_to_cache<<<nc, 256, 0, st>>>((const unsigned long long*)sl.d_coef, width,
+                                          (unsigned long long*)s->d_cache, cld, sl.d_rows, width);
+    k_rows_from_cache<<<n, 256, 0, st>>>((const unsigned long long*)s->d_cache, cld, sl.d_rows + D,
+                                         (unsigned long long*)sl.d_coef, width, width);
+    if (cudaGetLastError() != cudaSuccess) return fail(MM_ERR_CUDA);
+    s->launches.fetch_add(nc > 0 ? 2 : 1);
+    s->cache_hits.fetch_add(n - nc);
+    s->cache_misses.fetch_add(nc);
+    r = plan_set_active_assets(sl.p, n);
+    if (r != MM_OK) return fail(r);
+  }
   sl.N_used = Nu;
   r = mm_corr(sl.p, sl.d_coef, Nu, sl.req.h_S ? sl.d_S : nullptr, sl.d_R, st);
   if (r != MM_OK) return fail(r);
@@ -284,6 +503,8 @@ mm_completion finish(mm_server s, Slot& sl) {
     if (sl.req.h_R) memcpy(sl.req.h_R, sl.h_R, bytes);
     if (sl.req.h_S) memcpy(sl.req.h_S, sl.h_S, bytes);
   }
+  // zero variance concerns R only: the request's coefficients are valid
+  cache_release(s, sl, c.status == MM_OK || c.status == MM_ERR_ZERO_VARIANCE);
   sl.busy = false;
   return c;
 }
@@ -339,7 +560,7 @@ mm_status mm_server_create(const mm_server_desc* desc, mm_server* out) {
   if (!desc) return MM_ERR_INVALID_ARG;
   const mm_server_desc& d = *desc;
   if (d.D < 1 || d.D > 4096 || d.N_max < 1 || d.max_events < 1 || d.request_max_events < 0 ||
-      d.hbm_budget < 0 || d.max_slots < 1 || d.max_slots > 64 || d.reserved0 != 0)
+      d.hbm_budget < 0 || d.max_slots < 1 || d.max_slots > 64 || d.cache_rows < 0 || d.cache_rows > (1 << 22))
     return MM_ERR_INVALID_ARG;
   for (int i = 0; i < 4; ++i)
     if (d.reserved[i] != 0) return MM_ERR_INVALID_ARG;
@@ -357,6 +578,19 @@ mm_status mm_server_create(const mm_server_desc* desc, mm_server* out) {
     cudaFree(s->d_t_all);
     delete s;
     return MM_ERR_OOM;
+  }
+  if (d.cache_rows > 0) {
+    const size_t cs = 2 * s->rs;
+    if (cudaMalloc(&s->d_cache, (size_t)d.cache_rows * ((size_t)d.N_max + 1) * cs) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(s->d_off_all);
+      cudaFree(s->d_t_all);
+      cudaFree(s->d_p_all);
+      delete s;
+      return MM_ERR_OOM;
+    }
+    s->rows.resize(d.cache_rows);
+    cache_clear(s);
   }
   // slots: as many as the budget holds (at least one), each sized for the
   // largest admissible request
@@ -377,6 +611,7 @@ mm_status mm_server_create(const mm_server_desc* desc, mm_server* out) {
     cudaFree(s->d_off_all);
     cudaFree(s->d_t_all);
     cudaFree(s->d_p_all);
+    cudaFree(s->d_cache);
     delete s;
     return r != MM_OK ? r : MM_ERR_OOM;
   }
@@ -401,6 +636,7 @@ mm_status mm_server_load(mm_server s, const int64_t* h_offsets, const double* h_
       cudaMemcpy(s->d_t_all, h_t, E * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(s->d_p_all, h_logp, E * 8, cudaMemcpyHostToDevice) != cudaSuccess)
     return MM_ERR_CUDA;
+  cache_clear(s);  // the rows were of the previous store
   s->loaded = true;
   return MM_OK;
 }
@@ -458,6 +694,8 @@ mm_status mm_server_get_stats(mm_server s, mm_server_stats* st) {
   st->slot_bytes = s->slot_bytes;
   st->resident_bytes = (int64_t)(s->desc.D + 1) * 8 + 16 * s->desc.max_events;
   st->launches = s->launches.load();
+  st->cache_hits = s->cache_hits.load();
+  st->cache_misses = s->cache_misses.load();
   return MM_OK;
 }
 
@@ -474,6 +712,7 @@ mm_status mm_server_destroy(mm_server s) {
   cudaFree(s->d_off_all);
   cudaFree(s->d_t_all);
   cudaFree(s->d_p_all);
+  cudaFree(s->d_cache);
   delete s;
   return MM_OK;
 }

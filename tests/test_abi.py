@@ -95,7 +95,7 @@ def test_bad_batch_desc_rejected_on_host(lib, field, value, code):
 
 
 @pytest.mark.parametrize("field,value", [
-    ("D", 0), ("D", 5000), ("N_max", 0), ("max_events", 0), ("max_slots", 0), ("max_slots", 65), ("reserved0", 2),
+    ("D", 0), ("D", 5000), ("N_max", 0), ("max_events", 0), ("max_slots", 0), ("max_slots", 65), ("cache_rows", -1),
 ])
 def test_bad_server_desc_rejected_on_host(lib, field, value):
     from paper_2003_02842_gb300 import _lib

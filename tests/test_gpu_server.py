@@ -3,7 +3,9 @@
 window events with the window rescaling of Algorithm 4 over [t0, t1]; a
 request gives the same result alone and in a mix of concurrent requests;
 the scheduler runs several requests at once and reports failures per
-request. Tolerances: R, max |dR| <= 1e-4; Sigma, max |dSigma_ij| /
+request; resident coefficient rows serve later requests over the same
+window and cutoff (hits and misses counted exactly, eviction, no caching of
+device-found Nyquist cutoffs, concurrent requests). Tolerances: R, max |dR| <= 1e-4; Sigma, max |dSigma_ij| /
 sqrt(V_i V_j) <= 1e-4 with V the realised variances of the window."""
 import numpy as np
 import pytest
@@ -121,4 +123,61 @@ def test_budget_sets_slots_and_bad_requests_fail_alone(day):
     _check(day, good, done[t_good])
     with pytest.raises(mm.MMError):
         mm.mm_server_submit(srv, 5.0, 1.0, good["assets"])  # empty window
+    mm.mm_server_destroy(srv)
+
+
+def test_resident_coefficients_serve_repeated_windows(day):
+    import paper_2003_02842_gb300 as mm
+    srv = _server(day, cache_rows=16)
+
+    def run(req, N):
+        t = mm.mm_server_submit(srv, req["t0"], req["t1"], req["assets"], N=N, sigma=True)
+        return _wait(srv, 1)[t]
+
+    def counts():
+        st = mm.mm_server_get_stats(srv)
+        return st["cache_hits"], st["cache_misses"]
+
+    a = {"t0": 200.0, "t1": 2800.0, "assets": np.array([1, 2, 3, 4, 5, 6], np.int32)}
+    b = {"t0": 200.0, "t1": 2800.0, "assets": np.array([4, 5, 6, 7, 8, 9], np.int32)}
+    da = run(a, 120)
+    assert counts() == (0, 6)
+    db = run(b, 120)  # assets 4, 5, 6 over the same window at the same cutoff are resident
+    assert counts() == (3, 9)
+    _check(day, a, da)
+    _check(day, b, db)
+    da2 = run(a, 120)  # every row resident
+    assert counts() == (9, 9)
+    assert np.max(np.abs(da2["R"] - da["R"])) <= 1e-6
+    dc = run(a, 60)  # another cutoff: other rows
+    assert counts() == (9, 15)
+    _check(day, a, dc)
+    # more (asset, window) rows than the cache holds: older rows are evicted
+    for k in range(4):
+        w = {"t0": 100.0 + 50.0 * k, "t1": 2900.0, "assets": np.arange(6, dtype=np.int32)}
+        _check(day, w, run(w, 90))
+    assert counts() == (9, 39)
+    # the window's Nyquist cutoff is found on the device: not cached
+    dn = run(a, 0)
+    assert counts() == (9, 39)
+    _check(day, a, dn)
+    mm.mm_server_destroy(srv)
+
+
+def test_resident_coefficients_under_concurrent_requests(day):
+    # overlapping windows and subsets in flight together: rows written by one
+    # request become visible only once it has finished, so every result
+    # matches the oracle
+    import paper_2003_02842_gb300 as mm
+    srv = _server(day, cache_rows=48, max_slots=4)
+    base = synth.c5_requests(11, n=12, D=day.D, T=3000, w_range=(600, 2400), k_range=(3, 10))
+    reqs = []
+    for r in base:
+        reqs.append({"t0": 300.0, "t1": 2700.0, "assets": r["assets"]})  # one shared window
+    tks = [mm.mm_server_submit(srv, r["t0"], r["t1"], r["assets"], N=75, sigma=True) for r in reqs * 2]
+    done = _wait(srv, len(tks))
+    st = mm.mm_server_get_stats(srv)
+    assert st["cache_hits"] > 0 and st["cache_hits"] + st["cache_misses"] == sum(len(r["assets"]) for r in reqs * 2)
+    for t, r in zip(tks, reqs * 2):
+        _check(day, r, done[t])
     mm.mm_server_destroy(srv)
