@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--requests", type=int, default=10000, help="c5: requests in the stream")
     ap.add_argument("--slots", type=int, default=8, help="c5: execution slots at most")
     ap.add_argument("--hbm-budget-gb", type=float, default=16.0, help="c5: HBM budget for the slots")
+    ap.add_argument("--cache-rows", type=int, default=0, help="c5: resident coefficient rows (0: none)")
+    ap.add_argument("--windows", type=int, default=0,
+                    help="c5: requests share this many standing windows (0: every window random)")
     ap.add_argument("--load", type=float, default=0.7, help="c5: offered load of the latency phase, "
                                                             "as a fraction of the measured throughput")
     ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "3xtf32", "fp64"])
@@ -459,10 +462,11 @@ def bench_serve(args):
     from paper_2003_02842_gb300 import synth
 
     ev = synth.c5_day(seed=rank)
-    reqs = synth.c5_requests(seed=rank, n=args.requests, D=ev.D)
+    reqs = synth.c5_requests(seed=rank, n=args.requests, D=ev.D, windows=args.windows)
     Nmax = 14400
     srv = mm.mm_server_create(D=ev.D, N_max=Nmax, max_events=ev.n_events, hbm_budget=int(args.hbm_budget_gb * 2**30),
-                              max_slots=args.slots, tol=1e-6, kernel="es", basis="fejer", prec=args.prec)
+                              max_slots=args.slots, tol=1e-6, kernel="es", basis="fejer", prec=args.prec,
+                              cache_rows=args.cache_rows)
     mm.mm_server_load(srv, ev.offsets, ev.t, ev.logp)
     counts = np.diff(ev.offsets)
 
@@ -521,6 +525,7 @@ def bench_serve(args):
         "config": {"workload": ev.meta["workload"], "D": ev.D, "events": ev.n_events, "requests": len(reqs),
                    "N_max": Nmax, "kernel": "es", "tol": 1e-6, "basis": "fejer", "contraction": args.prec,
                    "slots": stats["slots"], "slot_bytes": stats["slot_bytes"], "hbm_budget_gb": args.hbm_budget_gb,
+                   "cache_rows": args.cache_rows, "windows": args.windows or "random",
                    "l2": "window events of a request exceed L2 on average (no flush)"},
         "requests_per_s": thr,
         "matrices_per_s": thr,
@@ -530,6 +535,7 @@ def bench_serve(args):
                        "p99": float(np.percentile(lat, 99)), "service_p50": float(np.percentile(svc, 50)),
                        "service_p99": float(np.percentile(svc, 99))},
         "peak_inflight": stats["peak_inflight"],
+        "cache": {"hits": stats["cache_hits"], "misses": stats["cache_misses"]},
         "clocks": clocks,
         "gpu_launches": int(launches),
     }

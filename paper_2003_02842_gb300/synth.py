@@ -356,16 +356,27 @@ def c5_day(seed=0, D=500, T=28800, n_factors=3, load_sd=0.3, idio_var=0.1, mu=0.
 
 
 def c5_requests(seed=0, n=10000, D=500, T=28800, w_range=(300, 28800), k_range=(10, 500),
-                dt_modes=(0.0, 60.0, 600.0)):
+                dt_modes=(0.0, 60.0, 600.0), windows=0):
     """Request stream of the serving workload: window length ~ U(w_range)
     seconds at a uniform start, asset subset of size ~ U{k_range} drawn
     without replacement, cutoff mode uniform over dt_modes (0: the window's
-    Nyquist cutoff, else Eq. (19) at that sampling interval)."""
+    Nyquist cutoff, else Eq. (19) at that sampling interval). windows > 0:
+    that many such windows are drawn first and every request takes one of
+    them uniformly (clients polling a few standing windows)."""
     rng = rng_for(6, seed)
-    out = []
-    for _ in range(n):
+    pool = []
+    for _ in range(windows):
         W = float(rng.uniform(*w_range))
         t0 = float(rng.uniform(0.0, T - W))
+        pool.append((t0, t0 + W))
+    out = []
+    for _ in range(n):
+        if pool:
+            t0, t1 = pool[int(rng.integers(len(pool)))]
+            W = t1 - t0
+        else:
+            W = float(rng.uniform(*w_range))
+            t0 = float(rng.uniform(0.0, T - W))
         k = int(rng.integers(k_range[0], min(k_range[1], D) + 1))
         assets = np.sort(rng.choice(D, size=k, replace=False)).astype(np.int32)
         dtm = float(dt_modes[int(rng.integers(len(dt_modes)))])
