@@ -31,13 +31,12 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
-#include <list>
 #include <mutex>
 #include <thread>
-#include <unordered_map>
 #include <vector>
 
 #include "mm_common.cuh"
+#include "server_cache.h"
 
 using namespace mmgpu;
 
@@ -127,37 +126,6 @@ __global__ void k_rows_from_cache(const unsigned long long* __restrict__ cache, 
   for (int64_t j = threadIdx.x; j < width; j += blockDim.x) b[j] = a[j];
 }
 
-struct CacheKey {
-  int asset = 0;
-  int N = 0;
-  double t0 = 0, t1 = 0;
-  bool operator==(const CacheKey& o) const {
-    return asset == o.asset && N == o.N && memcmp(&t0, &o.t0, sizeof(double)) == 0 &&
-           memcmp(&t1, &o.t1, sizeof(double)) == 0;
-  }
-};
-
-struct CacheKeyHash {
-  size_t operator()(const CacheKey& k) const {
-    uint64_t a, b;
-    memcpy(&a, &k.t0, 8);
-    memcpy(&b, &k.t1, 8);
-    uint64_t h = (uint64_t)(uint32_t)k.asset * 0x9E3779B97F4A7C15ull;
-    h ^= (uint64_t)(uint32_t)k.N + 0x632BE59BD9B4E019ull + (h << 6) + (h >> 2);
-    h ^= a + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
-    h ^= b + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
-    return (size_t)h;
-  }
-};
-
-struct CacheRow {
-  CacheKey key;
-  int pins = 0;          // requests in flight that read or write this row
-  bool indexed = false;  // visible to lookups
-  bool in_lru = false;   // unpinned and indexed: evictable
-  std::list<int>::iterator lru;
-};
-
 double now_s() {
   using namespace std::chrono;
   return duration<double>(steady_clock::now().time_since_epoch()).count();
@@ -223,83 +191,21 @@ struct mm_server_s {
   std::atomic<int64_t> launches{0};  // kernels launched for requests (start() runs outside mu)
   int inflight = 0, peak_inflight = 0;
   double t_origin = 0;
-  // resident coefficients (scheduler thread only, or under mu while idle)
+  // resident coefficients (the index is used by the scheduler thread only,
+  // or under mu while idle)
   void* d_cache = nullptr;  // cache_rows x (N_max + 1) coefficients
-  std::vector<CacheRow> rows;
-  std::unordered_map<CacheKey, int, CacheKeyHash> index;
-  std::list<int> lru;  // evictable rows, most recently used first
-  std::vector<int> free_rows;
+  CoefCache cache;
   std::atomic<int64_t> cache_hits{0}, cache_misses{0};
 };
 
 namespace {
 
-void cache_clear(mm_server s) {
-  s->index.clear();
-  s->lru.clear();
-  s->free_rows.clear();
-  for (int r = (int)s->rows.size() - 1; r >= 0; --r) {
-    s->rows[r] = CacheRow{};
-    s->free_rows.push_back(r);
-  }
-}
-
-void cache_pin(mm_server s, int r) {
-  CacheRow& c = s->rows[r];
-  if (c.in_lru) {
-    s->lru.erase(c.lru);
-    c.in_lru = false;
-  }
-  c.pins += 1;
-}
-
-void cache_unpin(mm_server s, int r) {
-  CacheRow& c = s->rows[r];
-  c.pins -= 1;
-  if (c.pins == 0 && c.indexed) {
-    s->lru.push_front(r);
-    c.lru = s->lru.begin();
-    c.in_lru = true;
-  }
-}
-
-// A row to write: a free one, else the least recently used unpinned one
-// (dropped from the index); -1 when every row is in use.
-int cache_take(mm_server s) {
-  if (!s->free_rows.empty()) {
-    const int r = s->free_rows.back();
-    s->free_rows.pop_back();
-    return r;
-  }
-  if (s->lru.empty()) return -1;
-  const int r = s->lru.back();
-  s->lru.pop_back();
-  CacheRow& c = s->rows[r];
-  s->index.erase(c.key);
-  c = CacheRow{};
-  return r;
-}
-
-void cache_free(mm_server s, int r) {
-  s->rows[r] = CacheRow{};
-  s->free_rows.push_back(r);
-}
-
 // A finished request's rows: the ones it read are unpinned; the ones it
 // wrote are published (unless the request failed, or the same key was
 // published meanwhile) or returned.
 void cache_release(mm_server s, Slot& sl, bool ok) {
-  for (int r : sl.pinned) cache_unpin(s, r);
-  for (int r : sl.reserved) {
-    CacheRow& c = s->rows[r];
-    if (ok && s->index.find(c.key) == s->index.end()) {
-      s->index.emplace(c.key, r);
-      c.indexed = true;
-      cache_unpin(s, r);
-    } else {
-      cache_free(s, r);
-    }
-  }
+  for (int r : sl.pinned) s->cache.unpin(r);
+  for (int r : sl.reserved) s->cache.finish_reserved(r, ok);
   sl.pinned.clear();
   sl.reserved.clear();
 }
@@ -384,7 +290,7 @@ void start(mm_server s, Slot& sl, Req&& rq) {
   // resident coefficients: with the cutoff known on the host, the assets
   // found in the cache are read from their rows and only the others are
   // computed (into rows reserved for them)
-  bool cached = !s->rows.empty() && N > 0;
+  bool cached = s->cache.size() > 0 && N > 0;
   std::vector<int> compute;  // positions in the request of the assets computed here
   std::vector<int> row_of;
   if (cached) {
@@ -395,28 +301,26 @@ void start(mm_server s, Slot& sl, Req&& rq) {
       k.N = N;
       k.t0 = sl.req.t0;
       k.t1 = sl.req.t1;
-      const auto it = s->index.find(k);
-      if (it != s->index.end()) {
-        cache_pin(s, it->second);
-        sl.pinned.push_back(it->second);
-        row_of[i] = it->second;
+      const int r = s->cache.acquire(k);
+      if (r >= 0) {
+        sl.pinned.push_back(r);
+        row_of[i] = r;
       } else {
         compute.push_back(i);
       }
     }
     for (int i : compute) {
-      const int r = cache_take(s);
+      CacheKey k;
+      k.asset = sl.req.assets[i];
+      k.N = N;
+      k.t0 = sl.req.t0;
+      k.t1 = sl.req.t1;
+      const int r = s->cache.reserve(k);
       if (r < 0) {  // every row in use: serve this request without the cache
         cache_release(s, sl, false);
         cached = false;
         break;
       }
-      CacheRow& c = s->rows[r];
-      c.key.asset = sl.req.assets[i];
-      c.key.N = N;
-      c.key.t0 = sl.req.t0;
-      c.key.t1 = sl.req.t1;
-      c.pins = 1;
       sl.reserved.push_back(r);
       row_of[i] = r;
     }
@@ -589,8 +493,7 @@ mm_status mm_server_create(const mm_server_desc* desc, mm_server* out) {
       delete s;
       return MM_ERR_OOM;
     }
-    s->rows.resize(d.cache_rows);
-    cache_clear(s);
+    s->cache.reset(d.cache_rows);
   }
   // slots: as many as the budget holds (at least one), each sized for the
   // largest admissible request
@@ -636,7 +539,7 @@ mm_status mm_server_load(mm_server s, const int64_t* h_offsets, const double* h_
       cudaMemcpy(s->d_t_all, h_t, E * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(s->d_p_all, h_logp, E * 8, cudaMemcpyHostToDevice) != cudaSuccess)
     return MM_ERR_CUDA;
-  cache_clear(s);  // the rows were of the previous store
+  s->cache.clear();  // the rows were of the previous store
   s->loaded = true;
   return MM_OK;
 }
