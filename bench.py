@@ -807,7 +807,8 @@ def main():
         info = mm.mm_plan_get_info(plan)
         stage_ms = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in stages.items()}
         dom = max((k for k in stages if k != "setup"), key=lambda k: stages[k][0])
-        # algorithmic bytes per launch ("Rooflines")
+        # algorithmic bytes per launch: each kernel's compulsory reads and
+        # writes (inputs once, outputs once), per event, grid cell and mode
         Mr = info["Mr"]
         cbytes = 8 if args.prec != "fp64" else 16
         gbytes = 4 if args.prec != "fp64" else 8
