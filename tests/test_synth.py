@@ -53,3 +53,15 @@ def test_sensitivity_covariances_in_range_and_definite():
     ev = synth.sensitivity_replications(1, covs[:2], reps=2, n=500)
     assert ev.D == 8 and ev.meta["truth"].shape == (4, 2, 2)
     assert np.allclose(ev.meta["truth"][0], covs[0] * 499 / 500)
+
+
+def test_request_stream_default_and_standing_windows():
+    a = synth.c5_requests(2, n=200, D=50, T=3000, w_range=(300, 3000), k_range=(3, 20))
+    # the default stream draws a fresh window per request
+    assert len({(r["t0"], r["t1"]) for r in a}) == len(a)
+    for r in a:
+        assert 0.0 <= r["t0"] < r["t1"] <= 3000.0 and 300.0 <= r["t1"] - r["t0"] <= 3000.0
+        assert 3 <= len(r["assets"]) <= 20 and len(set(r["assets"].tolist())) == len(r["assets"])
+        assert r["dt"] in (0.0, 60.0, 600.0)
+    b = synth.c5_requests(2, n=200, D=50, T=3000, w_range=(300, 3000), k_range=(3, 20), windows=5)
+    assert len({(r["t0"], r["t1"]) for r in b}) == 5
