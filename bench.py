@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "c4", "c5", "gram"])
+    ap.add_argument("--c1-n", type=int, default=1000,
+                    help="c1: synchronous points per asset (N = n/2; 100000 is the paper's timing table)")
     ap.add_argument("--gram-d", type=int, default=500, help="gram: assets (the largest C5 request)")
     ap.add_argument("--gram-n", type=int, default=14400, help="gram: cutoff (C5's N_max)")
     ap.add_argument("--reps", type=int, default=4096, help="c4: Monte Carlo replications per step")
@@ -84,7 +86,7 @@ def parse():
     return ap.parse_args()
 
 
-def workload(name, seed, reps=4096):
+def workload(name, seed, reps=4096, c1_n=1000):
     from paper_2003_02842_gb300 import synth
     if name == "c4":
         ev = synth.c4_batch(seed, reps=reps)
@@ -96,8 +98,8 @@ def workload(name, seed, reps=4096):
         ev = synth.c2_async(seed)
         N = ev.meta["N"]
     else:
-        ev = synth.c1_sync(seed)
-        N = 500
+        ev = synth.c1_sync(seed, n=c1_n)
+        N = c1_n // 2
     return ev, N
 
 
@@ -217,7 +219,7 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    ev, N = workload(args.workload, 0, args.reps)
+    ev, N = workload(args.workload, 0, args.reps, args.c1_n)
     import oracle
     oracle.build()
     per_step = max(0.01, min(2.0, 150.0 / max(args.steps + args.warmup, 1)))
@@ -683,7 +685,7 @@ def main():
     g.build()
     import paper_2003_02842_gb300 as mm
 
-    ev, N = workload(args.workload, seed=rank)
+    ev, N = workload(args.workload, seed=rank, c1_n=args.c1_n)
     off = torch.from_numpy(ev.offsets).to(dev)
     tt = torch.from_numpy(ev.t).to(dev)
     lp = torch.from_numpy(ev.logp).to(dev)
