@@ -661,13 +661,37 @@ __device__ __forceinline__ void red_shared_add(uint32_t addr, int v) {
 }
 
 // Float32 scatter with polynomial taps and exact integer accumulation.
-// Float atomics in shared memory run as compare-and-swap loops; integer ones
-// are native. Each tile therefore accumulates round(v phi 2^e) in int32 with
-// 2^e the largest power of two for which 2^e sum|v| over the tile's events
-// stays below 2^30: no cell can overflow (|phi| <= 1 + 1e-6), the sums are
-// exact and independent of the order of the atomics, and a cell is off by at
-// most half a unit (2^-e-1) per tap -- below float32 rounding of the cell
-// for the event densities of these workloads.
+// Shared-memory float atomics run as compare-and-swap loops and 64-bit
+// integer reductions are slower still (3.4x and 5.6x the time of an int32
+// reduction on GB300), so each tap's product x = v phi 2^eh goes to two int32
+// tiles by native int32 reductions: hi = round(x) and lo = round((x - hi) 2^k).
+// Both sums are exact and independent of the order of the atomics; a cell
+// holds (hi + lo 2^-k) 2^-eh with one quantum 2^-(eh + k) per tap.
+//
+// Scales (B = sum |v|, V = max |v| over the tile's n events, |phi| <= 1 + 1e-6):
+//  * eh = min(29 - ex(B), 21 - ex(V)) with B < 2^ex(B), V < 2^ex(V): every
+//    |x| < 2^21 (the rounding below needs |x| < 2^22) and a cell's hi sum is
+//    below 2^29 (1 + 1e-6) + n/2 < 2^31;
+//  * k = min(20, 30 - bitlen(n)): |lo| <= 2^(k-1) + 1 per tap, so a cell's lo
+//    sum is below n (2^(k-1) + 1) < 2^30.
+// The quantum per tap is therefore at most 2B 2^-(29 + k) = B 2^-(28 + k):
+// B 2^-48 for tiles of up to 1023 events, and for larger tiles B n 2^-58
+// (n < 2^bitlen(n) <= 2n). Against float32 rounding of a tap (2^-24 of the
+// tap's product) this is negligible up to about 2^20 events per tile.
+//
+// round(y) for |y| < 2^22 is taken as y + 1.5 2^23, whose float spacing is 1
+// (one FMA, no conversion instruction); the integer is the result's bits
+// minus those of 1.5 2^23.
+constexpr float kRoundMagic = 12582912.0f;  // 1.5 * 2^23
+constexpr int kRoundMagicBits = 0x4B400000;
+
+// Records staged per pass of the polynomial scatter (with two 4096-cell
+// tiles: 51 KB of shared memory per block).
+#ifndef MM_POLY_CHUNK
+#define MM_POLY_CHUNK 1536
+#endif
+constexpr int kPolyChunk = MM_POLY_CHUNK;
+
 template <int NT>
 __global__ void __launch_bounds__(kSpreadThreads) k_spread_poly(const int64_t* __restrict__ off,
                                                                const int* __restrict__ rb0,
@@ -675,19 +699,22 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_poly(const int64_t* _
                                                                const float* __restrict__ rv,
                                                                const int* __restrict__ gate, SpreadParams p,
                                                                KernelPoly poly, float* __restrict__ grid) {
-  constexpr int EC = EvChunk<float>::n;
+  constexpr int EC = kPolyChunk;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int* ev_p = reinterpret_cast<int*>(smem_raw);
   float* ev_d = reinterpret_cast<float*>(smem_raw + EC * sizeof(int));
   float* ev_v = ev_d + EC;
-  int* tile = reinterpret_cast<int*>(ev_v + EC);
-  const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile);
-  __shared__ float s_part[kSpreadThreads / 32];
+  const int tpad = (p.tile + 3) & ~3;  // tile cells rounded up to whole int4
+  int* tile_hi = reinterpret_cast<int*>(ev_v + EC);
+  int* tile_lo = tile_hi + tpad;
+  const uint32_t hi_s = (uint32_t)__cvta_generic_to_shared(tile_hi);
+  const uint32_t lo_s = (uint32_t)__cvta_generic_to_shared(tile_lo);
+  __shared__ float s_sum[kSpreadThreads / 32], s_max[kSpreadThreads / 32];
   const int64_t L = (int64_t)blockIdx.x * p.tile;
   const int Tlen = (int)min((int64_t)p.tile, p.Mr - L);
   {
-    int4* t4 = reinterpret_cast<int4*>(tile);
-    const int n4 = (Tlen + 3) / 4;
+    int4* t4 = reinterpret_cast<int4*>(tile_hi);
+    const int n4 = tpad / 2;  // both tiles
     for (int c = threadIdx.x; c < n4; c += kSpreadThreads) t4[c] = make_int4(0, 0, 0, 0);
   }
   pdl_wait();         // the records come from the prep kernel
@@ -697,31 +724,49 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_poly(const int64_t* _
   tile_ranges(off, rb0, p, a, L, Tlen, tr);
   const int64_t ntot = tr.n2 + tr.n1 + tr.n0;
   const int klo = p.klo;
-  // the tile's scale: sum |v| over its records (staged with the first chunk
-  // when one chunk holds them all, else a pass over the returns)
-  float part = 0.f;
+  // the tile's scales: sum and maximum of |v| over its records (staged with
+  // the first chunk when one chunk holds them all, else a pass over the returns)
+  float part = 0.f, pmax = 0.f;
   const int n_first = (int)min((int64_t)EC, ntot);
   for (int i = threadIdx.x; i < n_first; i += kSpreadThreads) {
     load_record<float>(rb0, rd, rv, p, tr, L, i, ev_p[i], ev_d[i], ev_v[i]);
     part += fabsf(ev_v[i]);
+    pmax = fmaxf(pmax, fabsf(ev_v[i]));
   }
   for (int64_t i = EC + threadIdx.x; i < ntot; i += kSpreadThreads) {
     int pp;
     float dd, vv;
     load_record<float>(rb0, rd, rv, p, tr, L, i, pp, dd, vv);
     part += fabsf(vv);
+    pmax = fmaxf(pmax, fabsf(vv));
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = part;
+  for (int o = 16; o > 0; o >>= 1) {
+    part += __shfl_xor_sync(0xffffffffu, part, o);
+    pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_sum[threadIdx.x >> 5] = part;
+    s_max[threadIdx.x >> 5] = pmax;
+  }
   __syncthreads();
-  float B = 0.f;
+  float B = 0.f, V = 0.f;
 #pragma unroll
-  for (int w = 0; w < kSpreadThreads / 32; ++w) B += s_part[w];
-  int ex = 0;
-  if (B > 0.f && B < 3.0e38f) frexpf(B, &ex);  // B < 2^ex
-  const int e = B > 0.f ? 30 - ex : 0;         // 2^e B < 2^30
-  const float scale = ldexpf(1.0f, e), inv = ldexpf(1.0f, -e);
+  for (int w = 0; w < kSpreadThreads / 32; ++w) {
+    B += s_sum[w];
+    V = fmaxf(V, s_max[w]);
+  }
+  int eh = 0, k = 0;
+  if (B > 0.f && B < 3.0e38f) {
+    int exB, exV;
+    frexpf(B, &exB);  // B < 2^exB
+    frexpf(V, &exV);  // V < 2^exV
+    eh = min(29 - exB, 21 - exV);
+    const int bitlen = 64 - __clzll((long long)ntot);
+    k = max(0, min(20, 30 - bitlen));
+  }
+  const float scale = ldexpf(1.0f, eh), kscale = ldexpf(1.0f, k);
+  const float inv_h = ldexpf(1.0f, -eh), inv_l = ldexpf(1.0f, -(eh + k));
   for (int64_t cs = 0; cs < ntot; cs += EC) {
     const int n = (int)min((int64_t)EC, ntot - cs);
     if (cs > 0) {
@@ -735,24 +780,20 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_poly(const int64_t* _
       if (pe == kNoCell) continue;
       const float z = ev_d[ei] - 0.5f;
       const float vs = ev_v[ei] * scale;
-      float w[NT];
+      const int c0 = pe + klo;
+      const bool inside = c0 >= 0 && c0 + NT <= Tlen;  // else test each tap's cell
 #pragma unroll
       for (int j = 0; j < NT; ++j) {
-        float acc = poly.c[j][kPolyDeg];
+        float w = poly.c[j][kPolyDeg];
 #pragma unroll
-        for (int i = kPolyDeg - 1; i >= 0; --i) acc = fmaf(acc, z, poly.c[j][i]);
-        w[j] = acc;
-      }
-      const int c0 = pe + klo;
-      if (c0 >= 0 && c0 + NT <= Tlen) {
-        const uint32_t a0 = tile_s + 4u * (uint32_t)c0;
-#pragma unroll
-        for (int j = 0; j < NT; ++j) red_shared_add(a0 + 4u * j, __float2int_rn(vs * w[j]));
-      } else {
-#pragma unroll
-        for (int j = 0; j < NT; ++j) {
-          const unsigned c = (unsigned)(c0 + j);
-          if (c < (unsigned)Tlen) red_shared_add(tile_s + 4u * c, __float2int_rn(vs * w[j]));
+        for (int i = kPolyDeg - 1; i >= 0; --i) w = fmaf(w, z, poly.c[j][i]);
+        const float h = fmaf(vs, w, kRoundMagic);      // round(vs w) + 1.5 2^23
+        const float r = fmaf(vs, w, kRoundMagic - h);  // vs w - round(vs w), |r| <= 1/2
+        const float l = fmaf(r, kscale, kRoundMagic);
+        const unsigned c = (unsigned)(c0 + j);
+        if (inside || c < (unsigned)Tlen) {
+          red_shared_add(hi_s + 4u * c, __float_as_int(h) - kRoundMagicBits);
+          red_shared_add(lo_s + 4u * c, __float_as_int(l) - kRoundMagicBits);
         }
       }
     }
@@ -762,7 +803,8 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_poly(const int64_t* _
     // the per-asset FFT's input order: complex point m = (L + c) / 2 goes to
     // its digit reversal (tiles and M_r are even, so cells pair up)
     float2* gz = reinterpret_cast<float2*>(grid + (int64_t)a * p.Mr);
-    const int2* t2 = reinterpret_cast<const int2*>(tile);
+    const int2* h2 = reinterpret_cast<const int2*>(tile_hi);
+    const int2* l2 = reinterpret_cast<const int2*>(tile_lo);
     const int m0 = (int)(L >> 1);
     for (int c2 = threadIdx.x; c2 < (Tlen >> 1); c2 += kSpreadThreads) {
       int m = m0 + c2, pos = 0;
@@ -775,22 +817,26 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_poly(const int64_t* _
           m = h;
         }
       }
-      const int2 v = t2[c2];
-      gz[pos] = make_float2((float)v.x * inv, (float)v.y * inv);
+      const int2 hv = h2[c2], lv = l2[c2];
+      gz[pos] = make_float2(fmaf((float)lv.x, inv_l, (float)hv.x * inv_h),
+                            fmaf((float)lv.y, inv_l, (float)hv.y * inv_h));
     }
     pdl_trigger();
     return;
   }
   float* g = grid + (int64_t)a * p.Mr + L;
   if (((reinterpret_cast<uintptr_t>(g) & 15) == 0) && (Tlen & 3) == 0) {
-    const int4* t4 = reinterpret_cast<const int4*>(tile);
+    const int4* h4 = reinterpret_cast<const int4*>(tile_hi);
+    const int4* l4 = reinterpret_cast<const int4*>(tile_lo);
     float4* g4 = reinterpret_cast<float4*>(g);
     for (int c = threadIdx.x; c < Tlen / 4; c += kSpreadThreads) {
-      const int4 q = t4[c];
-      g4[c] = make_float4((float)q.x * inv, (float)q.y * inv, (float)q.z * inv, (float)q.w * inv);
+      const int4 hq = h4[c], lq = l4[c];
+      g4[c] = make_float4(fmaf((float)lq.x, inv_l, (float)hq.x * inv_h), fmaf((float)lq.y, inv_l, (float)hq.y * inv_h),
+                          fmaf((float)lq.z, inv_l, (float)hq.z * inv_h), fmaf((float)lq.w, inv_l, (float)hq.w * inv_h));
     }
   } else {
-    for (int c = threadIdx.x; c < Tlen; c += kSpreadThreads) g[c] = (float)tile[c] * inv;
+    for (int c = threadIdx.x; c < Tlen; c += kSpreadThreads)
+      g[c] = fmaf((float)tile_lo[c], inv_l, (float)tile_hi[c] * inv_h);
   }
   pdl_trigger();
 }
@@ -804,7 +850,8 @@ cudaError_t launch_spread_poly(const int64_t* off, const int* rb0, const void* r
                                cudaStream_t s) {
   if (p.tile > spread_max_tile(false)) return cudaErrorInvalidValue;
   const int nt = p.khi - p.klo + 1;
-  const size_t smem = (size_t)EvChunk<float>::n * (sizeof(int) + 2 * sizeof(float)) + ((size_t)p.tile + 3) / 4 * 16;
+  // staged records, then the hi and lo tiles (each rounded up to whole int4)
+  const size_t smem = (size_t)kPolyChunk * (sizeof(int) + 2 * sizeof(float)) + 2 * (((size_t)p.tile + 3) / 4 * 16);
   dim3 grd(p.ntiles, p.D);
   auto go = [&](auto fn) -> cudaError_t {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -50,13 +50,18 @@ WORKLOADS = {
 @pytest.mark.parametrize("kernel", ["gauss", "kb", "es"])
 def test_polynomial_taps_across_tolerances(kernel, tol):
     # the float32 spreading's per-tap polynomials for every kernel width the
-    # tolerance rule gives, against the direct sum at the float32 bound
+    # tolerance rule gives, against the direct sum: the kernel width meets
+    # Eq. (15) at tol itself (Sec. 2.2.5: the M_sp rule achieves the
+    # tolerance), plus the float32 path's own rounding (grid, FFT and the
+    # deconvolution's amplification: at most 4.1e-7 over these kernels and
+    # tolerances on GB300), for which 1e-6 is allowed
     ev = synth.c2_async(6)
     N = ev.meta["N"]
     out = run(dict(tol=tol, kernel=kernel, basis="dirichlet", prec="bf16x3", spread_algo="scatter"), ev, N)
     assert out["info"]["spread_poly"] == 1
     ref = oracle.coeffs_F(ev.offsets, ev.t, ev.logp, N)
-    assert np.all(rel_l2_rows(out["F"], ref) <= max(1e-5, 10 * tol))
+    err = rel_l2_rows(out["F"], ref)
+    assert np.all(err <= tol + 1e-6), err
 
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
