@@ -33,16 +33,21 @@ sys.path.insert(0, ROOT)
 METRIC = "events/sec (NUFFT coeffs) & D×D corr matrices/sec vs FP64 GPU path at max|Δcorr|≤1e-4"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
-# dram bytes (read + write) per launch of the dominant kernel, from the ncu
-# capture summarised in profiles/ (None until a capture of the current kernel)
+# dram bytes (read + write) per launch of a kernel, from the ncu captures
+# summarised in profiles/ (a kernel changed since its capture has no entry)
 NCU_TRAFFIC = {
-    # from the ncu capture of the block workload in its default configuration
-    ("spread", "c3", "bf16x3", "es"): 9225984,
+    # the block workload in its default configuration
+    # (profiles/c3_block_D100_N10000_kernels_ncu.md)
     ("fft", "c3", "bf16x3", "es"): 16451584,
     ("prep", "c3", "bf16x3", "es"): 12287488,
     ("gram", "c3", "bf16x3", "es"): 8115712,
-    # the contraction alone at D = 500, N = 14400
+    # the contraction alone at D = 500, N = 14400 (profiles/gram_D500_N14400_kernel_ncu.md)
     ("gram", "gram_D500_N14400", "bf16x3", "es"): 59650560,
+}
+NCU_SOURCE = {
+    "c3": "profiles/c3_block_D100_N10000_kernels_ncu.md",
+    "c4": "profiles/c4_batch_R256_D10_kernels_ncu.md",
+    "gram_D500_N14400": "profiles/gram_D500_N14400_kernel_ncu.md",
 }
 # the batched workload is too large for a full ncu capture: dram bytes per
 # grid row of its FFT from a capture of 256 replications (2560 rows of grid
@@ -51,6 +56,49 @@ NCU_TRAFFIC = {
 NCU_TRAFFIC_PER_ROW = {
     ("fft", "c4", "bf16x3", "es", 57600): 334006.0,
 }
+
+# Stages (a)-(c) of the hot path, as the library's profiler names them.
+COEFF_STAGES = ("prep", "spread", "fft_cols", "fft_rows", "fft", "fused")
+
+
+def hbm_roofline(stage_ms, n_events, D, N, Mr, fp64, peaks, peak_src, traffic_key):
+    """Roofline of the dominant kernel and of the coefficient chain (a)-(c).
+
+    Algorithmic bytes follow the scope table's measurement rule: 16 B per
+    event (time and log-price read once) and one coefficient write per mode
+    (8 B in complex64, 16 B in complex128) per asset; the contraction reads
+    the coefficients once. Per kernel: the prep kernel owns the event reads,
+    the FFT (or the fused kernel) the coefficient writes, the contraction the
+    coefficient reads. Records and grid rows written and read back between
+    kernels are implementation bytes, reported beside them."""
+    cb = 16 if fp64 else 8
+    gb = 8 if fp64 else 4
+    rb = 4 + 2 * gb  # per-event record (cell, offset, return)
+    coef = float(cb * (N + 1) * D)
+    grid = float(gb * Mr * D)
+    alg = {"prep": 16.0 * n_events, "spread": 0.0, "fft_cols": 0.0, "fft_rows": coef, "fft": coef,
+           "fused": 16.0 * n_events + coef, "gram": coef, "reduce": 0.0}
+    impl = {"prep": float(rb * n_events), "spread": rb * n_events + grid, "fft_cols": 2.0 * grid,
+            "fft_rows": grid, "fft": grid, "fused": 0.0, "gram": 0.0, "reduce": 0.0}
+    timed = {k: v for k, v in stage_ms.items() if k != "setup" and v > 0}
+    dom = max(timed, key=lambda k: timed[k])
+    avg = timed[dom]
+    ach = alg.get(dom, 0.0) / (avg * 1e-3) / 1e9
+    traffic = NCU_TRAFFIC.get((dom,) + traffic_key)
+    roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"], "traffic": traffic, "peak_source": f"{peak_src} hbm_gbs",
+            "avg_launch_ms": avg, "algorithmic_bytes_per_launch": alg.get(dom, 0.0),
+            "implementation_bytes_per_launch": impl.get(dom, 0.0)}
+    if traffic is not None:
+        roof["traffic_source"] = NCU_SOURCE.get(traffic_key[0], "profiles/")
+    chain = [k for k in COEFF_STAGES if timed.get(k, 0.0) > 0]
+    ms = sum(timed[k] for k in chain)
+    cbytes = 16.0 * n_events + coef
+    roof["chain"] = {"kernels": chain, "ms": ms, "algorithmic_bytes": cbytes,
+                     "implementation_bytes": sum(impl[k] for k in chain),
+                     "achieved": cbytes / (ms * 1e-3) / 1e9 if ms > 0 else 0.0,
+                     "frac": cbytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"] if ms > 0 else 0.0}
+    return roof
 
 
 def parse():
@@ -387,29 +435,15 @@ def bench_batch(args):
     if rank == 0:
         peaks, peak_src = load_peaks()
         stage_ms = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in stages.items()}
-        dom = max((k for k in stages if k != "setup"), key=lambda k: stages[k][0])
         Mr = i1["Mr"]
         Dtot = reps * Dg
-        alg = {
-            "prep": 28.0 * ev.n_events,
-            "spread": 12.0 * ev.n_events + 4.0 * Mr * Dtot,
-            "fft": 4.0 * Mr * Dtot + 8.0 * (Nmax + 1) * Dtot,
-            "fft_cols": 8.0 * Mr * Dtot,
-            "fft_rows": 4.0 * Mr * Dtot + 8.0 * (Nmax + 1) * Dtot,
-            "gram": 8.0 * (Nmax + 1) * Dtot,
-        }
-        avg_ms = stage_ms[dom]
-        achieved = alg.get(dom, 0.0) / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
-        traffic = NCU_TRAFFIC.get((dom, "c4", args.prec, args.kernel))
-        per_row = NCU_TRAFFIC_PER_ROW.get((dom, "c4", args.prec, args.kernel, int(Mr)))
-        if traffic is None and per_row is not None:
-            traffic = per_row * Dtot
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "peak_source": f"{peak_src} hbm_gbs", "avg_launch_ms": avg_ms,
-                "algorithmic_bytes_per_launch": alg.get(dom, 0.0)}
-        if per_row is not None and traffic == per_row * Dtot:
-            roof["traffic_source"] = "per-row dram bytes of a 256-replication capture x rows of this launch"
+        roof = hbm_roofline(stage_ms, ev.n_events, Dtot, Nmax, Mr, False, peaks, peak_src,
+                            ("c4", args.prec, args.kernel))
+        per_row = NCU_TRAFFIC_PER_ROW.get((roof["kernel"], "c4", args.prec, args.kernel, int(Mr)))
+        if roof["traffic"] is None and per_row is not None:
+            roof["traffic"] = per_row * Dtot
+            roof["traffic_source"] = ("per-row dram bytes of a 256-replication capture x rows of this launch "
+                                      f"({NCU_SOURCE['c4']})")
         ev_c, secs, assets, threads = oracle_rate(ev, Nmax, args.cpu_budget)
         cpu = {"value": ev_c / secs if secs > 0 else 0.0, "unit": "events/s", "cores": threads, "kind": "oracle",
                "sample": f"direct sum of Eq. (4), k=0..N_max, on {assets} assets (~{secs:.1f} s, blocks of modes "
@@ -782,7 +816,7 @@ def main():
         mm.mm_estimate(p64, off, tt, lp, N, coeffs=c64, sigma=S64, R=R64)
         torch.cuda.synchronize()
         k64 = max(3, min(20, args.steps))
-        ms64 = 0.0
+        ev64 = []
         for _ in range(k64):
             flush.zero_()
             a = torch.cuda.Event(enable_timing=True)
@@ -790,13 +824,14 @@ def main():
             a.record()
             mm.mm_estimate(p64, off, tt, lp, N, coeffs=c64, sigma=S64, R=R64)
             b.record()
+            ev64.append((a, b))
         torch.cuda.synchronize()
-        ms64 = a.elapsed_time(b)  # last step (steady state)
+        ms64 = float(np.median([a.elapsed_time(b) for a, b in ev64]))  # median step
         dR = float((R.double() - R64).abs().max())
         dF = float(((coef.to(torch.complex128) - c64).abs().pow(2).sum(1).sqrt()
                     / c64.abs().pow(2).sum(1).sqrt().clamp_min(1e-300)).max())
-        fp64 = {"events_per_s": ev.n_events / (ms64 * 1e-3), "ms_per_step": ms64,
-                "max_abs_dcorr": dR, "max_rel_l2_dcoef": dF}
+        fp64 = {"events_per_s": ev.n_events / (ms64 * 1e-3), "ms_per_step": ms64, "steps": k64,
+                "timing": "median step", "max_abs_dcorr": dR, "max_rel_l2_dcoef": dF}
         mm.mm_destroy(p64)
 
     # max over ranks of the times, sum over ranks of the events
@@ -808,28 +843,9 @@ def main():
         peaks, peak_src = load_peaks()
         info = mm.mm_plan_get_info(plan)
         stage_ms = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in stages.items()}
-        dom = max((k for k in stages if k != "setup"), key=lambda k: stages[k][0])
-        # algorithmic bytes per launch: each kernel's compulsory reads and
-        # writes (inputs once, outputs once), per event, grid cell and mode
         Mr = info["Mr"]
-        cbytes = 8 if args.prec != "fp64" else 16
-        gbytes = 4 if args.prec != "fp64" else 8
-        rbytes = 4 + 2 * gbytes  # per-event record of the prep kernel (cell, offset, return)
-        alg = {
-            "prep": (16.0 + rbytes) * ev.n_events,           # t, logp in; records out
-            "spread": rbytes * ev.n_events + gbytes * Mr * D,  # records in; grid out
-            "fft_cols": 2.0 * gbytes * Mr * D,                 # grid in and out
-            "fft_rows": gbytes * Mr * D + cbytes * (N + 1) * D,
-            "fft": gbytes * Mr * D + cbytes * (N + 1) * D,     # grid in, coefficients out
-            "gram": cbytes * (N + 1) * D,                      # coefficients in
-            "reduce": 0.0,
-        }
-        avg_ms = stage_ms[dom]
-        achieved = alg.get(dom, 0.0) / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
-        traffic = NCU_TRAFFIC.get((dom, args.workload, args.prec, args.kernel))
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": f"{peak_src} hbm_gbs",
-                "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": alg.get(dom, 0.0)}
+        roof = hbm_roofline(stage_ms, ev.n_events, D, N, Mr, args.prec == "fp64", peaks, peak_src,
+                            (args.workload, args.prec, args.kernel))
         ev_c, secs, assets, threads = oracle_rate(ev, N, args.cpu_budget)
         cpu = {"value": ev_c / secs if secs > 0 else 0.0, "unit": "events/s", "cores": threads, "kind": "oracle",
                "sample": f"direct sum of Eq. (4), k=0..N, on {assets} of {D} assets (~{secs:.1f} s, "

@@ -230,7 +230,8 @@ mm_status mm_corr_pairwise(mm_plan plan, const void* d_coeffs, int32_t N_coeffs,
  * last call's contents, so calls that overlap on the GPU race: order them
  * (one stream, or explicit synchronisation). The call synchronises the
  * stream and returns the contraction's device status (MM_OK,
- * MM_ERR_ZERO_VARIANCE or MM_ERR_TIMEOUT). */
+ * MM_ERR_ZERO_VARIANCE or MM_ERR_TIMEOUT); on a stream that is being
+ * captured into a graph it launches nothing and returns MM_ERR_INVALID_ARG. */
 mm_status mm_corr_noalloc(int32_t D, int32_t N, mm_basis basis, mm_precision prec, const void* d_coeffs,
                           void* d_sigma_or_null, void* d_R, void* stream);
 
@@ -289,6 +290,19 @@ mm_status mm_profile_read(mm_plan plan, double* ms, int64_t* launches, int32_t r
  * launches; the graph reads the inputs' current contents. Other calls, and
  * every call with graphs off, launch eagerly. */
 mm_status mm_plan_set_graphs(mm_plan plan, int32_t on);
+
+/* Limit, in nanoseconds, of the tensor-core contraction's device-side waits
+ * on its own MMA completions (mm_cov, mm_corr, mm_estimate on the mixed
+ * precisions); ns = 0 makes each wait a single non-blocking test, ns < 0
+ * restores the default of one second. A diagnostic of the bounded-wait path
+ * (failure detection without a GPU fault): a limit shorter than the MMAs
+ * take (0 always is) makes the contraction give up, leave the
+ * accumulator unwritten, let the MMAs it issued finish, free its tensor
+ * memory and record MM_ERR_TIMEOUT, which the next mm_plan_sync (or the
+ * synchronous call) returns; Sigma and R of that call are then undefined.
+ * Later calls with the default limit are unaffected. Graphs captured with
+ * the old limit are re-captured. Not part of the paper's method. */
+mm_status mm_plan_set_wait_limit(mm_plan plan, int64_t ns);
 
 /* Static text for a status code. */
 const char* mm_status_string(mm_status s);

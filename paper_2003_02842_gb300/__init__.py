@@ -21,7 +21,7 @@ from ._lib import BASES, KERNELS, PRECISIONS, STAGES, STATUS_NAMES
 
 __all__ = [
     "MMError", "Plan", "mm_plan_create", "mm_destroy", "mm_coeffs", "mm_cov", "mm_corr", "mm_estimate",
-    "mm_estimate_host", "mm_nyquist", "mm_plan_sync", "mm_plan_get_info", "mm_profile_enable", "mm_plan_set_graphs",
+    "mm_estimate_host", "mm_nyquist", "mm_plan_sync", "mm_plan_get_info", "mm_profile_enable", "mm_plan_set_graphs", "mm_plan_set_wait_limit",
     "mm_corr_pairwise",
     "mm_profile_read", "mm_status_string", "mm_version", "mm_corr_noalloc", "mm_autotune", "KERNELS", "BASES", "PRECISIONS", "STAGES",
     "Batch", "mm_batch_create", "mm_batch_destroy", "mm_batch_epps", "mm_batch_autotune", "mm_batch_coeffs",
@@ -329,6 +329,13 @@ def mm_profile_enable(plan, on=True):
 def mm_plan_set_graphs(plan, on=True):
     """CUDA graph replay of steady mm_estimate calls (on by default)."""
     _check(_lib.load().mm_plan_set_graphs(plan.handle, 1 if on else 0), "mm_plan_set_graphs")
+
+
+def mm_plan_set_wait_limit(plan, ns=-1):
+    """Limit of the contraction's device-side waits in ns (0: one
+    non-blocking test; < 0: the 1 s default); a diagnostic of the
+    bounded-wait path."""
+    _check(_lib.load().mm_plan_set_wait_limit(plan.handle, int(ns)), "mm_plan_set_wait_limit")
 
 
 def mm_profile_read(plan, reset=False) -> dict:

@@ -188,6 +188,7 @@ def load():
         "mm_plan_get_info": ([p, ctypes.POINTER(PlanInfo)], st),
         "mm_profile_enable": ([p, i32], st),
         "mm_plan_set_graphs": ([p, i32], st),
+        "mm_plan_set_wait_limit": ([p, ctypes.c_int64], st),
         "mm_profile_read": ([p, p, p, i32], st),
         "mm_status_string": ([st], ctypes.c_char_p),
         "mm_version": ([], i32),

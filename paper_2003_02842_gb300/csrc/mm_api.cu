@@ -315,6 +315,7 @@ struct mm_plan_s {
   } eg[2];
   cudaStream_t cap = nullptr;  // capture stream
   int cfg_gen = 0;             // configuration generation (a graph holds one)
+  uint64_t wait_ns = kDefaultWaitNs;  // limit of the contraction's device waits
   bool graphs = true;
   int64_t graph_launches = 0;
   // instrumentation
@@ -603,6 +604,7 @@ mm_status check_plan(mm_plan p) {
 
 GramParams gram_params(mm_plan p, int N) {
   GramParams g{};
+  g.wait_ns = p->wait_ns;
   g.D = p->D;
   g.N = N;
   g.ld = N + 1;
@@ -1274,6 +1276,14 @@ mm_status mm_plan_sync(mm_plan p) {
   // a timed-out wait may leave a split FFT's pair words set: clear them
   if ((f & ST_TIMEOUT) && p->fft_sync) MM_CUDA(cudaMemset(p->fft_sync, 0, 2 * (size_t)p->desc.D * sizeof(int)));
   return flags_to_status(f);
+}
+
+mm_status mm_plan_set_wait_limit(mm_plan p, int64_t ns) {
+  mm_status r = check_plan(p);
+  if (r != MM_OK) return r;
+  p->wait_ns = ns >= 0 ? (uint64_t)ns : kDefaultWaitNs;
+  p->cfg_gen += 1;  // captured graphs hold the old limit
+  return MM_OK;
 }
 
 mm_status mm_plan_set_graphs(mm_plan p, int32_t on) {

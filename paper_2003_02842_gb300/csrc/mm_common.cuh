@@ -23,6 +23,10 @@ enum : int {
   ST_OUT_OF_WINDOW = 1 << 8,
 };
 
+// Device-side waits give up after this long (unless a plan sets its own
+// limit for the contraction) and report ST_TIMEOUT.
+constexpr uint64_t kDefaultWaitNs = 1000000000ull;  // 1 s
+
 template <typename T>
 struct __align__(2 * sizeof(T)) Cplx {
   T x, y;
@@ -153,6 +157,7 @@ struct GramParams {
   int nchunks;       // ceil((N+1) / chunk)
   int chunks_per_split;
   int Dp;            // row stride of the FP32 accumulator (D rounded up to 4)
+  unsigned long long wait_ns;  // limit of the tensor-core kernel's progress waits
 };
 
 struct GroupScale;  // per-problem fixed-point scales (mm_spread_dev.cuh)

@@ -15,8 +15,9 @@
 // canonical 128-byte-swizzled K-major layout), and one thread issues
 // tcgen05.mma (hi*hi + hi*lo + lo*hi) into a TMEM accumulator; commits are
 // tracked by mbarriers so the next tile is staged while the tensor core runs.
-// Every wait is bounded: after ~1 s it records MM_ERR_TIMEOUT and the CTA
-// drains and frees its TMEM.
+// Every wait is bounded: after the plan's wait limit (1 s unless
+// mm_plan_set_wait_limit changed it) it records MM_ERR_TIMEOUT, and the CTA
+// lets the MMAs it issued finish before it frees its TMEM.
 // The split-K partial products meet in an FP32 accumulator through vector
 // reductions in L2 (red.global.add.v4.f32); k_corr_acc then normalises in
 // FP64. FP64 path: a CUDA-core tiled kernel writing per-split partial tiles
@@ -340,10 +341,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_gram_tc(const float2* __restr
     if (two) load_chunk<MODE>(F, g, wsq, J * kTile, c0 * chunk, cb);
   }
   bool ok = true;
+  int committed = -1;  // last K-chunk whose MMAs were issued and committed
   for (int it = 0; it < nit; ++it) {
     const int st = it & 1;
     if (it >= 2) {
-      if (!mbar_wait(&bars[st], (uint32_t)(((it >> 1) - 1) & 1), kWaitLimitNs)) ok = false;
+      if (!mbar_wait(&bars[st], (uint32_t)(((it >> 1) - 1) & 1), g.wait_ns)) ok = false;
     }
     if (__syncthreads_or(!ok)) {
       ok = false;
@@ -373,11 +375,18 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_gram_tc(const float2* __restr
       }
       tc_commit(&bars[st]);
     }
+    committed = it;
   }
-  // drain: the last commit covers every MMA issued before it
-  if (nit > 0) {
-    const int last = nit - 1;
-    if (!mbar_wait(&bars[last & 1], (uint32_t)((last >> 1) & 1), ok ? kWaitLimitNs : kWaitLimitNs / 4)) ok = false;
+  // drain: the last commit covers every MMA issued before it. A wait that
+  // gives up still lets those MMAs finish (at the fixed limit) before the
+  // CTA frees its TMEM and shared memory.
+  if (committed >= 0) {
+    uint64_t* bar = &bars[committed & 1];
+    const uint32_t par = (uint32_t)((committed >> 1) & 1);
+    if (!mbar_wait(bar, par, g.wait_ns)) {
+      ok = false;
+      mbar_wait(bar, par, kWaitLimitNs);
+    }
   }
   if (!ok) atomicOr(&s_fail, 1);
   tc_fence_after();

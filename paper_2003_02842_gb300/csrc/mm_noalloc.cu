@@ -72,6 +72,14 @@ extern "C" mm_status mm_corr_noalloc(int32_t D, int32_t N, mm_basis basis, mm_pr
   if (D < 1 || N < 0) return MM_ERR_INVALID_ARG;
   if (D > kNaMaxD || N > kNaMaxN) return MM_ERR_UNSUPPORTED;  // beyond the fixed scratch
   if (basis == MM_BASIS_FEJER && N < 1) return MM_ERR_CUTOFF;
+  // the call reads its status back and synchronises the stream, which a
+  // stream being captured into a graph does not allow
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return MM_ERR_INVALID_ARG;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return MM_ERR_INVALID_ARG;
   void* base = nullptr;
   mm_status r = scratch_base(&base);
   if (r != MM_OK) return r;
@@ -82,6 +90,7 @@ extern "C" mm_status mm_corr_noalloc(int32_t D, int32_t N, mm_basis basis, mm_pr
 
   const bool fp64 = prec == MM_PREC_FP64;
   GramParams g{};
+  g.wait_ns = kDefaultWaitNs;
   g.D = D;
   g.N = N;
   g.ld = N + 1;

@@ -5,7 +5,8 @@
 // Gaussian gridding split, Eq. (17)), Kaiser-Bessel (Eq. (7)) or exponential
 // of semicircle (Eq. (9)) kernel.
 //
-// Phase reduction. GB300 executes float64 at 1/64 of the float32 rate, and a
+// Phase reduction. GB300 executes float64 at about 1/47 of the float32 rate
+// (measured: 4.8e11 float64 FMAs per second over the chip), and a
 // float32 cell coordinate loses the phase at large N. The cell coordinate
 // u = (t - t0) M_r / span is therefore computed in exact 64-bit fixed point on
 // the integer pipes: t_fix = trunc(t 2^F) is read off the float64 bit pattern,
@@ -674,10 +675,11 @@ __device__ __forceinline__ void red_shared_add(uint32_t addr, int v) {
 //    below 2^29 (1 + 1e-6) + n/2 < 2^31;
 //  * k = min(20, 30 - bitlen(n)): |lo| <= 2^(k-1) + 1 per tap, so a cell's lo
 //    sum is below n (2^(k-1) + 1) < 2^30.
-// The quantum per tap is therefore at most 2B 2^-(29 + k) = B 2^-(28 + k):
-// B 2^-48 for tiles of up to 1023 events, and for larger tiles B n 2^-58
-// (n < 2^bitlen(n) <= 2n). Against float32 rounding of a tap (2^-24 of the
-// tap's product) this is negligible up to about 2^20 events per tile.
+// The quantum per tap, 2^-(eh + k), is therefore at most
+// max(B 2^-(28 + k), V 2^-(20 + k)): max(B 2^-48, V 2^-40) for tiles of up to
+// 1023 events, and for larger tiles at most max(B n 2^-58, V n 2^-50)
+// (2^-k < 2n 2^-30). Against float32 rounding of a tap's product (2^-24 of
+// it) this is negligible up to about 2^20 events per tile.
 //
 // round(y) for |y| < 2^22 is taken as y + 1.5 2^23, whose float spacing is 1
 // (one FMA, no conversion instruction); the integer is the result's bits
@@ -685,12 +687,11 @@ __device__ __forceinline__ void red_shared_add(uint32_t addr, int v) {
 constexpr float kRoundMagic = 12582912.0f;  // 1.5 * 2^23
 constexpr int kRoundMagicBits = 0x4B400000;
 
-// Records staged per pass of the polynomial scatter (with two 4096-cell
-// tiles: 51 KB of shared memory per block).
-#ifndef MM_POLY_CHUNK
-#define MM_POLY_CHUNK 1536
-#endif
-constexpr int kPolyChunk = MM_POLY_CHUNK;
+// Records staged per pass of the polynomial scatter: with two 4096-cell
+// tiles, 44 KB of shared memory per block and five blocks per SM. On the
+// block workload 512 to 1536 records and 2048- or 4096-cell tiles all ran
+// the stage within 2 us of one another: its time is the reductions.
+constexpr int kPolyChunk = 1024;
 
 template <int NT>
 __global__ void __launch_bounds__(kSpreadThreads) k_spread_poly(const int64_t* __restrict__ off,

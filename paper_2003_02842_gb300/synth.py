@@ -134,7 +134,9 @@ def epps_replications(seed, reps, T=28800, rate=1 / 5, rho=0.35, var=(0.1, 0.2))
             ts.append(idx.astype(np.float64))
             ps.append(lp[idx, j])
     ev = from_lists(ts, ps)
-    ev.meta = {"workload": f"epps_R{reps}_T{T}", "reps": reps, "T": T, "rate": rate, "rho": rho}
+    dt = 1.0 / SECONDS_PER_DAY
+    ev.meta = {"workload": f"epps_R{reps}_T{T}", "reps": reps, "T": T, "rate": rate, "rho": rho,
+               "step_cov": cov * dt, "step_mean": (0.01 - 0.5 * np.diag(cov)) * dt}
     return ev
 
 

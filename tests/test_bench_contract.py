@@ -40,3 +40,30 @@ def test_reference_arm_other_ranks_print_nothing():
     r = _run({"RANK": "1", "WORLD_SIZE": "2"}, "--workload", "c1", "--steps", "1", "--warmup", "0")
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_roofline_counts_the_algorithmic_bytes_of_the_measurement_rule():
+    # 16 B per event and one complex64 coefficient write per mode and asset
+    # are algorithmic; records and grid rows are implementation bytes
+    sys.path.insert(0, ROOT)
+    import bench
+    stage_ms = {"prep": 0.013, "spread": 0.024, "fft": 0.031, "gram": 0.016, "reduce": 0.007, "setup": 0.5,
+                "fft_cols": 0.0, "fft_rows": 0.0, "fused": 0.0}
+    n, D, N, Mr = 766162, 100, 10000, 40500
+    roof = bench.hbm_roofline(stage_ms, n, D, N, Mr, False, {"hbm_gbs": 6792.7}, "measured", ("c3", "bf16x3", "es"))
+    assert roof["kernel"] == "fft"
+    assert roof["algorithmic_bytes_per_launch"] == 8.0 * (N + 1) * D
+    assert roof["implementation_bytes_per_launch"] == 4.0 * Mr * D
+    assert abs(roof["achieved"] - 8.0 * (N + 1) * D / 0.031e-3 / 1e9) < 1e-6
+    assert abs(roof["frac"] - roof["achieved"] / 6792.7) < 1e-12
+    ch = roof["chain"]
+    assert ch["kernels"] == ["prep", "spread", "fft"]
+    assert abs(ch["ms"] - 0.068) < 1e-12
+    assert ch["algorithmic_bytes"] == 16.0 * n + 8.0 * (N + 1) * D
+    assert ch["implementation_bytes"] == 12.0 * n + (12.0 * n + 4.0 * Mr * D) + 4.0 * Mr * D
+    # the spreading kernel moves no algorithmic bytes of its own
+    slow = dict(stage_ms, spread=0.05)
+    assert bench.hbm_roofline(slow, n, D, N, Mr, False, {"hbm_gbs": 6792.7}, "m", ("c3", "bf16x3", "es"))["frac"] == 0.0
+    # FP64: complex128 coefficients
+    r64 = bench.hbm_roofline(stage_ms, n, D, N, Mr, True, {"hbm_gbs": 6792.7}, "m", ("c3", "fp64", "es"))
+    assert r64["algorithmic_bytes_per_launch"] == 16.0 * (N + 1) * D

@@ -87,3 +87,46 @@ def test_variance_closed_form_special_case():
     meta = {"n": 2, "step_cov": np.array([[0.3, 0.1], [0.1, 0.2]]), "step_mean": np.zeros(2)}
     E, Var = sigma_moments(meta, 1, "dirichlet")
     assert np.isclose(E[0, 0], 0.3) and np.isclose(Var[0, 0], 2 * 0.3 ** 2)
+
+
+@pytest.mark.parametrize("basis", ["dirichlet", "fejer"])
+def test_grid_pair_conditional_expectation_agrees_with_pair_sum(basis):
+    # the histogram-and-FFT closed form of E[Sigma | times] for the
+    # arrival-time experiment against the pairwise sum over returns with
+    # explicit step sets and mode-by-mode kernels
+    from stat_helpers import grid_pair_conditional_sigma, grid_pair_conditional_sigma_bruteforce
+    rng = np.random.default_rng(3)
+    C = np.array([[2.0, 0.7], [0.7, 1.5]])
+    m = np.array([0.3, -0.2])
+    for trial in range(4):
+        t1 = np.sort(rng.choice(80, size=14, replace=False))
+        t2 = np.sort(rng.choice(80, size=11, replace=False))
+        cut = [1, 3, 9, 17]
+        got = grid_pair_conditional_sigma(t1, t2, cut, basis, C, m)
+        for j, N in enumerate(cut):
+            want = grid_pair_conditional_sigma_bruteforce(t1, t2, N, basis, C, m)
+            assert np.allclose(got[j], want, rtol=1e-12, atol=1e-12), (trial, N, got[j], want)
+
+
+@pytest.mark.parametrize("basis", ["dirichlet", "fejer"])
+def test_oracle_epps_sigma_matches_conditional_expectation(basis):
+    # the arrival-time experiment (Sec. 4.1) at a short horizon: the oracle's
+    # Sigma minus its expectation given each replication's arrival times has
+    # mean zero within four standard errors
+    from stat_helpers import grid_pair_conditional_sigma
+    reps, T = 300, 1500
+    ev = synth.epps_replications(77, reps, T=T, rate=1 / 5)
+    C, m = ev.meta["step_cov"], ev.meta["step_mean"]
+    cut = [5, 30, 140]
+    res = np.zeros((reps, len(cut), 2, 2))
+    for r in range(reps):
+        a0, a1 = 2 * r, 2 * r + 2
+        o0, o1 = int(ev.offsets[a0]), int(ev.offsets[a1])
+        e = synth.Events(ev.offsets[a0:a1 + 1] - o0, ev.t[o0:o1], ev.logp[o0:o1])
+        E = grid_pair_conditional_sigma(e.asset(0)[0], e.asset(1)[0], cut, basis, C, m)
+        for j, N in enumerate(cut):
+            res[r, j] = oracle.estimate(e.offsets, e.t, e.logp, N=N, basis=basis)["Sigma"] - E[j]
+    for j, N in enumerate(cut):
+        for a, b in [(0, 0), (1, 1), (0, 1)]:
+            x = res[:, j, a, b]
+            assert abs(x.mean()) <= 4.0 * x.std(ddof=1) / np.sqrt(reps), (basis, N, a, b)
