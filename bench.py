@@ -77,9 +77,11 @@ def hbm_roofline(stage_ms, n_events, D, N, Mr, fp64, peaks, peak_src, traffic_ke
     coef = float(cb * (N + 1) * D)
     grid = float(gb * Mr * D)
     alg = {"prep": 16.0 * n_events, "spread": 0.0, "fft_cols": 0.0, "fft_rows": coef, "fft": coef,
-           "fused": 16.0 * n_events + coef, "gram": coef, "reduce": 0.0}
+           "fused": 16.0 * n_events + coef, "gram": coef, "reduce": 0.0, "split": 0.0}
+    # the pre-split contraction reads its operand planes (hi + lo: as many
+    # bytes as the complex64 coefficients) instead of the coefficients
     impl = {"prep": float(rb * n_events), "spread": rb * n_events + grid, "fft_cols": 2.0 * grid,
-            "fft_rows": grid, "fft": grid, "fused": 0.0, "gram": 0.0, "reduce": 0.0}
+            "fft_rows": grid, "fft": grid, "fused": 0.0, "gram": 0.0, "reduce": 0.0, "split": 2.0 * coef}
     timed = {k: v for k, v in stage_ms.items() if k != "setup" and v > 0}
     dom = max(timed, key=lambda k: timed[k])
     avg = timed[dom]
@@ -112,6 +114,8 @@ def parse():
                     help="c1: synchronous points per asset (N = n/2; 100000 is the paper's timing table)")
     ap.add_argument("--gram-d", type=int, default=500, help="gram: assets (the largest C5 request)")
     ap.add_argument("--gram-n", type=int, default=14400, help="gram: cutoff (C5's N_max)")
+    ap.add_argument("--gram-algo", default="default", choices=["default", "convert", "tma"],
+                    help="contraction variant (default: the library's choice for D)")
     ap.add_argument("--reps", type=int, default=4096, help="c4: Monte Carlo replications per step")
     ap.add_argument("--cutoffs", type=int, default=64, help="c4: cutoffs of the Epps sweep")
     ap.add_argument("--requests", type=int, default=10000, help="c5: requests in the stream")
@@ -593,7 +597,7 @@ def bench_gram(args):
     Fh = synth.gram_coefficients(0, D, N)
     F = torch.from_numpy(Fh).to(dev)
     plan = mm.mm_plan_create(D=D, N_max=N, max_events=0, tol=1e-6, kernel=args.kernel, basis="dirichlet",
-                             prec=args.prec)
+                             prec=args.prec, gram_algo=args.gram_algo)
     S = torch.empty((D, D), dtype=torch.float32, device=dev)
     R = torch.empty_like(S)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)  # inputs (57.6 MB) fit in L2
@@ -627,6 +631,8 @@ def bench_gram(args):
     mm.mm_profile_enable(plan, False)
     stages = mm.mm_profile_read(plan, reset=True)
     gram_ms = stages["gram"][0] / max(stages["gram"][1], 1)
+    split_ms = stages["split"][0] / max(stages["split"][1], 1)
+    gram_algo = {1: "convert", 2: "tma"}.get(mm.mm_plan_get_info(plan)["gram_algo"])
     Rg = R.double().cpu().numpy()
     mm.mm_destroy(plan)
     # FP64 GPU path on the same coefficients
@@ -662,21 +668,31 @@ def bench_gram(args):
     peaks, src = load_peaks()
     flops = 2.0 * D * D * 2.0 * (N + 1)  # the real product A A^T, A = D x 2(N + 1)
     tiles = (D + 127) // 128
-    executed = 3.0 * (tiles * (tiles + 1) // 2) * 128 * 128 * 2.0 * (((N + 1 + 31) // 32) * 64)
+    chunk = 32 if args.prec == "bf16x3" else 16  # complex modes per K-chunk
+    executed = 3.0 * (tiles * (tiles + 1) // 2) * 128 * 128 * 2.0 * (((N + 1 + chunk - 1) // chunk) * 2 * chunk)
     achieved = flops / (gram_ms * 1e-3) / 1e12
+    # a contraction takes the peak of its own operand type: tf32 from the
+    # measured bf16 peak by the nominal dense ratio (1.1 / 2.25 PFLOP/s)
+    peak = peaks["bf16_tflops"] * (1.0 if args.prec == "bf16x3" else 1.1 / 2.25)
+    peak_src = f"{src} bf16_tflops (burst)" + ("" if args.prec == "bf16x3" else " x 1.1/2.25 (nominal tf32 ratio)")
     line = {
         "metric": METRIC, "value": steps / (ms * 1e-3), "unit": "matrices/s", "n_gpus": 1, "steps": steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16" if args.prec == "bf16x3" else "tf32",
         "data": "synthetic (seeded complex Gaussian coefficients at the scale of one day of GBM returns)",
         "config": {"workload": f"gram_D{D}_N{N}", "D": D, "N": N, "contraction": args.prec, "basis": "dirichlet",
-                   "l2": "flushed between steps (256 MB write)", "gram_splits": i1["gram_splits"]},
-        "stage_ms": {"gram": gram_ms, "reduce": stages["reduce"][0] / max(stages["reduce"][1], 1)},
-        "roofline": {"kernel": "gram", "bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"],
-                     "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops"],
-                     "traffic": NCU_TRAFFIC.get(("gram", f"gram_D{D}_N{N}", args.prec, "es")),
-                     "peak_source": f"{src} bf16_tflops (burst)", "avg_launch_ms": gram_ms,
-                     "algorithmic_flops_per_launch": flops, "executed_tensor_flops_per_launch": executed},
+                   "l2": "flushed between steps (256 MB write)", "gram_splits": i1["gram_splits"],
+                   "gram_algo": gram_algo},
+        "stage_ms": {"split": split_ms, "gram": gram_ms, "reduce": stages["reduce"][0] / max(stages["reduce"][1], 1)},
+        "roofline": {"kernel": "gram", "bound": "tensor", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": (NCU_TRAFFIC.get(("gram", f"gram_D{D}_N{N}", args.prec, "es"))
+                                 if gram_algo == "convert" else None),
+                     "peak_source": peak_src, "avg_launch_ms": gram_ms,
+                     "algorithmic_flops_per_launch": flops, "executed_tensor_flops_per_launch": executed,
+                     "executed_tflops": executed / (gram_ms * 1e-3) / 1e12,
+                     "with_split_pass": {"ms": gram_ms + split_ms,
+                                         "achieved": flops / ((gram_ms + split_ms) * 1e-3) / 1e12}},
         "fp64_gpu_path": {"matrices_per_s": 1e3 / ms64, "max_abs_dcorr": dcorr},
         "cpu_baseline": {"value": cpu_rate, "unit": "matrices/s", "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": f"the oracle's contraction (Algorithm 3 step C) of {ds} of {D} assets at "

@@ -120,7 +120,14 @@ typedef struct {
                            form their terms of both classes' modes and combine them
                            in the output, ordered by a per-asset counter). The FP64
                            path always uses 1. All compute Eqs. (13)-(14). */
-  int32_t reserved[4];  /* must be zero */
+  int32_t gram_algo;    /* stage (d) in the mixed precisions: 0 library default (2 from
+                           192 assets up, else 1); 1 each CTA converts its
+                           tiles of the weighted coefficients to split precision in
+                           registers; 2 a streaming pass writes the weighted operand once
+                           as hi and lo planes and the contraction loads them by TMA
+                           (warp-specialised producer / MMA / epilogue). Both compute
+                           Eqs. (2)/(3) with the same split products. */
+  int32_t reserved[3];  /* must be zero */
 } mm_plan_desc;
 
 typedef struct mm_plan_s* mm_plan;
@@ -129,7 +136,8 @@ typedef struct mm_plan_s* mm_plan;
  * launching stream, summed since the last reset). */
 enum { MM_STAGE_PREP = 0, MM_STAGE_SPREAD = 1, MM_STAGE_FFT_COLS = 2, MM_STAGE_FFT_ROWS = 3,
        MM_STAGE_GRAM = 4, MM_STAGE_REDUCE = 5, MM_STAGE_SETUP = 6, MM_STAGE_FUSED = 7, MM_STAGE_FFT = 8,
-       MM_NUM_STAGES = 9 };
+       MM_STAGE_SPLIT = 9, /* the contraction operand's pre-split pass */
+       MM_NUM_STAGES = 10 };
 
 typedef struct {
   int32_t msp;           /* spreading half-width M_sp */
@@ -154,6 +162,9 @@ typedef struct {
                             (error <= max(3e-7, tol/10)) and accumulates exactly in integers */
   int32_t graphs;        /* 1: steady mm_estimate calls replay a captured CUDA graph */
   int64_t graph_launches; /* mm_estimate calls served by a graph replay since creation */
+  int32_t gram_algo;     /* stage (d) of the last contraction: 1 in-register conversion,
+                            2 pre-split operand by TMA, 3 FP64 path; 0 before the first */
+  int32_t reserved_info;
 } mm_plan_info;
 
 /* Create a plan: validates desc, allocates the workspace on the current

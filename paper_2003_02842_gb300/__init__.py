@@ -102,18 +102,19 @@ def _dptr(x, dtype, name, device=True):
 
 
 def mm_plan_create(D, N_max, max_events=0, tol=1e-6, kernel="es", basis="dirichlet", prec="bf16x3",
-                   spread_tile=0, spread_algo="default", fft_algo="default") -> Plan:
+                   spread_tile=0, spread_algo="default", fft_algo="default", gram_algo="default") -> Plan:
     d = _lib.PlanDesc()
     d.D, d.N_max, d.max_events, d.tol = int(D), int(N_max), int(max_events), float(tol)
     d.kernel, d.basis, d.prec = KERNELS[kernel], BASES[basis], PRECISIONS[prec]
     d.spread_tile = int(spread_tile)
     d.spread_algo = _lib.SPREAD_ALGOS[spread_algo]
     d.fft_algo = _lib.FFT_ALGOS[fft_algo]
+    d.gram_algo = _lib.GRAM_ALGOS[gram_algo]
     h = ctypes.c_void_p()
     _check(_lib.load().mm_plan_create(ctypes.byref(d), ctypes.byref(h)), "mm_plan_create")
     return Plan(h, dict(D=int(D), N_max=int(N_max), max_events=int(max_events), tol=float(tol), kernel=kernel,
                         basis=basis, prec=prec, spread_tile=int(spread_tile), spread_algo=spread_algo,
-                        fft_algo=fft_algo))
+                        fft_algo=fft_algo, gram_algo=gram_algo))
 
 
 def mm_destroy(plan: Plan):

@@ -22,9 +22,10 @@ KERNELS = {"gauss": 0, "kb": 1, "es": 2}
 BASES = {"dirichlet": 0, "fejer": 1}
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "3xtf32": 2}
 SPREAD_ALGOS = {"default": 0, "scatter": 1, "gather": 2, "fused": 3, "scatter_direct": 4}
+GRAM_ALGOS = {"default": 0, "convert": 1, "tma": 2}
 FFT_ALGOS = {"default": 0, "two_pass": 1, "asset": 2, "asset_split": 3, "asset_pair": 4, "asset_perm": 5,
              "asset_split3": 6}
-STAGES = ["prep", "spread", "fft_cols", "fft_rows", "gram", "reduce", "setup", "fused", "fft"]
+STAGES = ["prep", "spread", "fft_cols", "fft_rows", "gram", "reduce", "setup", "fused", "fft", "split"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -39,7 +40,8 @@ class PlanDesc(ctypes.Structure):
         ("spread_tile", ctypes.c_int32),
         ("spread_algo", ctypes.c_int32),
         ("fft_algo", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("gram_algo", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -65,6 +67,8 @@ class PlanInfo(ctypes.Structure):
         ("spread_poly", ctypes.c_int32),
         ("graphs", ctypes.c_int32),
         ("graph_launches", ctypes.c_int64),
+        ("gram_algo", ctypes.c_int32),
+        ("reserved_info", ctypes.c_int32),
     ]
 
 

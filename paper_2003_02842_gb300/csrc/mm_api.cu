@@ -20,6 +20,7 @@ namespace {
 constexpr int kSMs = 152;           // GB300: 2 dies x 76 SMs
 constexpr int kGlNodes = 128;       // Gauss-Legendre nodes for the ES transform
 constexpr int kMaxGramCtas = 2 * kSMs;
+constexpr int kGramTmaMinAssets = 192;  // default switch to the pre-split contraction
 
 struct Prof {
   int stage;
@@ -260,6 +261,9 @@ struct mm_plan_s {
   void* partial = nullptr;        // FP64 path: per-split partial tiles
   size_t partial_bytes = 0;
   float* acc[2] = {nullptr, nullptr};  // mixed path: FP32 accumulators, used alternately
+  void* tma_hi = nullptr;         // mixed path, pre-split contraction: operand hi and lo planes
+  void* tma_lo = nullptr;         // (Dpad x kpc complex modes, pad rows zero)
+  int gram_used = 0;              // contraction variant of the last call (mm_plan_info.gram_algo)
   int* gram_done = nullptr;       // contraction CTAs finished (the last one runs the epilogue)
   int* fft_sync = nullptr;        // per asset: arrival counter and flag of the three-CTA FFT split
   int* pw_N = nullptr;            // pairwise-cutoff covariance: per-asset cutoffs,
@@ -350,7 +354,7 @@ void free_all(mm_plan p) {
   void* ptrs[] = {p->grid, p->rec_b0, p->rec_d, p->rec_v, p->W, p->atw, p->U, p->decon, p->glx, p->glw, p->bounds, p->gscale, p->status, p->gapbits, p->wsq,
                   p->partial, p->acc[0], p->acc[1], p->gram_done, p->fft_sync, p->pw_N, p->pw_sig, p->pw_A,
                   p->pw_V, p->pw_clip, p->s_off, p->s_t, p->s_p, p->s_coef,
-                  p->s_sigma, p->s_R, p->asset_order};
+                  p->s_sigma, p->s_R, p->asset_order, p->tma_hi, p->tma_lo};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->h_status) cudaFreeHost(p->h_status);
@@ -602,6 +606,14 @@ mm_status check_plan(mm_plan p) {
   return MM_OK;
 }
 
+// Stage (d) by the pre-split operand and TMA (mixed precisions, single
+// problems): on request, or by default from kGramTmaMinAssets assets up.
+bool gram_uses_tma(mm_plan p) {
+  if (p->fp64 || p->batch) return false;
+  if (p->desc.gram_algo != 0) return p->desc.gram_algo == 2;
+  return p->D >= kGramTmaMinAssets;
+}
+
 GramParams gram_params(mm_plan p, int N) {
   GramParams g{};
   g.wait_ns = p->wait_ns;
@@ -742,6 +754,7 @@ mm_status corr_impl(mm_plan p, const void* coeffs, int N, void* sigma, void* R, 
     p->w_basis = p->desc.basis;
   }
   if (p->fp64) {
+    p->gram_used = 3;
     {
       StageScope sc(p, MM_STAGE_GRAM, st);
       MM_CUDA(launch_gram_f64(coeffs, g, (const double*)p->wsq, (double*)p->partial, st));
@@ -759,14 +772,24 @@ mm_status corr_impl(mm_plan p, const void* coeffs, int N, void* sigma, void* R, 
     float* cur = p->acc[p->acc_sel];
     float* next = p->acc[p->acc_sel ^ 1];
     p->acc_dirty = true;  // until both launches below are queued
+    const int mode = p->desc.prec == MM_PREC_MIXED_BF16X3 ? 0 : 1;
     // few assets: the last contraction CTA writes Sigma and R itself (one
     // launch less); beyond that the separate epilogue's parallelism wins
-    const bool fuse = g.D <= 32 && R;
-    {
+    const bool tma = gram_uses_tma(p);
+    const bool fuse = !tma && g.D <= 32 && R;
+    if (tma) {
+      {
+        StageScope sc(p, MM_STAGE_SPLIT, st);
+        MM_CUDA(launch_gram_split(mode, coeffs, g, (const float*)p->wsq, p->tma_hi, p->tma_lo, st));
+      }
       StageScope sc(p, MM_STAGE_GRAM, st);
-      MM_CUDA(launch_gram_tc(p->desc.prec == MM_PREC_MIXED_BF16X3 ? 0 : 1, coeffs, g, (const float*)p->wsq, cur,
-                             p->status, fuse ? p->gram_done : nullptr, (float*)sigma, (float*)R, next, st));
+      MM_CUDA(launch_gram_tma(mode, g, p->tma_hi, p->tma_lo, cur, p->status, st));
+    } else {
+      StageScope sc(p, MM_STAGE_GRAM, st);
+      MM_CUDA(launch_gram_tc(mode, coeffs, g, (const float*)p->wsq, cur, p->status, fuse ? p->gram_done : nullptr,
+                             (float*)sigma, (float*)R, next, st));
     }
+    p->gram_used = tma ? 2 : 1;
     if (!fuse) {
       StageScope sc(p, MM_STAGE_REDUCE, st);
       MM_CUDA(launch_corr_acc(cur, g, (float*)sigma, (float*)R, next, p->status, st));
@@ -903,7 +926,8 @@ mm_status plan_create_impl(const mm_plan_desc* desc, int gsize, bool batch, mm_p
   if (d.spread_tile < 0 || d.spread_tile > 50000) return MM_ERR_INVALID_ARG;
   if (d.spread_algo < 0 || d.spread_algo > 4) return MM_ERR_INVALID_ARG;
   if (d.fft_algo < 0 || d.fft_algo > 6) return MM_ERR_INVALID_ARG;
-  for (int i = 0; i < 4; ++i)
+  if (d.gram_algo < 0 || d.gram_algo > 2) return MM_ERR_INVALID_ARG;
+  for (int i = 0; i < 3; ++i)
     if (d.reserved[i] != 0) return MM_ERR_INVALID_ARG;
   const int msp = msp_rule(d.kernel, d.tol);
   if (msp < 1 || msp > 30) return MM_ERR_UNSUPPORTED;
@@ -968,6 +992,13 @@ mm_status plan_create_impl(const mm_plan_desc* desc, int gsize, bool batch, mm_p
       A((void**)&p->acc[0], D * (size_t)g.Dp * sizeof(float));
       A((void**)&p->acc[1], D * (size_t)g.Dp * sizeof(float));
       A((void**)&p->gram_done, sizeof(int));
+      if (gram_uses_tma(p)) {
+        const size_t pb = gram_tma_plane_bytes(d.prec == MM_PREC_MIXED_BF16X3 ? 0 : 1, d.D, d.N_max, g.chunk);
+        A(&p->tma_hi, pb);
+        A(&p->tma_lo, pb);
+        if (r == MM_OK && (cudaMemset(p->tma_hi, 0, pb) != cudaSuccess || cudaMemset(p->tma_lo, 0, pb) != cudaSuccess))
+          r = MM_ERR_CUDA;
+      }
     }
   }
   if (d.max_events > 0 && !batch && staging) {
@@ -1316,6 +1347,7 @@ mm_status mm_plan_get_info(mm_plan p, mm_plan_info* info) {
   info->fft_split = p->use_afft ? (p->afft.pair ? 3 : p->afft.split == 3 ? 4 : p->afft.split) : 0;
   info->graphs = p->graphs ? 1 : 0;
   info->graph_launches = p->graph_launches;
+  info->gram_algo = p->gram_used;
   for (int q = 0; q < 4; ++q) info->fft_radix[q] = p->use_afft && q < p->afft.npass ? p->afft.rad[q] : 0;
   return MM_OK;
 }

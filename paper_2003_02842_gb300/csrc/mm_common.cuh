@@ -235,6 +235,14 @@ cudaError_t launch_corr_acc(const float* acc, const GramParams& g, float* sigma,
 cudaError_t launch_reduce_corr(bool fp64, const void* partial, const GramParams& g,
                                void* sigma, void* R, int* status, cudaStream_t s);
 size_t gram_tc_smem(int mode, bool two_tiles);
+// Pre-split contraction (mm_gram_tma.cu): the operand's hi and lo planes
+// (gram_tma_plane_bytes each, for D assets up to N_max), the split pass, and
+// the TMA-fed contraction into the FP32 accumulator.
+size_t gram_tma_plane_bytes(int mode, int D, int N_max, int chunk);
+cudaError_t launch_gram_split(int mode, const void* coeffs, const GramParams& g, const float* wsq, void* hi,
+                              void* lo, cudaStream_t s);
+cudaError_t launch_gram_tma(int mode, const GramParams& g, void* hi, void* lo, float* acc, int* status,
+                            cudaStream_t s);
 int epps_max_assets();
 
 // Plan internals used by the serving engine (mm_server.cu).

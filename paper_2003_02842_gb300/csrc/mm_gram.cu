@@ -27,6 +27,7 @@
 
 #include "mm_async.cuh"
 #include "mm_common.cuh"
+#include "mm_tc.cuh"
 
 namespace mmgpu {
 
@@ -46,16 +47,6 @@ cudaError_t launch_gram_weights(int basis, int N, bool fp64, void* wsq, cudaStre
   if (fp64) k_gram_weights<double><<<blocks, 256, 0, s>>>(basis, N, (double*)wsq);
   else k_gram_weights<float><<<blocks, 256, 0, s>>>(basis, N, (float*)wsq);
   return cudaGetLastError();
-}
-
-__device__ __forceinline__ void pair_of(int p, int nt, int& I, int& J) {
-  int i = 0;
-  while (p >= nt - i) {
-    p -= nt - i;
-    ++i;
-  }
-  I = i;
-  J = i + p;
 }
 
 // ------------------------------------------------------------ FP64 path
@@ -117,59 +108,9 @@ cudaError_t launch_gram_f64(const void* coeffs, const GramParams& g, const doubl
 }
 
 // ------------------------------------------------------------ tcgen05 path
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor: K-major operand in the canonical
-// 128-byte-swizzle layout (8-row atoms of 128-byte rows, atoms 1024 B apart).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);        // start address
-  d |= (uint64_t)1 << 16;                           // leading byte offset (unused for this layout)
-  d |= (uint64_t)(1024u >> 4) << 32;                // stride byte offset: next 8-row atom
-  d |= (uint64_t)1 << 46;                           // descriptor version
-  d |= (uint64_t)2 << 61;                           // 128-byte swizzle
-  return d;
-}
-
-template <int MODE>
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  if (MODE == 0) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-  }
-}
-__device__ __forceinline__ void tc_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ uint32_t f32_to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-
 constexpr int kTcThreads = 512;
 constexpr int kTcWarps = kTcThreads / 32;
 constexpr int kRowsPerWarp = 128 / kTcWarps;  // operand rows a warp converts
-constexpr int kTile = 128;                 // rows per operand tile
-constexpr int kTileBytes = kTile * 128;    // 128-byte rows
-constexpr uint32_t kTmemCols = 128;
 
 size_t gram_tc_smem(int, bool two_tiles) {
   return (size_t)2 /*stages*/ * (two_tiles ? 4 : 2) * kTileBytes + 1024 /*alignment slack*/;
@@ -241,12 +182,6 @@ __device__ __forceinline__ void store_chunk(const Chunk<MODE>& c, uint8_t* hi, u
       *reinterpret_cast<uint2*>(lo + off) = make_uint2(lr, li);
     }
   }
-}
-
-__device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
-  asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c),
-               "f"(d)
-               : "memory");
 }
 
 // One CTA per (output tile pair I <= J, K-split): the split's partial

@@ -60,8 +60,11 @@ def test_reserved_fields_must_be_zero(lib):
     from paper_2003_02842_gb300 import _lib
     d = _lib.PlanDesc()
     d.D, d.N_max, d.max_events, d.tol, d.kernel, d.basis, d.prec = 4, 10, 100, 1e-6, 2, 0, 1
-    d.reserved[3] = 1
+    d.reserved[2] = 1
     h = ctypes.c_void_p()
+    assert lib.mm_plan_create(ctypes.byref(d), ctypes.byref(h)) == 1
+    d.reserved[2] = 0
+    d.gram_algo = 3  # no such contraction variant
     assert lib.mm_plan_create(ctypes.byref(d), ctypes.byref(h)) == 1
 
 

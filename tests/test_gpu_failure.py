@@ -25,15 +25,20 @@ def _built():
     g.build()
 
 
+@pytest.mark.parametrize("gram", ["convert", "tma"])
 @pytest.mark.parametrize("prec", ["bf16x3", "3xtf32"])
 @pytest.mark.parametrize("D", [20, 100, 200])
-def test_contraction_wait_gives_up_and_the_plan_recovers(prec, D):
-    # D = 20: the contraction's last CTA writes Sigma and R itself; D = 100:
-    # one output tile and the separate epilogue; D = 200: several tiles
+def test_contraction_wait_gives_up_and_the_plan_recovers(prec, D, gram):
+    # D = 20: the contraction's last CTA writes Sigma and R itself (the
+    # in-register variant); D = 100: one output tile and the separate
+    # epilogue; D = 200: several tiles. Both contraction variants: the
+    # in-register one and the warp-specialised one fed by TMA (whose producer
+    # and MMA threads both give up and wait for their copies and MMAs)
     import paper_2003_02842_gb300 as mm
     ev = synth.random_events(70 + D, D=D, n_range=(30, 300), T=6000.0)
     N = 400
-    plan = mm.mm_plan_create(D=D, N_max=N, max_events=ev.n_events, tol=1e-6, kernel="es", basis="fejer", prec=prec)
+    plan = mm.mm_plan_create(D=D, N_max=N, max_events=ev.n_events, tol=1e-6, kernel="es", basis="fejer", prec=prec,
+                             gram_algo=gram)
     off, t, p = to_dev(ev)
     F, _ = mm.mm_coeffs(plan, off, t, p, N)
     assert mm.mm_plan_sync(plan) == 0

@@ -441,3 +441,39 @@ def test_covariance_call_without_correlation(prec, D):
         # split-K partial sums reach the accumulator in any order: equal to rounding
         assert sigma_err(S2.cpu().numpy().astype(np.float64), Sg) <= (1e-12 if prec == "fp64" else 1e-6)
         mm.mm_destroy(plan)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "3xtf32"])
+@pytest.mark.parametrize("D", [1, 100, 130, 300])
+def test_pre_split_tma_contraction(prec, D):
+    # stage (d) from the pre-split operand planes loaded by TMA: one tile,
+    # a ragged second tile, several tile pairs; cutoffs on and off the
+    # K-chunk boundaries, both bases, repeated calls (the accumulators
+    # alternate); against the oracle and the in-register variant
+    import paper_2003_02842_gb300 as mm
+    ev = synth.random_events(81 + D, D=D, n_range=(2, 200), T=5000.0)
+    tl = TOL[prec]
+    off, t, p = to_dev(ev)
+    for basis in ("dirichlet", "fejer"):
+        plan = mm.mm_plan_create(D=D, N_max=700, max_events=ev.n_events, tol=tl["tol"], kernel="es", basis=basis,
+                                 prec=prec, gram_algo="tma")
+        conv = mm.mm_plan_create(D=D, N_max=700, max_events=ev.n_events, tol=tl["tol"], kernel="es", basis=basis,
+                                 prec=prec, gram_algo="convert")
+        for N in (700, 31, 32, 1, 511):
+            F, _ = mm.mm_coeffs(plan, off, t, p, N)
+            S, R = mm.mm_corr(plan, F, N)
+            S2, R2 = mm.mm_corr(conv, F, N)
+            assert mm.mm_plan_sync(plan) == 0 or D < 3  # tiny random assets may lack returns
+            mm.mm_plan_sync(conv)
+            assert mm.mm_plan_get_info(plan)["gram_algo"] == 2 and mm.mm_plan_get_info(conv)["gram_algo"] == 1
+            ref = oracle.estimate(ev.offsets, ev.t, ev.logp, N=N, basis=basis)
+            Sg = S.cpu().numpy().astype(np.float64)
+            assert sigma_err(Sg, ref["Sigma"]) <= tl["sig"], (basis, N)
+            assert sigma_err(Sg, S2.cpu().numpy().astype(np.float64)) <= tl["sig"], (basis, N)
+            ok = np.diag(ref["Sigma"]) > 0
+            sub = np.ix_(ok, ok)
+            Rg = R.cpu().numpy().astype(np.float64)
+            assert np.max(np.abs(Rg[sub] - ref["R"][sub])) <= tl["R"], (basis, N)
+            assert np.array_equal(Sg, Sg.T) and np.array_equal(Rg, Rg.T, equal_nan=True)
+        mm.mm_destroy(plan)
+        mm.mm_destroy(conv)
