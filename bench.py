@@ -41,8 +41,9 @@ NCU_TRAFFIC = {
     ("fft", "c3", "bf16x3", "es"): 16451584,
     ("prep", "c3", "bf16x3", "es"): 12287488,
     ("gram", "c3", "bf16x3", "es"): 8115712,
-    # the contraction alone at D = 500, N = 14400 (profiles/gram_D500_N14400_kernel_ncu.md)
-    ("gram", "gram_D500_N14400", "bf16x3", "es"): 59650560,
+    # the pre-split contraction alone at D = 500, N = 14400
+    # (profiles/gram_D500_N14400_kernel_ncu.md)
+    ("gram", "gram_D500_N14400", "bf16x3", "es", "tma"): 60790272,
 }
 NCU_SOURCE = {
     "c3": "profiles/c3_block_D100_N10000_kernels_ncu.md",
@@ -686,8 +687,8 @@ def bench_gram(args):
         "stage_ms": {"split": split_ms, "gram": gram_ms, "reduce": stages["reduce"][0] / max(stages["reduce"][1], 1)},
         "roofline": {"kernel": "gram", "bound": "tensor", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": (NCU_TRAFFIC.get(("gram", f"gram_D{D}_N{N}", args.prec, "es"))
-                                 if gram_algo == "convert" else None),
+                     "traffic": NCU_TRAFFIC.get(("gram", f"gram_D{D}_N{N}", args.prec, "es", gram_algo)),
+                     "traffic_source": NCU_SOURCE.get(f"gram_D{D}_N{N}"),
                      "peak_source": peak_src, "avg_launch_ms": gram_ms,
                      "algorithmic_flops_per_launch": flops, "executed_tensor_flops_per_launch": executed,
                      "executed_tflops": executed / (gram_ms * 1e-3) / 1e12,

@@ -634,6 +634,9 @@ GramParams gram_params(mm_plan p, int N) {
     const double tile_bytes = (double)g.tile * g.tile * 8.0;
     const int s_traffic = (int)std::max(1.0, ceil(a_bytes / (4.0 * g.npairs * tile_bytes)));
     S = std::max(1, std::min({g.nchunks, std::max(1, kMaxGramCtas / g.npairs), s_traffic}));
+  } else if (gram_uses_tma(p)) {
+    // one CTA per SM (its stage ring fills the shared memory): one wave
+    S = std::max(1, std::min((g.nchunks + 1) / 2, std::max(1, kSMs / g.npairs)));
   } else {
     // about two CTAs per SM, at least two K-chunks each (the partial sums meet
     // in L2 through vector reductions, so more splits cost little traffic)

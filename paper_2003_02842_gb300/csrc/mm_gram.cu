@@ -187,13 +187,27 @@ __device__ __forceinline__ void store_chunk(const Chunk<MODE>& c, uint8_t* hi, u
 // One CTA per (output tile pair I <= J, K-split): the split's partial
 // 128 x 128 product accumulates in TMEM and is then added into the FP32
 // accumulator acc (row stride Dp) with vector reductions in L2.
+// 1 / sqrt(v) in float64 for a float32 v > 0: the single-precision
+// reciprocal square root as a seed (relative error below 2^-21), then two
+// Newton-Raphson steps y <- y (3 - v y^2) / 2, each of which squares the
+// relative error (to below 2^-40, then to float64 rounding). GB300 runs
+// float64 at a small fraction of the float32 rate, and its float64 square
+// root and division are long instruction sequences.
+__device__ __forceinline__ double inv_sqrt_f64(float v) {
+  const double x = (double)v;
+  double y = (double)rsqrtf(v);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  return y;
+}
+
 // Sigma and R from the accumulator by one CTA (the last split to finish):
 // the same arithmetic as k_corr_acc, block-strided over the D x Dp entries.
 __device__ void corr_epilogue_block(const float* __restrict__ acc, const GramParams& g, float* __restrict__ sigma,
                                     float* __restrict__ R, float* __restrict__ zero_next, double* s_inv, int* status) {
   for (int d = threadIdx.x; d < g.D; d += blockDim.x) {
-    const double v = __ldcg(acc + (int64_t)d * g.Dp + d);
-    s_inv[d] = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
+    const float v = __ldcg(acc + (int64_t)d * g.Dp + d);
+    s_inv[d] = v > 0.0f ? inv_sqrt_f64(v) : 0.0;
   }
   __syncthreads();
   bool zero = false;
@@ -408,8 +422,8 @@ __global__ void __launch_bounds__(256) k_corr_acc(const float* __restrict__ acc,
     const int d = (threadIdx.x < 16 ? blockIdx.y : blockIdx.x) * 16 + q;
     double inv = 0.0;
     if (d < g.D) {
-      const double v = acc[(int64_t)d * g.Dp + d];
-      inv = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
+      const float v = acc[(int64_t)d * g.Dp + d];
+      inv = v > 0.0f ? inv_sqrt_f64(v) : 0.0;
     }
     if (threadIdx.x < 16) s_inv_i[q] = inv;
     else s_inv_j[q] = inv;

@@ -38,7 +38,11 @@ namespace mmgpu {
 
 // ------------------------------------------------------------ split pass
 // Row a of the operand: complex mode k -> elements 2k, 2k+1 of both planes;
-// modes N < k < kpc are zero.
+// modes N < k < kpc are zero. Each thread takes four consecutive modes: four
+// 8-byte coefficient loads in flight and one 16-byte store per plane (bf16)
+// or two (tf32); kpc is a multiple of 16, so a row's quads never straddle.
+constexpr int kSplitModes = 4;
+
 template <int MODE>
 __global__ void __launch_bounds__(256) k_gram_split(const float2* __restrict__ F, GramParams g,
                                                     const float* __restrict__ wsq, void* __restrict__ hi,
@@ -46,26 +50,49 @@ __global__ void __launch_bounds__(256) k_gram_split(const float2* __restrict__ F
   pdl_wait();  // the coefficients come from the FFT kernel
   pdl_trigger();
   const int a = blockIdx.y;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= kpc) return;
-  float xr = 0.f, xi = 0.f;
-  if (k <= g.N) {
-    const float s = __ldg(wsq + k);
-    const float2 f = __ldg(F + (int64_t)a * g.ld + k);
-    xr = f.x * s;
-    xi = f.y * s;
+  const int k0 = (blockIdx.x * blockDim.x + threadIdx.x) * kSplitModes;
+  if (k0 >= kpc) return;
+  float xr[kSplitModes], xi[kSplitModes];
+  const float2* row = F + (int64_t)a * g.ld;
+#pragma unroll
+  for (int q = 0; q < kSplitModes; ++q) {
+    const int k = k0 + q;
+    xr[q] = 0.f;
+    xi[q] = 0.f;
+    if (k <= g.N) {
+      const float sc = __ldg(wsq + k);
+      const float2 f = __ldg(row + k);
+      xr[q] = f.x * sc;
+      xi[q] = f.y * sc;
+    }
   }
-  const int64_t o = (int64_t)a * kpc + k;
+  const int64_t o = (int64_t)a * kpc + k0;  // in complex modes
   if (MODE == 0) {
-    const __nv_bfloat162 H = __floats2bfloat162_rn(xr, xi);
-    const __nv_bfloat162 L = __floats2bfloat162_rn(xr - __low2float(H), xi - __high2float(H));
-    reinterpret_cast<__nv_bfloat162*>(hi)[o] = H;
-    reinterpret_cast<__nv_bfloat162*>(lo)[o] = L;
+    uint32_t h[kSplitModes], l[kSplitModes];
+#pragma unroll
+    for (int q = 0; q < kSplitModes; ++q) {
+      const __nv_bfloat162 H = __floats2bfloat162_rn(xr[q], xi[q]);
+      const __nv_bfloat162 L = __floats2bfloat162_rn(xr[q] - __low2float(H), xi[q] - __high2float(H));
+      h[q] = *reinterpret_cast<const uint32_t*>(&H);
+      l[q] = *reinterpret_cast<const uint32_t*>(&L);
+    }
+    reinterpret_cast<uint4*>(reinterpret_cast<uint32_t*>(hi) + o)[0] = make_uint4(h[0], h[1], h[2], h[3]);
+    reinterpret_cast<uint4*>(reinterpret_cast<uint32_t*>(lo) + o)[0] = make_uint4(l[0], l[1], l[2], l[3]);
   } else {
-    const uint32_t hr = f32_to_tf32(xr), hi_ = f32_to_tf32(xi);
-    reinterpret_cast<uint2*>(hi)[o] = make_uint2(hr, hi_);
-    reinterpret_cast<uint2*>(lo)[o] = make_uint2(f32_to_tf32(xr - __uint_as_float(hr)),
-                                                 f32_to_tf32(xi - __uint_as_float(hi_)));
+    uint32_t h[2 * kSplitModes], l[2 * kSplitModes];
+#pragma unroll
+    for (int q = 0; q < kSplitModes; ++q) {
+      h[2 * q] = f32_to_tf32(xr[q]);
+      h[2 * q + 1] = f32_to_tf32(xi[q]);
+      l[2 * q] = f32_to_tf32(xr[q] - __uint_as_float(h[2 * q]));
+      l[2 * q + 1] = f32_to_tf32(xi[q] - __uint_as_float(h[2 * q + 1]));
+    }
+    uint4* hp = reinterpret_cast<uint4*>(reinterpret_cast<uint2*>(hi) + o);
+    uint4* lp = reinterpret_cast<uint4*>(reinterpret_cast<uint2*>(lo) + o);
+    hp[0] = make_uint4(h[0], h[1], h[2], h[3]);
+    hp[1] = make_uint4(h[4], h[5], h[6], h[7]);
+    lp[0] = make_uint4(l[0], l[1], l[2], l[3]);
+    lp[1] = make_uint4(l[4], l[5], l[6], l[7]);
   }
 }
 
@@ -267,7 +294,7 @@ size_t gram_tma_plane_bytes(int mode, int D, int N_max, int chunk) {
 cudaError_t launch_gram_split(int mode, const void* coeffs, const GramParams& g, const float* wsq, void* hi, void* lo,
                               cudaStream_t s) {
   const int kpc = gram_tma_kpc(g);
-  dim3 grd((kpc + 255) / 256, g.D);
+  dim3 grd((kpc / kSplitModes + 255) / 256, g.D);
   if (mode == 0)
     return launch_pdl(k_gram_split<0>, grd, dim3(256), 0, s, (const float2*)coeffs, g, wsq, hi, lo, kpc);
   return launch_pdl(k_gram_split<1>, grd, dim3(256), 0, s, (const float2*)coeffs, g, wsq, hi, lo, kpc);
