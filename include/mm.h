@@ -349,7 +349,10 @@ typedef struct {
   mm_basis basis;
   mm_precision prec;     /* MM_PREC_MIXED_*: stages (a)-(c) in float32; the sweep
                             contraction accumulates in float32 on the CUDA cores
-                            (D <= 12 makes it memory-bound), normalised in float64 */
+                            (D <= 12 makes it memory-bound), normalised in float64.
+                            MM_PREC_FP64: the same form in float64 throughout
+                            (complex128 coefficients, float64 Sigma and R): the
+                            mixed form's comparator */
   int32_t reserved[5];   /* must be zero */
 } mm_batch_desc;
 
@@ -370,13 +373,13 @@ typedef struct {
 
 /* Create a batch: validates desc and allocates the workspace of reps * D
  * assets (grids, coefficients at N_max, tables) on the current device.
- * MM_ERR_UNSUPPORTED for FP64 or D > 12. */
+ * MM_ERR_UNSUPPORTED for D > 12. */
 mm_status mm_batch_create(const mm_batch_desc* desc, mm_batch* out);
 mm_status mm_batch_destroy(mm_batch batch);
 
 /* Sweep: h_cutoffs (host, n_cutoffs <= 128, strictly increasing, each in
  * [0 or 1 (Fejer), N_max]); d_R and d_sigma_or_null receive
- * reps * n_cutoffs * D * D floats. Asynchronous on stream (a change of
+ * reps * n_cutoffs * D * D floats (doubles for MM_PREC_FP64). Asynchronous on stream (a change of
  * cutoffs synchronises it once); device-side errors are reported by
  * mm_batch_sync. */
 mm_status mm_batch_epps(mm_batch batch, const int64_t* d_offsets, const double* d_t, const double* d_logp,
@@ -388,12 +391,12 @@ mm_status mm_batch_epps(mm_batch batch, const int64_t* d_offsets, const double* 
 mm_status mm_batch_autotune(mm_batch batch, const int64_t* d_offsets, const double* d_t, const double* d_logp,
                             int32_t N, int32_t reps, void* stream);
 
-/* Device pointer to the coefficients of the last sweep (complex64,
- * [reps * D][*ld], F-convention, k = 0..N_J) and their row stride. Valid
- * until the next call; owned by the batch. */
+/* Device pointer to the coefficients of the last sweep (complex64, or
+ * complex128 for MM_PREC_FP64; [reps * D][*ld], F-convention, k = 0..N_J)
+ * and their row stride. Valid until the next call; owned by the batch. */
 mm_status mm_batch_coeffs(mm_batch batch, const void** d_coeffs, int32_t* ld);
 
-/* Copy those coefficients (reps * D * ld complex64) into d_dst on stream. */
+/* Copy those coefficients (reps * D * ld complex64 or complex128) into d_dst on stream. */
 mm_status mm_batch_copy_coeffs(mm_batch batch, void* d_dst, void* stream);
 
 /* Per-stage timing of the batch's launches, as mm_profile_enable /

@@ -384,23 +384,25 @@ def mm_batch_destroy(batch: Batch):
 
 def mm_batch_epps(batch, offsets, t, logp, cutoffs, sigma=True, R=None, stream=None):
     """Covariance / correlation of every problem at every cutoff (ascending).
-    Returns (Sigma or None, R), each [reps, len(cutoffs), D, D] float32."""
+    Returns (Sigma or None, R), each [reps, len(cutoffs), D, D] float32
+    (float64 for an FP64 batch)."""
     torch = _torch()
     reps, D = batch.desc["reps"], batch.desc["D"]
     J = len(cutoffs)
     cut = (ctypes.c_int32 * J)(*[int(x) for x in cutoffs])
     dev = t.device
+    dt = torch.float64 if batch.desc["prec"] == "fp64" else torch.float32
     if R is None:
-        R = torch.empty((reps, J, D, D), dtype=torch.float32, device=dev)
+        R = torch.empty((reps, J, D, D), dtype=dt, device=dev)
     if sigma is True:
-        S = torch.empty((reps, J, D, D), dtype=torch.float32, device=dev)
+        S = torch.empty((reps, J, D, D), dtype=dt, device=dev)
     elif sigma is None or sigma is False:
         S = None
     else:
         S = sigma
-    ps = _dptr(S, torch.float32, "sigma") if S is not None else ctypes.c_void_p(0)
+    ps = _dptr(S, dt, "sigma") if S is not None else ctypes.c_void_p(0)
     po, pt, pp = _events(offsets, t, logp)
-    _check(_lib.load().mm_batch_epps(batch.handle, po, pt, pp, cut, J, ps, _dptr(R, torch.float32, "R"),
+    _check(_lib.load().mm_batch_epps(batch.handle, po, pt, pp, cut, J, ps, _dptr(R, dt, "R"),
                                      _stream(stream)), "mm_batch_epps")
     return S, R
 
@@ -413,11 +415,13 @@ def mm_batch_autotune(batch, offsets, t, logp, N, reps=3, stream=None) -> dict:
 
 
 def mm_batch_coeffs(batch, stream=None):
-    """Copy of the last sweep's coefficients: complex64 [reps * D, N_J + 1]."""
+    """Copy of the last sweep's coefficients: complex64 (complex128 for an
+    FP64 batch) [reps * D, N_J + 1]."""
     torch = _torch()
     ptr, ld = ctypes.c_void_p(), ctypes.c_int32()
     _check(_lib.load().mm_batch_coeffs(batch.handle, ctypes.byref(ptr), ctypes.byref(ld)), "mm_batch_coeffs")
-    out = torch.empty((batch.desc["reps"] * batch.desc["D"], ld.value), dtype=torch.complex64, device="cuda")
+    cdt = torch.complex128 if batch.desc["prec"] == "fp64" else torch.complex64
+    out = torch.empty((batch.desc["reps"] * batch.desc["D"], ld.value), dtype=cdt, device="cuda")
     _check(_lib.load().mm_batch_copy_coeffs(batch.handle, ctypes.c_void_p(out.data_ptr()), _stream(stream)),
            "mm_batch_copy_coeffs")
     return out

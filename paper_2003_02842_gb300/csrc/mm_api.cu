@@ -1446,8 +1446,8 @@ mm_status batch_enqueue(mm_batch b, const int64_t* off, const double* t, const d
   if (r != MM_OK) return r;
   StageScope sc(p, MM_STAGE_GRAM, st);
   const int grid = std::max(1, std::min(p->G, 2 * kSMs));
-  MM_CUDA(launch_epps(b->desc.D, b->desc.basis == MM_BASIS_FEJER, b->coef, N + 1, b->d_cut, (int)b->cut.size(), p->G,
-                      (float*)sigma, (float*)R, p->status, grid, st));
+  MM_CUDA(launch_epps(b->desc.D, b->desc.basis == MM_BASIS_FEJER, p->fp64, b->coef, N + 1, b->d_cut,
+                      (int)b->cut.size(), p->G, sigma, R, p->status, grid, st));
   return MM_OK;
 }
 
@@ -1463,7 +1463,7 @@ mm_status mm_batch_create(const mm_batch_desc* desc, mm_batch* out) {
   if (d.reps < 1 || d.D < 1 || d.N_max < 1 || d.max_events < 0 || d.reserved0 != 0) return MM_ERR_INVALID_ARG;
   for (int i = 0; i < 5; ++i)
     if (d.reserved[i] != 0) return MM_ERR_INVALID_ARG;
-  if (d.prec != MM_PREC_MIXED_BF16X3 && d.prec != MM_PREC_MIXED_3XTF32) return MM_ERR_UNSUPPORTED;
+  if (d.prec < MM_PREC_FP64 || d.prec > MM_PREC_MIXED_3XTF32) return MM_ERR_INVALID_ARG;
   if (d.D > epps_max_assets()) return MM_ERR_UNSUPPORTED;
   if ((int64_t)d.reps * d.D > (int64_t)1 << 30) return MM_ERR_UNSUPPORTED;
   mm_plan_desc pd{};
@@ -1481,7 +1481,7 @@ mm_status mm_batch_create(const mm_batch_desc* desc, mm_batch* out) {
     delete b;
     return r;
   }
-  const size_t coef_bytes = (size_t)pd.D * ((size_t)d.N_max + 1) * 8;
+  const size_t coef_bytes = (size_t)pd.D * ((size_t)d.N_max + 1) * (d.prec == MM_PREC_FP64 ? 16 : 8);
   if (dalloc(b->p, &b->coef, coef_bytes) != MM_OK || dalloc(b->p, (void**)&b->d_cut, kMaxCutoffs * sizeof(int)) != MM_OK ||
       cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
     if (b->coef) cudaFree(b->coef);
@@ -1602,7 +1602,7 @@ mm_status mm_batch_copy_coeffs(mm_batch b, void* d_dst, void* stream) {
   if (!b || !d_dst) return MM_ERR_INVALID_ARG;
   mm_status r = check_plan(b->p);
   if (r != MM_OK) return r;
-  MM_CUDA(cudaMemcpyAsync(d_dst, b->coef, (size_t)b->p->desc.D * b->ld * 8, cudaMemcpyDeviceToDevice,
+  MM_CUDA(cudaMemcpyAsync(d_dst, b->coef, (size_t)b->p->desc.D * b->ld * (b->p->fp64 ? 16 : 8), cudaMemcpyDeviceToDevice,
                           (cudaStream_t)stream));
   return MM_OK;
 }

@@ -250,8 +250,8 @@ mm_status plan_create_no_staging(const mm_plan_desc* desc, mm_plan* out);  // no
 mm_status plan_set_active_assets(mm_plan p, int D);
 int* plan_status_word(mm_plan p);
 mm_status plan_flags_to_status(int flags);
-cudaError_t launch_epps(int Dg, bool fejer, const void* coef, int ld, const int* cut, int ncut, int G, float* sigma,
-                        float* R, int* status, int grid, cudaStream_t s);
+cudaError_t launch_epps(int Dg, bool fejer, bool fp64, const void* coef, int ld, const int* cut, int ncut, int G,
+                        void* sigma, void* R, int* status, int grid, cudaStream_t s);
 
 // Pairwise-cutoff covariance (float64 D x D into sig) and its repair to the
 // nearest positive semi-definite matrix (one CTA, D <= pairwise_psd_max_assets()).

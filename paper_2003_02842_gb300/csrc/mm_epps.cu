@@ -25,7 +25,9 @@
 // Dg coefficients F_i(k)) adding the Dg (Dg+1)/2 products into registers,
 // and one warp-shuffle reduction per chunk adds them into the chunk's segment
 // in shared memory. Accumulation is float32 (the sums run over at most
-// N_max + 1 modes); the diagonal normalisation is float64.
+// N_max + 1 modes); the diagonal normalisation is float64. The FP64 form
+// (the comparator of the mixed one) runs the same sweep on complex128
+// coefficients with float64 accumulation and float64 Sigma and R.
 #include "mm_common.cuh"
 
 namespace mmgpu {
@@ -40,21 +42,27 @@ struct Pairs {
   static constexpr int n = DG * (DG + 1) / 2;
 };
 
-template <int DG, bool FEJER>
-__global__ void __launch_bounds__(kEppsThreads) k_epps(const float2* __restrict__ coef, int ld, const int* __restrict__ cut_g,
-                                                       int ncut, int G, float* __restrict__ sigma,
-                                                       float* __restrict__ Rout, const int* __restrict__ gate,
-                                                       int* status) {
+template <typename T> struct Cx;
+template <> struct Cx<float> { using type = float2; };
+template <> struct Cx<double> { using type = double2; };
+
+template <typename T, int DG, bool FEJER>
+__global__ void __launch_bounds__(kEppsThreads) k_epps(const typename Cx<T>::type* __restrict__ coef, int ld,
+                                                       const int* __restrict__ cut_g, int ncut, int G,
+                                                       T* __restrict__ sigma, T* __restrict__ Rout,
+                                                       const int* __restrict__ gate, int* status) {
+  using C2 = typename Cx<T>::type;
   constexpr int NP = Pairs<DG>::n;
   constexpr int NS = FEJER ? 2 : 1;
   constexpr int NW = kEppsThreads / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* sacc = reinterpret_cast<float*>(smem_raw);                     // [NS][ncut][NP]
-  double* ssig = reinterpret_cast<double*>(smem_raw + (((size_t)NS * ncut * NP * 4 + 15) & ~(size_t)15));  // [ncut][NP]
+  T* sacc = reinterpret_cast<T*>(smem_raw);  // [NS][ncut][NP]
+  double* ssig =
+      reinterpret_cast<double*>(smem_raw + (((size_t)NS * ncut * NP * sizeof(T) + 15) & ~(size_t)15));  // [ncut][NP]
   __shared__ int scut[kMaxCutoffs];
   __shared__ int cstart[kMaxCutoffs + 1];                  // first chunk of each segment
   __shared__ double swt[kMaxCutoffs];                      // basis weight per cutoff
-  __shared__ float sinv[kMaxCutoffs * DG];                 // 1 / sqrt(Sigma_aa(N_j))
+  __shared__ T sinv[kMaxCutoffs * DG];                     // 1 / sqrt(Sigma_aa(N_j))
   if (*gate) return;  // uniform
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < ncut; i += kEppsThreads) {
@@ -79,9 +87,9 @@ __global__ void __launch_bounds__(kEppsThreads) k_epps(const float2* __restrict_
   const int nchunks = cstart[ncut];
   int zero_var = 0;
   for (int g = blockIdx.x; g < G; g += gridDim.x) {
-    for (int i = threadIdx.x; i < NS * ncut * NP; i += kEppsThreads) sacc[i] = 0.f;
+    for (int i = threadIdx.x; i < NS * ncut * NP; i += kEppsThreads) sacc[i] = (T)0;
     __syncthreads();
-    const float2* cg = coef + (size_t)g * DG * ld;
+    const C2* cg = coef + (size_t)g * DG * ld;
     // each warp takes whole chunks: all 32 lanes in one segment, registers
     // accumulate over the chunk, one warp reduction per chunk
     for (int ch = warp; ch < nchunks; ch += NW) {
@@ -98,38 +106,39 @@ __global__ void __launch_bounds__(kEppsThreads) k_epps(const float2* __restrict_
       const int kb = (sj ? scut[sj - 1] + 1 : 0) + (ch - cstart[sj]) * kChunkModes;
       const int ke = min(kb + kChunkModes, scut[sj] + 1);
       const int es = scut[sj];  // the segment's end cutoff: weights e_s - k >= 0
-      float acc[NP], acc1[FEJER ? NP : 1];
+      T acc[NP], acc1[FEJER ? NP : 1];
 #pragma unroll
-      for (int p = 0; p < NP; ++p) acc[p] = 0.f;
+      for (int p = 0; p < NP; ++p) acc[p] = (T)0;
 #pragma unroll
-      for (int p = 0; p < (FEJER ? NP : 1); ++p) acc1[p] = 0.f;
+      for (int p = 0; p < (FEJER ? NP : 1); ++p) acc1[p] = (T)0;
       for (int k = kb + lane; k < ke; k += 32) {
-        float2 c[DG];
-        const float sc = k == 0 ? 1.0f : 1.41421356237309515f;  // sqrt(d_k)
+        C2 c[DG];
+        const T sc = k == 0 ? (T)1 : (T)1.41421356237309515;  // sqrt(d_k)
 #pragma unroll
         for (int i = 0; i < DG; ++i) {
-          const float2 v = __ldg(cg + (size_t)i * ld + k);
-          c[i] = make_float2(v.x * sc, v.y * sc);
+          const C2 v = __ldg(cg + (size_t)i * ld + k);
+          c[i].x = v.x * sc;
+          c[i].y = v.y * sc;
         }
-        const float kf = (float)(es - k);
+        const T kf = (T)(es - k);
         int p = 0;
 #pragma unroll
         for (int i = 0; i < DG; ++i)
 #pragma unroll
           for (int j = i; j < DG; ++j, ++p) {
-            const float q = fmaf(c[i].x, c[j].x, c[i].y * c[j].y);
+            const T q = fma(c[i].x, c[j].x, c[i].y * c[j].y);
             acc[p] += q;
-            if (FEJER) acc1[p] = fmaf(kf, q, acc1[p]);
+            if (FEJER) acc1[p] = fma(kf, q, acc1[p]);
           }
       }
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
-        float v = acc[p];
+        T v = acc[p];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) atomicAdd(&sacc[sj * NP + p], v);
         if (FEJER) {
-          float w = acc1[p];
+          T w = acc1[p];
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
           if (lane == 0) atomicAdd(&sacc[(ncut + sj) * NP + p], w);
@@ -153,7 +162,7 @@ __global__ void __launch_bounds__(kEppsThreads) k_epps(const float2* __restrict_
     for (int e = threadIdx.x; e < ncut * DG; e += kEppsThreads) {
       const int j = e / DG, a = e - j * DG;
       const double d = ssig[j * NP + a * DG - a * (a - 1) / 2];
-      sinv[e] = d > 0.0 ? (float)rsqrt(d) : __int_as_float(0x7fc00000);
+      sinv[e] = d > 0.0 ? (T)rsqrt(d) : (T)__longlong_as_double(0x7ff8000000000000ll);
       if (!(d > 0.0)) zero_var = 1;
     }
     __syncthreads();
@@ -163,10 +172,10 @@ __global__ void __launch_bounds__(kEppsThreads) k_epps(const float2* __restrict_
       const int a = r / DG, b = r - a * DG;
       const int lo = a < b ? a : b, hi = a < b ? b : a;
       const int p = lo * DG - lo * (lo - 1) / 2 + (hi - lo);  // index of pair (lo, hi)
-      const float sv = (float)ssig[j * NP + p];
+      const T sv = (T)ssig[j * NP + p];
       const size_t o = ((size_t)g * ncut + j) * DG * DG + r;
       if (sigma) sigma[o] = sv;
-      Rout[o] = a == b ? (sinv[j * DG + a] == sinv[j * DG + a] ? 1.0f : sinv[j * DG + a])
+      Rout[o] = a == b ? (sinv[j * DG + a] == sinv[j * DG + a] ? (T)1 : sinv[j * DG + a])
                        : sv * sinv[j * DG + a] * sinv[j * DG + b];
     }
     __syncthreads();
@@ -174,45 +183,53 @@ __global__ void __launch_bounds__(kEppsThreads) k_epps(const float2* __restrict_
   if (zero_var) atomicOr(status, ST_ZERO_VAR);
 }
 
-template <int DG>
-cudaError_t launch_dg(bool fejer, const void* coef, int ld, const int* cut, int ncut, int G, float* sigma, float* R,
+template <typename T, int DG>
+cudaError_t launch_dg(bool fejer, const void* coef, int ld, const int* cut, int ncut, int G, void* sigma, void* R,
                       const int* status_gate, int* status, int grid, cudaStream_t s) {
   constexpr int NP = Pairs<DG>::n;
   const int NS = fejer ? 2 : 1;
-  const size_t smem = (((size_t)NS * ncut * NP * 4 + 15) & ~(size_t)15) + (size_t)ncut * NP * 8;
+  const size_t smem = (((size_t)NS * ncut * NP * sizeof(T) + 15) & ~(size_t)15) + (size_t)ncut * NP * 8;
   auto go = [&](auto fn) -> cudaError_t {
     // static + dynamic shared memory may pass 48 KB: always opt in
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fn<<<grid, kEppsThreads, smem, s>>>((const float2*)coef, ld, cut, ncut, G, sigma, R, status_gate, status);
+    fn<<<grid, kEppsThreads, smem, s>>>((const typename Cx<T>::type*)coef, ld, cut, ncut, G, (T*)sigma, (T*)R,
+                                        status_gate, status);
     return cudaGetLastError();
   };
-  return fejer ? go(k_epps<DG, true>) : go(k_epps<DG, false>);
+  return fejer ? go(k_epps<T, DG, true>) : go(k_epps<T, DG, false>);
+}
+
+template <typename T>
+cudaError_t launch_t(int Dg, bool fejer, const void* coef, int ld, const int* cut, int ncut, int G, void* sigma,
+                     void* R, int* status, int grid, cudaStream_t s) {
+  const int* gate = status + 1;
+  switch (Dg) {
+    case 1: return launch_dg<T, 1>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
+    case 2: return launch_dg<T, 2>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
+    case 3: return launch_dg<T, 3>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
+    case 4: return launch_dg<T, 4>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
+    case 5: return launch_dg<T, 5>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
+    case 6: return launch_dg<T, 6>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
+    case 7: return launch_dg<T, 7>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
+    case 8: return launch_dg<T, 8>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
+    case 9: return launch_dg<T, 9>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
+    case 10: return launch_dg<T, 10>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
+    case 11: return launch_dg<T, 11>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
+    case 12: return launch_dg<T, 12>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
 
 int epps_max_assets() { return kMaxEppsAssets; }
 
-cudaError_t launch_epps(int Dg, bool fejer, const void* coef, int ld, const int* cut, int ncut, int G, float* sigma,
-                        float* R, int* status, int grid, cudaStream_t s) {
+cudaError_t launch_epps(int Dg, bool fejer, bool fp64, const void* coef, int ld, const int* cut, int ncut, int G,
+                        void* sigma, void* R, int* status, int grid, cudaStream_t s) {
   if (ncut < 1 || ncut > kMaxCutoffs || G < 1) return cudaErrorInvalidValue;
-  const int* gate = status + 1;
-  switch (Dg) {
-    case 1: return launch_dg<1>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
-    case 2: return launch_dg<2>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
-    case 3: return launch_dg<3>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
-    case 4: return launch_dg<4>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
-    case 5: return launch_dg<5>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
-    case 6: return launch_dg<6>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
-    case 7: return launch_dg<7>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
-    case 8: return launch_dg<8>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
-    case 9: return launch_dg<9>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
-    case 10: return launch_dg<10>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
-    case 11: return launch_dg<11>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
-    case 12: return launch_dg<12>(fejer, coef, ld, cut, ncut, G, sigma, R, gate, status, grid, s);
-    default: return cudaErrorInvalidValue;
-  }
+  return fp64 ? launch_t<double>(Dg, fejer, coef, ld, cut, ncut, G, sigma, R, status, grid, s)
+              : launch_t<float>(Dg, fejer, coef, ld, cut, ncut, G, sigma, R, status, grid, s);
 }
 
 }  // namespace mmgpu

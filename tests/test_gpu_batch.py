@@ -190,3 +190,57 @@ def test_sweep_contraction_relative_to_sigma_itself(basis):
             scale = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
             assert np.all(np.diag(ref) > 0)
             assert np.max(np.abs(S[r, j] - ref) / scale) <= 2e-5, (r, N, S[r, j], ref)
+
+
+@pytest.mark.parametrize("basis", ["dirichlet", "fejer"])
+def test_fp64_batch_matches_oracle_per_replication(basis):
+    # the batched form in float64 throughout (the mixed form's comparator):
+    # coefficients, Sigma and R of every replication and cutoff against the
+    # oracle at the FP64 path's tolerances (Eq. (15) <= 1e-10 at tol 1e-12;
+    # Sigma relative to the realised variances and R <= 1e-9)
+    import paper_2003_02842_gb300 as mm
+    reps, D = 5, 3
+    ev = synth.c4_batch(9, reps=reps, D=D, T=2000, median_n=300)
+    cutoffs = [1, 2, 7, 40, 333, 800]
+    b = mm.mm_batch_create(reps=reps, D=D, N_max=max(cutoffs), max_events=ev.n_events, tol=1e-12, kernel="es",
+                           basis=basis, prec="fp64")
+    off, t, p = to_dev(ev)
+    for _ in range(2):  # the eager first call, then the graph replay
+        S, R = mm.mm_batch_epps(b, off, t, p, cutoffs)
+    assert mm.mm_batch_sync(b) == 0
+    assert S.dtype == torch_float64()
+    F = mm.mm_batch_coeffs(b).cpu().numpy()
+    S, R = S.cpu().numpy(), R.cpu().numpy()
+    for r, e in enumerate(_split(ev, reps, D)):
+        ref = oracle.coeffs_F(e.offsets, e.t, e.logp, max(cutoffs))
+        assert np.all(rel_l2_rows(F[r * D:(r + 1) * D], ref) <= 1e-10), r
+        V = np.array([np.sum(np.diff(e.asset(i)[1]) ** 2) for i in range(D)])
+        for j, N in enumerate(cutoffs):
+            o = oracle.estimate(e.offsets, e.t, e.logp, N=N, basis=basis)
+            assert np.max(np.abs(S[r, j] - o["Sigma"]) / np.sqrt(np.outer(V, V))) <= 1e-9, (r, N)
+            assert np.max(np.abs(R[r, j] - o["R"])) <= 1e-9, (r, N)
+            assert np.all(np.diag(R[r, j]) == 1.0)
+    mm.mm_batch_destroy(b)
+
+
+def test_mixed_batch_agrees_with_fp64_batch():
+    # the like-for-like comparison of the two forms on one batch
+    import paper_2003_02842_gb300 as mm
+    reps, D = 64, 10
+    ev = synth.c4_batch(10, reps=reps, D=D, T=4000, median_n=600)
+    cutoffs = synth.sweep_cutoffs(int(ev.meta["nyquist"].min()), 16)
+    off, t, p = to_dev(ev)
+    out = {}
+    for prec, tol in (("fp64", 1e-12), ("bf16x3", 1e-6)):
+        b = mm.mm_batch_create(reps=reps, D=D, N_max=max(cutoffs), max_events=ev.n_events, tol=tol, kernel="es",
+                               basis="dirichlet", prec=prec)
+        _, R = mm.mm_batch_epps(b, off, t, p, cutoffs, sigma=False)
+        assert mm.mm_batch_sync(b) == 0
+        out[prec] = R.double().cpu().numpy()
+        mm.mm_batch_destroy(b)
+    assert np.max(np.abs(out["bf16x3"] - out["fp64"])) <= 1e-4
+
+
+def torch_float64():
+    import torch
+    return torch.float64
