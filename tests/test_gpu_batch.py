@@ -143,8 +143,6 @@ def test_batch_rejects_bad_requests():
     import paper_2003_02842_gb300 as mm
     with pytest.raises(mm.MMError):
         mm.mm_batch_create(reps=2, D=13, N_max=10, max_events=100)  # D above the sweep kernel's limit
-    with pytest.raises(mm.MMError):
-        mm.mm_batch_create(reps=2, D=3, N_max=10, max_events=100, prec="fp64")
     ev = synth.c4_batch(1, reps=2, D=3, T=500, median_n=100)
     b = mm.mm_batch_create(reps=2, D=3, N_max=50, max_events=ev.n_events, basis="fejer")
     off, t, p = to_dev(ev)
