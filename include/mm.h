@@ -211,9 +211,11 @@ mm_status mm_corr(mm_plan plan, const void* d_coeffs, int32_t N, void* d_sigma_o
  * sqrt(Sigma_ii Sigma_jj), R_ii = 1. Such a matrix need not be positive
  * semi-definite; psd_repair = 1 replaces Sigma (before R is formed) by the
  * positive semi-definite matrix closest to it in the Frobenius norm,
- * V max(Lambda, 0) V^T from its eigendecomposition (a Jacobi iteration in
- * one CTA, in float64 for FP64 plans and float32 for the mixed precisions;
- * D <= 256, else MM_ERR_UNSUPPORTED), leaving it unchanged when
+ * V max(Lambda, 0) V^T from its eigendecomposition (a cyclic Jacobi
+ * iteration, in float64 for FP64 plans and float32 for the mixed precisions:
+ * in one CTA while the matrix and its eigenvectors fit its shared memory,
+ * else over every SM under a cooperative launch; D <= 4000, else
+ * MM_ERR_UNSUPPORTED), leaving it unchanged when
  * no eigenvalue is negative; *d_clipped_or_null (device int) receives the
  * number of negative eigenvalues clipped (0 without repair).
  * h_N: host array of D cutoffs, each in [0, N_coeffs] ([1, N_coeffs] for

@@ -271,6 +271,7 @@ struct mm_plan_s {
   double* pw_A = nullptr;         // the repair's working matrix and eigenvectors
   double* pw_V = nullptr;         // (allocated on first use)
   int* pw_clip = nullptr;
+  void* pw_sync = nullptr;        // the multi-CTA repair's barrier words
   int acc_sel = 0;
   bool acc_dirty = true;          // clear both before the next contraction
   int acc_D = -1;                 // D whose D x Dp region the last epilogue cleared
@@ -354,7 +355,7 @@ void free_all(mm_plan p) {
   void* ptrs[] = {p->grid, p->rec_b0, p->rec_d, p->rec_v, p->W, p->atw, p->U, p->decon, p->glx, p->glw, p->bounds, p->gscale, p->status, p->gapbits, p->wsq,
                   p->partial, p->acc[0], p->acc[1], p->gram_done, p->fft_sync, p->pw_N, p->pw_sig, p->pw_A,
                   p->pw_V, p->pw_clip, p->s_off, p->s_t, p->s_p, p->s_coef,
-                  p->s_sigma, p->s_R, p->asset_order, p->tma_hi, p->tma_lo};
+                  p->s_sigma, p->s_R, p->asset_order, p->tma_hi, p->tma_lo, p->pw_sync};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->h_status) cudaFreeHost(p->h_status);
@@ -1088,6 +1089,7 @@ mm_status mm_corr_pairwise(mm_plan p, const void* d_coeffs, int32_t N_coeffs, co
     if (a == MM_OK && p->desc.D <= pairwise_psd_max_assets()) a = dalloc(p, (void**)&p->pw_A, dd);
     if (a == MM_OK && p->desc.D <= pairwise_psd_max_assets()) a = dalloc(p, (void**)&p->pw_V, dd);
     if (a == MM_OK) a = dalloc(p, (void**)&p->pw_clip, sizeof(int));
+    if (a == MM_OK) a = dalloc(p, &p->pw_sync, psd_sync_bytes());
     if (a != MM_OK) return a;
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -1100,7 +1102,7 @@ mm_status mm_corr_pairwise(mm_plan p, const void* d_coeffs, int32_t N_coeffs, co
   }
   StageScope sc(p, MM_STAGE_REDUCE, st, psd_repair ? 2 : 1);
   int* clip = d_clipped_or_null ? (int*)d_clipped_or_null : p->pw_clip;
-  if (psd_repair) MM_CUDA(launch_psd_repair(p->fp64, p->pw_sig, p->pw_A, p->pw_V, D, clip, st));
+  if (psd_repair) MM_CUDA(launch_psd_repair(p->fp64, p->pw_sig, p->pw_A, p->pw_V, D, clip, p->pw_sync, p->status, st));
   else MM_CUDA(cudaMemsetAsync(clip, 0, sizeof(int), st));
   MM_CUDA(launch_pairwise_out(p->fp64, p->pw_sig, D, d_sigma_or_null, d_R, p->status, st));
   return MM_OK;

@@ -254,11 +254,14 @@ cudaError_t launch_epps(int Dg, bool fejer, bool fp64, const void* coef, int ld,
                         void* sigma, void* R, int* status, int grid, cudaStream_t s);
 
 // Pairwise-cutoff covariance (float64 D x D into sig) and its repair to the
-// nearest positive semi-definite matrix (one CTA, D <= pairwise_psd_max_assets()).
+// nearest positive semi-definite matrix (D <= pairwise_psd_max_assets(): one CTA while the
+// matrix and eigenvectors fit its shared memory, else every SM under a cooperative launch).
 int pairwise_psd_max_assets();
 cudaError_t launch_pairwise(bool fp64, bool fejer, const void* coeffs, int ld, const int* Nv, int D,
                             double* sig, cudaStream_t s);
-cudaError_t launch_psd_repair(bool fp64, double* sig, double* A, double* V, int D, int* clipped, cudaStream_t s);
+cudaError_t launch_psd_repair(bool fp64, double* sig, double* A, double* V, int D, int* clipped, void* sync,
+                              int* status, cudaStream_t s);
+size_t psd_sync_bytes();  // the multi-CTA repair's barrier and reduction words
 cudaError_t launch_pairwise_out(bool fp64, const double* sig, int D, void* sigma, void* R, int* status,
                                 cudaStream_t s);
 

@@ -35,7 +35,7 @@ constexpr int kPT = 16;        // tile edge (pairs per tile: 16 x 16)
 constexpr int kPChunk = 128;   // modes staged per chunk
 constexpr int kJacobiThreads = 1024;
 constexpr int kJacobiSweeps = 40;
-constexpr int kPsdMaxD = 256;  // largest matrix the one-CTA repair takes
+constexpr int kPsdMaxD = 256;  // rotation arrays of the one-CTA repair (it takes what fits 200 KB)
 constexpr size_t kPsdSmemBytes = 200 * 1024;  // the working matrix and eigenvectors in shared memory up to this
 
 __device__ __forceinline__ void tile_of(int p, int nt, int& I, int& J) {
@@ -235,6 +235,216 @@ __global__ void __launch_bounds__(kJacobiThreads) k_psd_repair(double* __restric
   }
 }
 
+// The same cyclic Jacobi iteration over the whole GPU, for matrices larger
+// than one CTA's shared memory holds: one CTA per SM under a cooperative
+// launch (every CTA resident), A and V in global memory (read through L2).
+// A round-robin step's rotations act on disjoint index pairs, so J^T A J
+// splits into independent 2 x 2 blocks (rows p_i, q_i; columns p_j, q_j):
+// after a grid barrier every CTA recomputes the step's D/2 rotations from
+// A's current diagonal and pivot entries, and the threads of the grid update
+// the blocks of A and the column pairs of V (each element written by one
+// thread). One barrier per step, one reduction per sweep; every barrier wait
+// is bounded (ST_TIMEOUT, and the CTA leaves).
+struct GridSync {
+  unsigned count;  // arrivals at the current barrier
+  unsigned gen;    // barriers completed
+  int neg;         // negative eigenvalues
+  int pad;
+  double red[3];   // [0] squared norm, [1], [2] off-diagonal sums of alternate sweeps
+};
+
+__device__ __forceinline__ uint64_t grid_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier for a cooperative launch; false when the wait timed out.
+__device__ bool grid_barrier(GridSync* gs, unsigned nblocks, int* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &gs->gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&gs->count, 1u) == nblocks - 1) {
+      atomicExch(&gs->count, 0u);
+      __threadfence();
+      atomicAdd(&gs->gen, 1u);
+    } else {
+      const uint64_t t0 = grid_timer_ns();
+      while (*vgen == g) {
+        if (grid_timer_ns() - t0 > kDefaultWaitNs) {
+          ok = 0;
+          atomicOr(status, ST_TIMEOUT);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+constexpr int kGridJacobiThreads = 512;
+constexpr int kGridMaxD = 4000;  // rotations of one step fit 48 KB of shared memory
+
+template <typename W>
+__global__ void __launch_bounds__(kGridJacobiThreads) k_psd_repair_grid(double* __restrict__ sig, W* __restrict__ A,
+                                                                        W* __restrict__ V, int D, int* clipped,
+                                                                        GridSync* gs, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = (D + 1) & ~1, nh = m / 2;
+  W* rc = reinterpret_cast<W*>(smem_raw);
+  W* rs = rc + nh;
+  int* rp = reinterpret_cast<int*>(rs + nh);
+  int* rq = rp + nh;
+  __shared__ double s_red[kGridJacobiThreads / 32];
+  const unsigned nb = gridDim.x;
+  const int tid = threadIdx.x;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + tid, gnth = (int64_t)gridDim.x * blockDim.x;
+  const int64_t DD = (int64_t)D * D;
+  auto block_sum_to = [&](double v, double* dst) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) s_red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kGridJacobiThreads / 32; ++w) t += s_red[w];
+      atomicAdd(dst, t);
+    }
+    __syncthreads();
+  };
+  double nrm = 0.0;
+  for (int64_t e = gtid; e < DD; e += gnth) {
+    const W a = (W)sig[e];
+    A[e] = a;
+    const int64_t r = e / D;
+    V[e] = (r == e - r * D) ? (W)1 : (W)0;
+    nrm += (double)a * (double)a;
+  }
+  block_sum_to(nrm, &gs->red[0]);
+  if (!grid_barrier(gs, nb, status)) return;
+  const double norm2 = __ldcg(&gs->red[0]);
+  const double eps = sizeof(W) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-8;
+  const double rel2 = (2.0 * D * eps) * (2.0 * D * eps);
+  for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
+    double* slot = &gs->red[1 + (sweep & 1)];
+    double off = 0.0;
+    for (int64_t e = gtid; e < DD; e += gnth) {
+      const int64_t r = e / D;
+      if (r != e - r * D) {
+        const double a = (double)__ldcg(A + e);
+        off += a * a;
+      }
+    }
+    block_sum_to(off, slot);
+    if (!grid_barrier(gs, nb, status)) return;
+    const double off_all = __ldcg(slot);
+    // the other slot was last read before this barrier: clear it for the next sweep
+    if (blockIdx.x == 0 && tid == 0) gs->red[1 + ((sweep + 1) & 1)] = 0.0;
+    if (!(off_all > rel2 * norm2)) break;  // uniform: every CTA read the same sum
+    for (int step = 0; step < m - 1; ++step) {
+      for (int i = tid; i < nh; i += blockDim.x) {
+        int p, q;
+        if (i == 0) {
+          p = step;
+          q = m - 1;
+        } else {
+          p = (step + i) % (m - 1);
+          q = (step - i + (m - 1)) % (m - 1);
+        }
+        if (p > q) {
+          const int x = p;
+          p = q;
+          q = x;
+        }
+        W c = 1, sn = 0;
+        if (q < D) {
+          const W apq = __ldcg(A + (int64_t)p * D + q);
+          if (apq != (W)0) {
+            const W tau = (__ldcg(A + (int64_t)q * D + q) - __ldcg(A + (int64_t)p * D + p)) / ((W)2 * apq);
+            const W t = (tau >= (W)0 ? (W)1 : (W)-1) / (fabs(tau) + sqrt((W)1 + tau * tau));
+            c = (W)1 / sqrt((W)1 + t * t);
+            sn = t * c;
+          }
+        }
+        rp[i] = p;
+        rq[i] = q;
+        rc[i] = c;
+        rs[i] = sn;
+      }
+      __syncthreads();
+      // A <- J^T A J by 2 x 2 blocks (rows of pair i, columns of pair j)
+      const int64_t nblk = (int64_t)nh * nh;
+      for (int64_t e = gtid; e < nblk; e += gnth) {
+        const int i = (int)(e / nh), j = (int)(e - (int64_t)i * nh);
+        const int pi = rp[i], qi = rq[i], pj = rp[j], qj = rq[j];
+        const bool vi = qi < D, vj = qj < D;
+        const W ci = rc[i], si = rs[i], cj = rc[j], sj = rs[j];
+        const W app = __ldcg(A + (int64_t)pi * D + pj);
+        const W apq = vj ? __ldcg(A + (int64_t)pi * D + qj) : (W)0;
+        const W aqp = vi ? __ldcg(A + (int64_t)qi * D + pj) : (W)0;
+        const W aqq = (vi && vj) ? __ldcg(A + (int64_t)qi * D + qj) : (W)0;
+        // rows: J_i^T, then columns: J_j
+        const W bpp = ci * app - si * aqp, bpq = ci * apq - si * aqq;
+        const W bqp = si * app + ci * aqp, bqq = si * apq + ci * aqq;
+        A[(int64_t)pi * D + pj] = cj * bpp - sj * bpq;
+        if (vj) A[(int64_t)pi * D + qj] = sj * bpp + cj * bpq;
+        if (vi) A[(int64_t)qi * D + pj] = cj * bqp - sj * bqq;
+        if (vi && vj) A[(int64_t)qi * D + qj] = sj * bqp + cj * bqq;
+      }
+      // V <- V J by column pairs
+      const int64_t nv = (int64_t)D * nh;
+      for (int64_t e = gtid; e < nv; e += gnth) {
+        const int x = (int)(e / nh), j = (int)(e - (int64_t)x * nh);
+        const int pj = rp[j], qj = rq[j];
+        if (qj >= D) continue;
+        const W cj = rc[j], sj = rs[j];
+        const W vp = __ldcg(V + (int64_t)x * D + pj), vq = __ldcg(V + (int64_t)x * D + qj);
+        V[(int64_t)x * D + pj] = cj * vp - sj * vq;
+        V[(int64_t)x * D + qj] = sj * vp + cj * vq;
+      }
+      if (!grid_barrier(gs, nb, status)) return;
+    }
+  }
+  // eigenvalues: the diagonal, negatives clipped
+  int neg = 0;
+  for (int i = (int)gtid; i < D; i += (int)gnth)
+    if (__ldcg(A + (int64_t)i * D + i) < (W)0) ++neg;
+  if (neg) atomicAdd(&gs->neg, neg);
+  if (!grid_barrier(gs, nb, status)) return;
+  const int negs = *(volatile int*)&gs->neg;
+  if (blockIdx.x == 0 && tid == 0 && clipped) *clipped = negs;
+  if (negs == 0) return;  // already positive semi-definite: Sigma unchanged
+  // the clipped eigenvalues in this CTA's shared memory (the rotation arrays
+  // hold at least 8 D bytes)
+  double* lam = reinterpret_cast<double*>(smem_raw);
+  for (int k = tid; k < D; k += blockDim.x) {
+    const double l = (double)__ldcg(A + (int64_t)k * D + k);
+    lam[k] = l > 0.0 ? l : 0.0;
+  }
+  __syncthreads();
+  const int64_t npairs = (int64_t)D * (D + 1) / 2;
+  for (int64_t e = gtid; e < npairs; e += gnth) {
+    // pair (i, j), i <= j, in row-major order of the upper triangle
+    int i = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+    while ((int64_t)(i + 1) * (i + 2) / 2 <= e) ++i;
+    while ((int64_t)i * (i + 1) / 2 > e) --i;
+    const int jj = (int)(e - (int64_t)i * (i + 1) / 2);  // 0..i
+    const int r = jj, c = i;                             // r <= c
+    double v = 0.0;
+    for (int k = 0; k < D; ++k)
+      if (lam[k] > 0.0) v += (double)__ldcg(V + (int64_t)r * D + k) * lam[k] * (double)__ldcg(V + (int64_t)c * D + k);
+    sig[(int64_t)r * D + c] = v;
+    sig[(int64_t)c * D + r] = v;
+  }
+}
+
 // Sigma and R in the output precision: R_ij = Sigma_ij / sqrt(Sigma_ii Sigma_jj)
 // (float64), R_ii = 1; a non-positive variance gives NaN and ST_ZERO_VAR.
 template <typename T>
@@ -261,7 +471,7 @@ __global__ void k_pairwise_out(const double* __restrict__ sig, int D, T* __restr
 
 namespace mmgpu {
 
-int pairwise_psd_max_assets() { return kPsdMaxD; }
+int pairwise_psd_max_assets() { return kGridMaxD; }
 
 cudaError_t launch_pairwise(bool fp64, bool fejer, const void* coeffs, int ld, const int* Nv, int D,
                             double* sig, cudaStream_t s) {
@@ -277,30 +487,50 @@ cudaError_t launch_pairwise(bool fp64, bool fejer, const void* coeffs, int ld, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_psd_repair(bool fp64, double* sig, double* A, double* V, int D, int* clipped, cudaStream_t s) {
-  if (D > kPsdMaxD) return cudaErrorInvalidValue;
-  auto go = [&](auto kern, size_t wbytes) -> cudaError_t {
-    const size_t need = 2 * (size_t)D * D * wbytes;
-    const size_t smem = need <= kPsdSmemBytes ? need : 0;
-    if (smem) {
-      const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_psd_repair(bool fp64, double* sig, double* A, double* V, int D, int* clipped, void* sync,
+                              int* status, cudaStream_t s) {
+  if (D > kGridMaxD) return cudaErrorInvalidValue;
+  const size_t wb = fp64 ? 8 : 4;
+  const size_t need = 2 * (size_t)D * D * wb;
+  if (need <= kPsdSmemBytes) {
+    // the working matrix and eigenvectors in one CTA's shared memory
+    auto one = [&](auto kern) -> cudaError_t {
+      const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
       if (e != cudaSuccess) return e;
+      return cudaSuccess;
+    };
+    cudaError_t e;
+    if (fp64) {
+      if ((e = one(k_psd_repair<double>)) != cudaSuccess) return e;
+      k_psd_repair<double><<<1, kJacobiThreads, need, s>>>(sig, A, V, D, clipped);
+    } else {
+      if ((e = one(k_psd_repair<float>)) != cudaSuccess) return e;
+      k_psd_repair<float><<<1, kJacobiThreads, need, s>>>(sig, (float*)A, (float*)V, D, clipped);
     }
-    return cudaSuccess;
-  };
-  cudaError_t e;
-  if (fp64) {
-    if ((e = go(k_psd_repair<double>, 8)) != cudaSuccess) return e;
-    const size_t need = 2 * (size_t)D * D * 8;
-    k_psd_repair<double><<<1, kJacobiThreads, need <= kPsdSmemBytes ? need : 0, s>>>(sig, A, V, D, clipped);
-  } else {
-    if ((e = go(k_psd_repair<float>, 4)) != cudaSuccess) return e;
-    const size_t need = 2 * (size_t)D * D * 4;
-    k_psd_repair<float><<<1, kJacobiThreads, need <= kPsdSmemBytes ? need : 0, s>>>(sig, (float*)A, (float*)V, D,
-                                                                                     clipped);
+    return cudaGetLastError();
   }
-  return cudaGetLastError();
+  // the whole GPU: one CTA per SM, every CTA resident (cooperative launch)
+  cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(GridSync), s);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int nh = ((D + 1) & ~1) / 2;
+  const size_t smem = (size_t)nh * (2 * wb + 2 * sizeof(int));
+  GridSync* gs = reinterpret_cast<GridSync*>(sync);
+  auto launch = [&](auto kern, void* Aw, void* Vw) -> cudaError_t {
+    int per_sm = 0;
+    cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGridJacobiThreads, smem);
+    if (r != cudaSuccess) return r;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    void* args[] = {(void*)&sig, &Aw, &Vw, (void*)&D, (void*)&clipped, (void*)&gs, (void*)&status};
+    return cudaLaunchCooperativeKernel((const void*)kern, dim3(sms), dim3(kGridJacobiThreads), args, smem, s);
+  };
+  if (fp64) return launch(k_psd_repair_grid<double>, (void*)A, (void*)V);
+  return launch(k_psd_repair_grid<float>, (void*)A, (void*)V);
 }
+
+size_t psd_sync_bytes() { return sizeof(GridSync); }
 
 cudaError_t launch_pairwise_out(bool fp64, const double* sig, int D, void* sigma, void* R, int* status,
                                 cudaStream_t s) {

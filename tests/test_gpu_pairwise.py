@@ -30,8 +30,10 @@ def _built():
 
 
 def _case(seed, D=24):
+    # per-asset cutoffs from 2 to 119 (fewer distinct values for many assets:
+    # the oracle evaluates Algorithm 3 once per distinct pairwise cutoff)
     ev = synth.random_events(80 + seed, D=D, n_range=(30, 300), T=3000.0)
-    Ns = np.random.default_rng(seed).integers(2, 120, size=D)
+    Ns = np.random.default_rng(seed).integers(2, 120 if D <= 24 else 30, size=D)
     return ev, [int(x) for x in Ns]
 
 
@@ -66,19 +68,33 @@ def test_pairwise_cutoffs_match_oracle(prec, basis):
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 @pytest.mark.parametrize("basis", ["dirichlet", "fejer"])
-@pytest.mark.parametrize("seed", [1, 3])
-def test_psd_repair_matches_oracle(prec, basis, seed):
-    ev, Ns = _case(seed)
+@pytest.mark.parametrize("seed,D", [(1, 24), (3, 24), (5, 200), (7, 500)])
+def test_psd_repair_matches_oracle(prec, basis, seed, D):
+    # D = 24: the one-CTA Jacobi iteration in shared memory; D = 200 and 500
+    # (the serving workload's largest request): the iteration over every SM.
+    # The iteration stops once the off-diagonal norm is below 2 D eps of the
+    # matrix norm (eps of its working type), and every element meets about 2D
+    # rotations per sweep, so the decomposition's backward error is of order
+    # D eps of the norm: the repaired matrix is held to 8 D eps of the norm
+    # (about 1e-4 in float32 at D = 200-500, the mixed path's own Sigma
+    # tolerance) beyond twice the input's own distance from the oracle's.
+    ev, Ns = _case(seed, D=D)
     raw = _run(ev, Ns, prec, basis, repair=False)
     out = _run(ev, Ns, prec, basis, repair=True)
     S_ref, _ = oracle.cov_pairwise_cutoffs(ev.offsets, ev.t, ev.logp, Ns, basis=basis)
     P_ref, neg = oracle.nearest_psd(S_ref)
     assert neg >= 1  # the pairwise estimate is not positive semi-definite here
-    assert out["status"] == 0 and out["clipped"] == neg
+    assert out["status"] == 0
+    # eigenvalues within the iteration's accuracy of zero may fall either way
+    lam = np.linalg.eigvalsh(0.5 * (S_ref + S_ref.T))
+    eps_w = 1.1e-16 if prec == "fp64" else 6e-8
+    tiny = np.sum(np.abs(lam) <= 4 * D * eps_w * np.abs(lam).max())
+    assert abs(out["clipped"] - neg) <= tiny
     d_in = np.linalg.norm(raw["S"] - S_ref)
-    assert np.linalg.norm(out["S"] - P_ref) <= 2.0 * d_in + TOL[prec]["eig"] * np.linalg.norm(S_ref)
-    assert np.linalg.eigvalsh(out["S"]).min() >= -1e-5 * np.abs(np.linalg.eigvalsh(S_ref)).max()
-    assert np.max(np.abs(out["R"] - oracle.corr(P_ref))) <= 10 * TOL[prec]["R"]
+    tol_eig = max(TOL[prec]["eig"], 8 * D * eps_w)
+    assert np.linalg.norm(out["S"] - P_ref) <= 2.0 * d_in + tol_eig * np.linalg.norm(S_ref)
+    assert np.linalg.eigvalsh(out["S"]).min() >= -max(1e-5, tol_eig) * np.abs(lam).max()
+    assert np.max(np.abs(out["R"] - oracle.corr(P_ref))) <= 10 * max(TOL[prec]["R"], tol_eig)
 
 
 @pytest.mark.parametrize("basis", ["dirichlet", "fejer"])
@@ -112,12 +128,12 @@ def test_pairwise_rejects_bad_arguments():
         with pytest.raises((mm.MMError, ValueError)):
             mm.mm_corr_pairwise(plan, F, Nc, bad)
     mm.mm_destroy(plan)
-    big = synth.random_events(9, D=300, n_range=(2, 20), T=500.0)
-    plan = mm.mm_plan_create(D=300, N_max=8, max_events=big.n_events, tol=1e-6, kernel="es")
-    off, t, p = to_dev(big)
-    F, _ = mm.mm_coeffs(plan, off, t, p, 8)
+    D = 4001  # beyond the repair's limit (its rotation arrays fill 48 KB)
+    plan = mm.mm_plan_create(D=D, N_max=8, max_events=0, tol=1e-6, kernel="es")
+    F = torch.zeros((D, 9), dtype=torch.complex64, device="cuda")
+    F[:, 1] = 1.0
     with pytest.raises(mm.MMError):
-        mm.mm_corr_pairwise(plan, F, 8, [8] * 300, psd_repair=True)  # the one-CTA repair takes D <= 256
-    S, R, c = mm.mm_corr_pairwise(plan, F, 8, [8] * 300)
+        mm.mm_corr_pairwise(plan, F, 8, [8] * D, psd_repair=True)
+    S, R, c = mm.mm_corr_pairwise(plan, F, 8, [8] * D)
     torch.cuda.synchronize()
     mm.mm_destroy(plan)
