@@ -100,26 +100,25 @@ typedef struct {
   mm_precision prec;
   int32_t spread_tile;  /* grid cells per spreading block; 0 = library default */
   int32_t spread_algo;  /* 0 library default (= 1 unless mm_autotune chose otherwise);
-                           1 separate prep / scatter-into-tile / FFT kernels; 2 as 1
-                           with a gather per grid cell; 3 stages (a)-(c) fused in one
-                           CTA per asset when the grid fits in shared memory, else 1;
-                           4 as 1 with the kernel evaluated directly per tap and float
-                           accumulation (the mixed-path default 1 uses per-tap
-                           polynomials and integer accumulation). All compute Eq. (12). */
+                           1 separate prep / scatter-into-tile / FFT kernels (the mixed
+                           path evaluates the kernel as per-tap polynomials and
+                           accumulates exactly in integers); 2 as 1 with a gather per
+                           grid cell (no atomics: the FP64 path's sums then come out
+                           in a fixed order); 3 stages (a)-(c) fused in one CTA per
+                           asset when the grid fits in shared memory, else 1. All
+                           compute Eq. (12). */
   int32_t fft_algo;     /* stages (b)-(c) in the mixed precisions: 0 library default
                            (the grid in shared memory when it fits: as 2 when one
                            asset's row fits one CTA, else as 4; otherwise 1);
-                           1 two-pass FFT through
-                           global memory; 2 one CTA per asset; 3 two CTAs per asset
-                           (radix-2 step on load); 4 a cluster of two CTAs per asset
-                           (decimation in time by 2, halves joined through distributed
-                           shared memory); 5 as 2 with the polynomial scatter storing
-                           the grid in the FFT's digit-reversed input order (one bulk
-                           copy per row); 6 three CTAs per asset (radix-3 step on
-                           load; the CTAs of the output classes k = 1, 2 mod 3 each
-                           form their terms of both classes' modes and combine them
-                           in the output, ordered by a per-asset counter). The FP64
-                           path always uses 1. All compute Eqs. (13)-(14). */
+                           1 two-pass FFT through global memory; 2 one CTA per
+                           asset; 4 a cluster of two CTAs per asset (decimation in
+                           time by 2, halves joined through distributed shared
+                           memory); 5 as 2 with the polynomial scatter storing the
+                           grid in the FFT's digit-reversed input order (one bulk
+                           copy per row). 3 and 6 (two or three CTAs per asset with
+                           a radix-2 or radix-3 step on load) are not built: they
+                           measured slower on every workload. The FP64 path always
+                           uses 1. All compute Eqs. (13)-(14). */
   int32_t gram_algo;    /* stage (d) in the mixed precisions: 0 library default (2 from
                            192 assets up, else 1); 1 each CTA converts its
                            tiles of the weighted coefficients to split precision in
@@ -155,9 +154,8 @@ typedef struct {
   int32_t fft_algo;      /* stages (b)-(c) in use: 0 per-asset shared-memory FFT, 1 two-pass */
   int32_t fft_passes;    /* per-asset FFT: number of radix passes (0 when not in use) */
   int32_t fft_radix[4];  /* per-asset FFT: radix of each pass */
-  int32_t fft_split;     /* per-asset FFT: 1 one CTA per asset, 2 two CTAs (radix-2 step on
-                            load), 3 a cluster of two CTAs joined through distributed shared
-                            memory, 4 three CTAs (radix-3 step on load); 0 when not in use */
+  int32_t fft_split;     /* per-asset FFT: 1 one CTA per asset, 3 a cluster of two CTAs joined
+                            through distributed shared memory; 0 when not in use */
   int32_t spread_poly;   /* 1: float32 spreading evaluates the kernel as per-tap polynomials
                             (error <= max(3e-7, tol/10)) and accumulates exactly in integers */
   int32_t graphs;        /* 1: steady mm_estimate calls replay a captured CUDA graph */

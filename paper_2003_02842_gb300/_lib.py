@@ -21,10 +21,9 @@ STATUS_NAMES = {
 KERNELS = {"gauss": 0, "kb": 1, "es": 2}
 BASES = {"dirichlet": 0, "fejer": 1}
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "3xtf32": 2}
-SPREAD_ALGOS = {"default": 0, "scatter": 1, "gather": 2, "fused": 3, "scatter_direct": 4}
+SPREAD_ALGOS = {"default": 0, "scatter": 1, "gather": 2, "fused": 3}
 GRAM_ALGOS = {"default": 0, "convert": 1, "tma": 2}
-FFT_ALGOS = {"default": 0, "two_pass": 1, "asset": 2, "asset_split": 3, "asset_pair": 4, "asset_perm": 5,
-             "asset_split3": 6}
+FFT_ALGOS = {"default": 0, "two_pass": 1, "asset": 2, "asset_pair": 4, "asset_perm": 5}
 STAGES = ["prep", "spread", "fft_cols", "fft_rows", "gram", "reduce", "setup", "fused", "fft", "split"]
 
 

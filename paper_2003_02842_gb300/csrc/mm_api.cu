@@ -265,7 +265,6 @@ struct mm_plan_s {
   void* tma_lo = nullptr;         // (Dpad x kpc complex modes, pad rows zero)
   int gram_used = 0;              // contraction variant of the last call (mm_plan_info.gram_algo)
   int* gram_done = nullptr;       // contraction CTAs finished (the last one runs the epilogue)
-  int* fft_sync = nullptr;        // per asset: arrival counter and flag of the three-CTA FFT split
   int* pw_N = nullptr;            // pairwise-cutoff covariance: per-asset cutoffs,
   double* pw_sig = nullptr;       // the float64 estimate,
   double* pw_A = nullptr;         // the repair's working matrix and eigenvectors
@@ -294,7 +293,7 @@ struct mm_plan_s {
   int tune_rowblk = -1;   // FFT pass 2: lower rows per block
   float tune_ms = 0.f;    // time of the chosen configuration
   int tune_fft = -1;      // 0 per-asset shared-memory FFT, 1 two-pass FFT
-  int tune_split = -1;    // per-asset FFT: CTAs per asset (1 or 2)
+  int tune_split = -1;    // per-asset FFT: 1 one CTA per asset, 3 the cluster pair
   int tune_maxr = -1;     // per-asset FFT: largest radix (16 or 32)
   int tune_perm = -1;     // 1: the scatter stores the grid in the FFT's input order (split 1)
   int64_t Mr = 0;
@@ -353,7 +352,7 @@ mm_status dalloc(mm_plan p, void** ptr, size_t bytes) {
 
 void free_all(mm_plan p) {
   void* ptrs[] = {p->grid, p->rec_b0, p->rec_d, p->rec_v, p->W, p->atw, p->U, p->decon, p->glx, p->glw, p->bounds, p->gscale, p->status, p->gapbits, p->wsq,
-                  p->partial, p->acc[0], p->acc[1], p->gram_done, p->fft_sync, p->pw_N, p->pw_sig, p->pw_A,
+                  p->partial, p->acc[0], p->acc[1], p->gram_done, p->pw_N, p->pw_sig, p->pw_A,
                   p->pw_V, p->pw_clip, p->s_off, p->s_t, p->s_p, p->s_coef,
                   p->s_sigma, p->s_R, p->asset_order, p->tma_hi, p->tma_lo, p->pw_sync};
   for (void* q : ptrs)
@@ -469,7 +468,6 @@ mm_status configure(mm_plan p, int N) {
   }
   const bool fits = fused_smem(f, Mr, p->fp64) + 2048 <= (size_t)p->smem_optin;
   int algo = p->desc.spread_algo == 2 ? 1 : (p->desc.spread_algo == 3 ? 2 : 0);
-  const bool direct_taps = p->desc.spread_algo == 4;  // scatter evaluating the kernel directly
   if (p->tune_algo >= 0) algo = p->tune_algo;
   if (algo == 2 && (!fits || p->G > 1)) algo = 0;
   s.algo = algo == 1 ? 1 : 0;
@@ -484,7 +482,7 @@ mm_status configure(mm_plan p, int N) {
   s.kb_inv_phi0 = kPi * p->msp / sinh(s.kb_b * p->msp);
   p->tau = kPi * lam / ((double)Mr * (double)Mr);
   p->poly_ok = false;
-  if (!p->fp64 && s.algo == 0 && !s.fused && p->tune_poly != 0 && !direct_taps &&
+  if (!p->fp64 && s.algo == 0 && !s.fused && p->tune_poly != 0 &&
       spread_poly_supported(s.khi - s.klo + 1)) {
     // the fit must stay far below the NUFFT tolerance and near float32 rounding
     const double err = fit_kernel_poly(s, &p->poly);
@@ -498,24 +496,20 @@ mm_status configure(mm_plan p, int N) {
   // set by latency (a CTA alone on an SM takes as long as two sharing one),
   // so splitting an asset over more SMs does not pay for its extra loads.
   // Larger rows: two CTAs per asset as a cluster (decimation in time by 2,
-  // joined through distributed shared memory). Two or three CTAs per asset
-  // with a radix-2 or radix-3 step on load are taken on request.
+  // joined through distributed shared memory), also on request.
   int split = 1;
   int pair = 0;
   const bool caller_split = p->desc.fft_algo >= 2 && p->tune_split < 1;
-  if (caller_split) {  // the caller's choice of per-asset variant
-    split = (p->desc.fft_algo == 2 || p->desc.fft_algo == 5) ? 1 : p->desc.fft_algo == 6 ? 3 : 2;
-    pair = p->desc.fft_algo == 4 ? 1 : 0;
+  if (caller_split && p->desc.fft_algo == 4) {  // the caller's choice: the cluster pair
+    split = 2;
+    pair = 1;
   }
-  if (p->tune_split == 1 || p->tune_split == 2) {
-    split = p->tune_split;
+  if (p->tune_split == 1) {
+    split = 1;
     pair = 0;
   } else if (p->tune_split == 3) {
     split = 2;
     pair = 1;
-  } else if (p->tune_split == 4) {
-    split = 3;
-    pair = 0;
   }
   // radices up to 16 by default: the fully unrolled codelets of 25 to 32
   // points stall on instruction fetch, so four small passes beat three large
@@ -534,8 +528,8 @@ mm_status configure(mm_plan p, int N) {
   };
   bool afft = !p->fp64 && fits_split(split);
   if (!p->fp64 && !afft && p->tune_split < 1 && p->desc.fft_algo < 2) {
-    // another split (a large grid fits in shared memory only as two halves)
-    split = split == 1 ? 2 : split == 3 ? 2 : 1;
+    // the other form (a large grid fits in shared memory only as two halves)
+    split = split == 1 ? 2 : 1;
     pair = split == 2 ? 1 : 0;
     afft = fits_split(split);
   }
@@ -724,7 +718,7 @@ mm_status coeffs_impl(mm_plan p, const int64_t* off, const double* t, const doub
     if (p->use_afft) {
       StageScope sc(p, MM_STAGE_FFT, st);
       MM_CUDA(launch_fft_asset((const float*)p->grid, p->afft, D, p->W, p->atw, p->U, p->decon, coeffs, p->status,
-                               p->fft_sync, st));
+                               st));
     } else {
     {
       StageScope sc(p, MM_STAGE_FFT_COLS, st);
@@ -928,8 +922,8 @@ mm_status plan_create_impl(const mm_plan_desc* desc, int gsize, bool batch, mm_p
   if (d.basis < MM_BASIS_DIRICHLET || d.basis > MM_BASIS_FEJER) return MM_ERR_INVALID_ARG;
   if (d.prec < MM_PREC_FP64 || d.prec > MM_PREC_MIXED_3XTF32) return MM_ERR_INVALID_ARG;
   if (d.spread_tile < 0 || d.spread_tile > 50000) return MM_ERR_INVALID_ARG;
-  if (d.spread_algo < 0 || d.spread_algo > 4) return MM_ERR_INVALID_ARG;
-  if (d.fft_algo < 0 || d.fft_algo > 6) return MM_ERR_INVALID_ARG;
+  if (d.spread_algo < 0 || d.spread_algo > 3) return MM_ERR_INVALID_ARG;
+  if (d.fft_algo < 0 || d.fft_algo > 5 || d.fft_algo == 3) return MM_ERR_INVALID_ARG;
   if (d.gram_algo < 0 || d.gram_algo > 2) return MM_ERR_INVALID_ARG;
   for (int i = 0; i < 3; ++i)
     if (d.reserved[i] != 0) return MM_ERR_INVALID_ARG;
@@ -974,7 +968,6 @@ mm_status plan_create_impl(const mm_plan_desc* desc, int gsize, bool batch, mm_p
   if (!p->fp64) {
     p->atw_cap = 2 * n;  // sum_p m_p (R_p - 1) < n (1 + 1/R_1 + ...) < 2n
     A(&p->atw, (size_t)p->atw_cap * p->cs);
-    A((void**)&p->fft_sync, 2 * D * sizeof(int));
   }
   A(&p->U, Np1 * p->cs);
   A(&p->decon, Np1 * p->rs);
@@ -1017,7 +1010,6 @@ mm_status plan_create_impl(const mm_plan_desc* desc, int gsize, bool batch, mm_p
   if (r == MM_OK) {
     if (cudaMemset(p->status, 0, 4 * sizeof(int)) != cudaSuccess) r = MM_ERR_CUDA;
     if (p->gram_done && cudaMemset(p->gram_done, 0, sizeof(int)) != cudaSuccess) r = MM_ERR_CUDA;
-    if (p->fft_sync && cudaMemset(p->fft_sync, 0, 2 * D * sizeof(int)) != cudaSuccess) r = MM_ERR_CUDA;
   }
   if (r == MM_OK) {
     if (launch_gl_nodes(kGlNodes, p->glx, p->glw, 0) != cudaSuccess) r = MM_ERR_CUDA;
@@ -1165,10 +1157,8 @@ mm_status mm_estimate_host(mm_plan p, const int64_t* h_offsets, const double* h_
   MM_CUDA(cudaStreamSynchronize(st));
   const int f = *p->h_status;
   if (f) {
-    // as mm_plan_sync: clear the status, and a split FFT's pair words after a timed-out wait
+    // as mm_plan_sync: clear the status
     MM_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), st));
-    if ((f & ST_TIMEOUT) && p->fft_sync)
-      MM_CUDA(cudaMemsetAsync(p->fft_sync, 0, 2 * (size_t)p->desc.D * sizeof(int), st));
     MM_CUDA(cudaStreamSynchronize(st));
   }
   return flags_to_status(f);
@@ -1187,7 +1177,7 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
   std::vector<Cand> cands;
   const int tmax = spread_max_tile(p->fp64);
   if (!p->fp64) {
-    for (int split : {1, 2, 3, 4})  // 3: two CTAs per asset as a cluster; 4: three CTAs as a cluster
+    for (int split : {1, 3})  // 3: two CTAs per asset as a cluster
       for (int maxr : {16, 32}) {
         for (int tile : {tmax / 4, tmax / 2, tmax}) cands.push_back({0, tile, -1, -1, 0, split, maxr, 1});
         if (split == 1) cands.push_back({0, tmax / 2, -1, -1, 0, split, maxr, 1, 1});
@@ -1221,7 +1211,7 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
     p->cfg_N = -1;  // force reconfiguration
     if (configure(p, N) != MM_OK) continue;
     if (c.algo == 2 && !p->sp.fused) continue;  // fused variant does not fit
-    if (c.fft == 0 && (!p->use_afft || p->afft.split != (c.split == 3 ? 2 : c.split == 4 ? 3 : c.split) ||
+    if (c.fft == 0 && (!p->use_afft || p->afft.split != (c.split == 3 ? 2 : c.split) ||
                        p->afft.pair != (c.split == 3 ? 1 : 0)))
       continue;  // not available
     // warm-up (also builds the tables for N)
@@ -1310,7 +1300,6 @@ mm_status mm_plan_sync(mm_plan p) {
   MM_CUDA(cudaMemcpy(&f, p->status, sizeof(int), cudaMemcpyDeviceToHost));
   if (f) MM_CUDA(cudaMemset(p->status, 0, sizeof(int)));
   // a timed-out wait may leave a split FFT's pair words set: clear them
-  if ((f & ST_TIMEOUT) && p->fft_sync) MM_CUDA(cudaMemset(p->fft_sync, 0, 2 * (size_t)p->desc.D * sizeof(int)));
   return flags_to_status(f);
 }
 
@@ -1349,7 +1338,7 @@ mm_status mm_plan_get_info(mm_plan p, mm_plan_info* info) {
   info->tuned_ms = p->tune_ms;
   info->fft_algo = p->use_afft ? 0 : 1;
   info->fft_passes = p->use_afft ? p->afft.npass : 0;
-  info->fft_split = p->use_afft ? (p->afft.pair ? 3 : p->afft.split == 3 ? 4 : p->afft.split) : 0;
+  info->fft_split = p->use_afft ? (p->afft.pair ? 3 : 1) : 0;
   info->graphs = p->graphs ? 1 : 0;
   info->graph_launches = p->graph_launches;
   info->gram_algo = p->gram_used;

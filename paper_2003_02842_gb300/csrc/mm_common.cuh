@@ -131,8 +131,8 @@ constexpr int kMaxAssetPasses = 4;
 struct AssetFft {
   int n;
   int nl;
-  int split;    // CTAs per asset: 1, 2 (radix-2 step on load), 3 (radix-3 step on load)
-  int pair;     // split 2 as a cluster of two CTAs (decimation in time by 2)
+  int split;    // CTAs per asset: 1, or 2 as a cluster (pair)
+  int pair;     // split 2: a cluster of two CTAs (decimation in time by 2)
   int pre_perm; // split 1: the spread kernel stored the grid in digit-reversed order
   int dif;      // decimation in frequency (natural-order input); else in time
   int N;
@@ -216,12 +216,9 @@ cudaError_t launch_coeff_fused(bool fp64, const int64_t* off, const double* t, c
 size_t fft_cols_smem(const FftParams& f, bool fp64);
 bool asset_fft_radix_ok(int R);
 size_t asset_fft_smem(const AssetFft& f);
-int asset_fft_threads(int split);
 cudaError_t launch_asset_twiddles(const AssetFft& f, void* tw, cudaStream_t s);
-// sync: 2 ints per asset, zero between launches (used by the three-CTA split)
 cudaError_t launch_fft_asset(const float* grid, const AssetFft& f, int D, const void* W, const void* tw,
-                             const void* U, const void* decon, void* coeffs, int* status, int* sync,
-                             cudaStream_t s);
+                             const void* U, const void* decon, void* coeffs, int* status, cudaStream_t s);
 size_t fft_rows_smem(const FftParams& f, bool fp64);
 
 cudaError_t launch_gram_weights(int basis, int N, bool fp64, void* wsq, cudaStream_t s);

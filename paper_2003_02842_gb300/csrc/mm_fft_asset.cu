@@ -4,21 +4,13 @@
 // of Eq. (13) taken as an n = M_r/2-point complex FFT, and its deconvolved,
 // truncated coefficients of Eq. (14) are written for k = 0..N.
 //
-// An asset is handled by S = 1, 2 or 3 CTAs. With S > 1 the first radix-S step
-// of the transform (decimation in frequency) is done while loading: CTA c
-// keeps the sequence
-//   y_c[j] = w_n^{c j} sum_{s<S} w_S^{c s} z[j + s n/S],   j < L = n/S,
-// whose L-point DFT gives the outputs of class c, Z_{S k'+c}. The real-input
-// unpacking pairs Z_k with Z_{n-k}, of class -c mod S: with S = 2 that is
-// the CTA's own class, so each CTA finishes its half of the modes alone. With
-// S = 3 the classes 1 and 2 complete each other's modes: each mode is the sum
-// of a term from Z_k and a term from conj Z_{n-k}; each of the two CTAs forms
-// its terms for both classes, the first to get there stores them into the
-// output, and the second adds its own (it waits, with a time limit, only for
-// a CTA that is already running, so no co-residency is assumed). A workload
-// of fewer assets than SMs thus spreads each asset's FFT over two or three
-// SMs.
-//
+// An asset is handled by one CTA when its row fits one CTA's shared memory,
+// else by a cluster of two CTAs (decimation in time by 2, the halves joined
+// through distributed shared memory; k_fft_asset_pair below). Two or three
+// CTAs per asset with the first radix-2 or radix-3 step done while loading
+// were measured slower on every workload and are not built: each CTA's time
+// is set by latency, so splitting an asset only added load work.
+
 // The local transform of L = R_1 R_2 ... R_s points (every R_p <= 32) runs in
 // place in shared memory, pass p working on blocks of length L_p = R_p m_p
 // with stride m_p = L / (R_1 ... R_p): each butterfly's R_p points are
@@ -27,8 +19,7 @@
 // folded into immediates) and stored back. With k = q_1 + R_1 (q_2 + R_2 (q_3
 // + ...)) and rev(k) = sum_p q_p m_p, two orders are used:
 //  - decimation in frequency (the default): natural-order input, so the grid
-//    row lands in shared memory by bulk asynchronous copies (or, with a split,
-//    in coalesced order); passes p = 1..s multiply output q of butterfly j by
+//    row lands in shared memory by bulk asynchronous copies; passes p = 1..s multiply output q of butterfly j by
 //    w_{L_p}^{j q} after the DFT; output k ends up at position rev(k), which
 //    the unpacking step reads;
 //  - decimation in time: input k stored at position rev(k) (as the polynomial
@@ -336,94 +327,17 @@ __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-constexpr int kLoadBatch = 8;     // global loads in flight per thread (split load)
 constexpr uint32_t kBulkChunk = 32768;  // bytes per bulk copy instruction
 constexpr int kUnpackBatch = 8;   // table reads in flight per thread in the unpacking step
 constexpr int kPairBatch = 4;     // the same for the cluster variant (more values per mode)
 constexpr int kPairThreads = 512; // one CTA of a pair per SM (each holds half an asset's grid)
-
-// Classes c and 3 - c (c = 1, 2) of a three-CTA split complete each other's
-// modes: mode k of class c is d_k (alpha_k Z_k + beta_k conj Z_{n-k}) with
-// Z_k in this CTA (output q, k = c + 3q) and Z_{n-k} in the partner; mode k
-// of the partner's class takes this CTA's output L - 1 - q (k = 3 - c + 3q)
-// as its conj Z_{n-k}. Both terms are formed in place in shared memory (the
-// slots [0, Q_c) and [L - Q_{3-c}, L) are disjoint since N < n/2), then
-// sync[0] orders the pair: the first CTA stores its terms into the output
-// and raises sync[1]; the second waits for that flag (bounded), adds its
-// terms to the stored ones and clears both words for the next launch. The
-// sum of two rounded terms is the same whichever CTA comes first.
-template <int NTH>
-__device__ __forceinline__ void pair_terms(Cplx<float>* s, const AssetFft& f, const RevTab& rt, int c,
-                                           const Cplx<float>* __restrict__ U, const float* __restrict__ decon,
-                                           Cplx<float>* oa, int* sync, int* status) {
-  const int L = f.nl;
-  const int cp = 3 - c;
-  const int Qc = c <= f.N ? (f.N - c) / 3 + 1 : 0;
-  const int Qp = cp <= f.N ? (f.N - cp) / 3 + 1 : 0;
-  for (int q = threadIdx.x; q < Qc + Qp; q += NTH) {
-    const bool own = q < Qc;
-    const int k = own ? c + 3 * q : cp + 3 * (q - Qc);
-    const int slot = out_pos(own ? q : L - 1 - (q - Qc), f, rt);
-    const float dk = __ldg(decon + k);
-    const Cplx<float> u = U[k];
-    const Cplx<float> z = own ? s[slot] : cconj(s[slot]);
-    // alpha = (1 + u.y, -u.x) / 2, beta = (1 - u.y, u.x) / 2
-    const Cplx<float> ab = own ? Cplx<float>{0.5f * (1.0f + u.y), -0.5f * u.x}
-                               : Cplx<float>{0.5f * (1.0f - u.y), 0.5f * u.x};
-    const Cplx<float> t = cmul(ab, z);
-    s[slot] = Cplx<float>{t.x * dk, t.y * dk};
-  }
-  __shared__ int s_role;
-  __syncthreads();
-  if (threadIdx.x == 0) s_role = atomicAdd(sync, 1);
-  __syncthreads();
-  if (s_role == 0) {
-    for (int q = threadIdx.x; q < Qc + Qp; q += NTH) {
-      const bool own = q < Qc;
-      oa[own ? c + 3 * q : cp + 3 * (q - Qc)] = s[out_pos(own ? q : L - 1 - (q - Qc), f, rt)];
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) atomicExch(sync + 1, 1);
-    return;
-  }
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) {
-    // the first CTA is running (it took the counter): its flag comes
-    const uint64_t t0 = globaltimer_ns();
-    int ok = 0;
-    for (;;) {
-      int v;
-      asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(sync + 1) : "memory");
-      if (v == 1) {
-        ok = 1;
-        break;
-      }
-      if (globaltimer_ns() - t0 > kWaitLimitNs) break;
-      __nanosleep(64);
-    }
-    if (!ok) atomicOr(status, ST_TIMEOUT);
-    sync[0] = 0;
-    sync[1] = 0;
-    s_ok = ok;
-  }
-  __syncthreads();
-  if (!s_ok) return;
-  for (int q = threadIdx.x; q < Qc + Qp; q += NTH) {
-    const bool own = q < Qc;
-    const int k = own ? c + 3 * q : cp + 3 * (q - Qc);
-    const Cplx<float> t = s[out_pos(own ? q : L - 1 - (q - Qc), f, rt)];
-    const float2 o = __ldcg(reinterpret_cast<const float2*>(oa + k));
-    oa[k] = Cplx<float>{t.x + o.x, t.y + o.y};
-  }
-}
 
 template <int NTH>
 __global__ void __launch_bounds__(NTH, 512 / NTH)
     k_fft_asset(const float* __restrict__ grid, AssetFft f, const Cplx<float>* __restrict__ W,
                 const Cplx<float>* __restrict__ tw, const Cplx<float>* __restrict__ U,
                 const float* __restrict__ decon, Cplx<float>* __restrict__ out, const int* __restrict__ gate,
-                int* status, int* __restrict__ sync) {
+                int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cplx<float>* s = reinterpret_cast<Cplx<float>*>(smem_raw);
   float4* anc = reinterpret_cast<float4*>(smem_raw + anchor_offset(f.nl));  // twiddle anchors, 32 B per row
@@ -442,12 +356,10 @@ __global__ void __launch_bounds__(NTH, 512 / NTH)
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src + i) : "memory");
     }
   }
-  const int c = blockIdx.x;  // which half of the modes (S = 2), else 0
   const int a = blockIdx.y;
   const int L = f.nl;
 
-  // load in the order of the transform's direction (with the first radix-S
-  // step when S > 1)
+  // load in the order of the transform's direction
   const Cplx<float>* z = reinterpret_cast<const Cplx<float>*>(grid) + (size_t)a * f.n;
   if (f.pre_perm || (f.dif && f.split == 1)) {
     // the row as stored (natural order, or digit-reversed by the polynomial
@@ -480,64 +392,12 @@ __global__ void __launch_bounds__(NTH, 512 / NTH)
       __syncthreads();
       return;
     }
-  } else if (f.split == 1) {
+  } else {
     // asynchronous 8-byte copies straight into their shared-memory slots:
     // the whole grid row is in flight at once, no registers held
     for (int j = threadIdx.x; j < L; j += NTH) {
       const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s + digit_rev(j, f, mr));
       asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(z + j) : "memory");
-    }
-  } else if (f.split == 3) {
-    // radix-3 step: w_3^c z1 + w_3^{2c} z2 = -(z1 + z2)/2 -+ i sin(pi/3) (z1 - z2)
-    // (upper sign for c = 1), then the twiddle w_n^{c j}
-    constexpr float kH = 0.86602540378443865f;  // sin(pi/3)
-    const float hs = c == 1 ? kH : -kH;
-    for (int j0 = threadIdx.x; j0 < L; j0 += NTH * kLoadBatch) {
-      Cplx<float> z0[kLoadBatch], z1[kLoadBatch], z2[kLoadBatch], w[kLoadBatch];
-#pragma unroll
-      for (int u = 0; u < kLoadBatch; ++u) {
-        const int j = j0 + u * NTH;
-        if (j < L) {
-          z0[u] = z[j];
-          z1[u] = z[j + L];
-          z2[u] = z[j + 2 * L];
-          if (c) w[u] = W[c * j];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kLoadBatch; ++u) {
-        const int j = j0 + u * NTH;
-        if (j < L) {
-          const Cplx<float> sm = cadd(z1[u], z2[u]), df = csub(z1[u], z2[u]);
-          Cplx<float> y;
-          if (c == 0) {
-            y = cadd(z0[u], sm);
-          } else {
-            y = Cplx<float>{fmaf(hs, df.y, fmaf(-0.5f, sm.x, z0[u].x)), fmaf(-hs, df.x, fmaf(-0.5f, sm.y, z0[u].y))};
-            y = cmul(y, w[u]);
-          }
-          s[f.dif ? j : digit_rev(j, f, mr)] = y;
-        }
-      }
-    }
-  } else {
-    for (int j0 = threadIdx.x; j0 < L; j0 += NTH * kLoadBatch) {
-      Cplx<float> y[kLoadBatch], z1[kLoadBatch], w[kLoadBatch];
-#pragma unroll
-      for (int u = 0; u < kLoadBatch; ++u) {
-        const int j = j0 + u * NTH;
-        if (j < L) {
-          y[u] = z[j];
-          z1[u] = z[j + L];
-          if (c) w[u] = W[j];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kLoadBatch; ++u) {
-        const int j = j0 + u * NTH;
-        if (j < L)
-          s[f.dif ? j : digit_rev(j, f, mr)] = c == 0 ? cadd(y[u], z1[u]) : cmul(csub(y[u], z1[u]), w[u]);
-      }
     }
   }
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
@@ -548,22 +408,15 @@ __global__ void __launch_bounds__(NTH, 512 / NTH)
   // G(k) = (Z_k + conj Z_{n-k}) / 2 + w_{2n}^k (Z_k - conj Z_{n-k}) / (2i)
   //      = alpha_k Z_k + beta_k conj Z_{n-k},
   // alpha_k = (1 - i w_{2n}^k) / 2, beta_k = (1 + i w_{2n}^k) / 2, for the
-  // modes k = c + S q <= N of this CTA's class. Z_k is its own output q, and
-  // Z_{n-k} is output L - q (c = 0; 0 for k = 0) or L - 1 - q (c > 0) of
-  // class -c mod S. U[k] = w_{2n}^k and the deconvolution factors are read
-  // kUnpackBatch at a time per thread.
-  const int S = f.split;
+  // modes k <= N (Z_0 pairs with itself). U[k] = w_{2n}^k and the
+  // deconvolution factors are read kUnpackBatch at a time per thread.
   Cplx<float>* oa = out + (size_t)a * (f.N + 1);
-  if (S == 3 && c != 0) {
-    pair_terms<NTH>(s, f, rt, c, U, decon, oa, sync + 2 * a, status);
-    return;
-  }
-  for (int q0 = threadIdx.x; c + S * q0 <= f.N; q0 += NTH * kUnpackBatch) {
+  for (int k0 = threadIdx.x; k0 <= f.N; k0 += NTH * kUnpackBatch) {
     float dk[kUnpackBatch];
     Cplx<float> Uk[kUnpackBatch];
 #pragma unroll
     for (int u = 0; u < kUnpackBatch; ++u) {
-      const int k = c + S * (q0 + u * NTH);
+      const int k = k0 + u * NTH;
       if (k <= f.N) {
         dk[u] = __ldg(decon + k);
         Uk[u] = U[k];
@@ -571,12 +424,11 @@ __global__ void __launch_bounds__(NTH, 512 / NTH)
     }
 #pragma unroll
     for (int u = 0; u < kUnpackBatch; ++u) {
-      const int q = q0 + u * NTH;
-      const int k = c + S * q;
+      const int k = k0 + u * NTH;
       if (k <= f.N) {
-        const int qn = c == 0 ? (q == 0 ? 0 : L - q) : L - 1 - q;
-        const Cplx<float> Zk = s[out_pos(q, f, rt)];
-        const Cplx<float> Zc = cconj(s[out_pos(qn, f, rt)]);
+        const int kn = k == 0 ? 0 : L - k;
+        const Cplx<float> Zk = s[out_pos(k, f, rt)];
+        const Cplx<float> Zc = cconj(s[out_pos(kn, f, rt)]);
         const Cplx<float> E = {0.5f * (Zk.x + Zc.x), 0.5f * (Zk.y + Zc.y)};
         const Cplx<float> dlt = csub(Zk, Zc);
         const Cplx<float> O = {0.5f * dlt.y, -0.5f * dlt.x};  // (Z_k - conj Z_{n-k}) / (2i)
@@ -704,8 +556,6 @@ size_t asset_fft_smem(const AssetFft& f) {
   return anchor_offset(f.nl) + (size_t)f.tw_rows * 32 + (f.dif ? (size_t)(f.rev_lo + f.rev_hi) * 4 : 0);
 }
 
-int asset_fft_threads(int split) { return split >= 2 ? 256 : 512; }
-
 cudaError_t launch_asset_twiddles(const AssetFft& f, void* tw, cudaStream_t s) {
   int cnt = 1;
   for (int p = 0; p < f.npass; ++p) cnt = std::max(cnt, 4 * f.stride[p]);
@@ -714,30 +564,20 @@ cudaError_t launch_asset_twiddles(const AssetFft& f, void* tw, cudaStream_t s) {
 }
 
 cudaError_t launch_fft_asset(const float* grid, const AssetFft& f, int D, const void* W, const void* tw,
-                             const void* U, const void* decon, void* coeffs, int* status, int* sync,
-                             cudaStream_t s) {
-  if (f.split == 3 && !sync) return cudaErrorInvalidValue;
+                             const void* U, const void* decon, void* coeffs, int* status, cudaStream_t s) {
   const size_t smem = asset_fft_smem(f);
-  dim3 grd(f.split, D);
   auto set = [&](auto fn) { return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); };
   cudaError_t e;
   if (f.pair) {
     if ((e = set(k_fft_asset_pair<kPairThreads>)) != cudaSuccess) return e;
-    return launch_pdl(k_fft_asset_pair<kPairThreads>, grd, dim3(kPairThreads), smem, s, grid, f,
+    return launch_pdl(k_fft_asset_pair<kPairThreads>, dim3(2, D), dim3(kPairThreads), smem, s, grid, f,
                       (const Cplx<float>*)W, (const Cplx<float>*)tw, (const Cplx<float>*)U, (const float*)decon,
                       (Cplx<float>*)coeffs, (const int*)(status + 1));
-  } else if (asset_fft_threads(f.split) == 256) {
-    if ((e = set(k_fft_asset<256>)) != cudaSuccess) return e;
-    return launch_pdl(k_fft_asset<256>, grd, dim3(256), smem, s, grid, f, (const Cplx<float>*)W,
-                      (const Cplx<float>*)tw, (const Cplx<float>*)U, (const float*)decon, (Cplx<float>*)coeffs,
-                      (const int*)(status + 1), status, sync);
-  } else {
-    if ((e = set(k_fft_asset<512>)) != cudaSuccess) return e;
-    return launch_pdl(k_fft_asset<512>, grd, dim3(512), smem, s, grid, f, (const Cplx<float>*)W,
-                      (const Cplx<float>*)tw, (const Cplx<float>*)U, (const float*)decon, (Cplx<float>*)coeffs,
-                      (const int*)(status + 1), status, sync);
   }
-  return cudaGetLastError();
+  if ((e = set(k_fft_asset<512>)) != cudaSuccess) return e;
+  return launch_pdl(k_fft_asset<512>, dim3(1, D), dim3(512), smem, s, grid, f, (const Cplx<float>*)W,
+                    (const Cplx<float>*)tw, (const Cplx<float>*)U, (const float*)decon, (Cplx<float>*)coeffs,
+                    (const int*)(status + 1), status);
 }
 
 }  // namespace mmgpu

@@ -43,8 +43,8 @@ def test_status_strings_and_version(lib):
 
 @pytest.mark.parametrize("field,value", [
     ("D", 0), ("N_max", -1), ("tol", 0.0), ("tol", 0.7), ("kernel", 7), ("basis", 3), ("prec", 9),
-    ("max_events", -5), ("spread_tile", -1), ("spread_algo", 5), ("spread_algo", -1),
-    ("fft_algo", 7), ("fft_algo", -1),
+    ("max_events", -5), ("spread_tile", -1), ("spread_algo", 4), ("spread_algo", -1),
+    ("fft_algo", 6), ("fft_algo", 3), ("fft_algo", -1),
 ])
 def test_bad_desc_rejected_on_host(lib, field, value):
     from paper_2003_02842_gb300 import _lib
