@@ -694,7 +694,7 @@ constexpr int kRoundMagicBits = 0x4B400000;
 constexpr int kPolyChunk = 1024;
 
 template <int NT>
-__global__ void __launch_bounds__(kSpreadThreads) k_spread_poly(const int64_t* __restrict__ off,
+__global__ void __launch_bounds__(kSpreadThreads, 5) k_spread_poly(const int64_t* __restrict__ off,
                                                                const int* __restrict__ rb0,
                                                                const float* __restrict__ rd,
                                                                const float* __restrict__ rv,
@@ -776,27 +776,87 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_poly(const int64_t* _
         load_record<float>(rb0, rd, rv, p, tr, L, cs + i, ev_p[i], ev_d[i], ev_v[i]);
     }
     __syncthreads();
-    for (int ei = threadIdx.x; ei < n; ei += kSpreadThreads) {
-      const int pe = ev_p[ei];
-      if (pe == kNoCell) continue;
-      const float z = ev_d[ei] - 0.5f;
-      const float vs = ev_v[ei] * scale;
-      const int c0 = pe + klo;
-      const bool inside = c0 >= 0 && c0 + NT <= Tlen;  // else test each tap's cell
+    if (2 * n < Tlen) {
+      // sparse: one record per lane, its taps added at once (neighbouring
+      // lanes' records rarely share a cell)
+      for (int ei = threadIdx.x; ei < n; ei += kSpreadThreads) {
+        const int pe = ev_p[ei];
+        if (pe == kNoCell) continue;
+        const float z = ev_d[ei] - 0.5f;
+        const float vs = ev_v[ei] * scale;
+        const int c0 = pe + klo;
+        const bool inside = c0 >= 0 && c0 + NT <= Tlen;  // else test each tap's cell
 #pragma unroll
-      for (int j = 0; j < NT; ++j) {
-        float w = poly.c[j][kPolyDeg];
+        for (int j = 0; j < NT; ++j) {
+          float w = poly.c[j][kPolyDeg];
 #pragma unroll
-        for (int i = kPolyDeg - 1; i >= 0; --i) w = fmaf(w, z, poly.c[j][i]);
-        const float h = fmaf(vs, w, kRoundMagic);      // round(vs w) + 1.5 2^23
-        const float r = fmaf(vs, w, kRoundMagic - h);  // vs w - round(vs w), |r| <= 1/2
-        const float l = fmaf(r, kscale, kRoundMagic);
-        const unsigned c = (unsigned)(c0 + j);
-        if (inside || c < (unsigned)Tlen) {
-          red_shared_add(hi_s + 4u * c, __float_as_int(h) - kRoundMagicBits);
-          red_shared_add(lo_s + 4u * c, __float_as_int(l) - kRoundMagicBits);
+          for (int i = kPolyDeg - 1; i >= 0; --i) w = fmaf(w, z, poly.c[j][i]);
+          const float h = fmaf(vs, w, kRoundMagic);      // round(vs w) + 1.5 2^23
+          const float r = fmaf(vs, w, kRoundMagic - h);  // vs w - round(vs w), |r| <= 1/2
+          const float l = fmaf(r, kscale, kRoundMagic);
+          const unsigned c = (unsigned)(c0 + j);
+          if (inside || c < (unsigned)Tlen) {
+            red_shared_add(hi_s + 4u * c, __float_as_int(h) - kRoundMagicBits);
+            red_shared_add(lo_s + 4u * c, __float_as_int(l) - kRoundMagicBits);
+          }
         }
       }
+      continue;
+    }
+    // dense (at least one record per two cells): each thread takes a
+    // contiguous stretch of the staged (cell-sorted) records and, for each
+    // run of records in one cell, sums their taps in registers (exact integer
+    // sums, within the same per-cell bounds) before adding them to the tiles;
+    // one record per lane would have the lanes of a warp reduce into the same
+    // few cells at once. A run is swept twice, for the first and the second
+    // half of the taps, so that only half the sums are live. An odd stretch
+    // keeps the lanes' staged reads on distinct banks.
+    constexpr int H = (NT + 1) / 2;
+    int cnt = (n + kSpreadThreads - 1) / kSpreadThreads;
+    cnt |= 1;
+    const int e0 = min(n, (int)threadIdx.x * cnt), e1 = min(n, e0 + cnt);
+    for (int ei = e0; ei < e1;) {
+      const int pe = ev_p[ei];
+      int ej = ei + 1;
+      while (ej < e1 && ev_p[ej] == pe) ++ej;
+      if (pe != kNoCell) {
+        const int c0 = pe + klo;
+        const bool inside = c0 >= 0 && c0 + NT <= Tlen;  // else test each tap's cell
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          int ah[H], al[H];
+#pragma unroll
+          for (int q = 0; q < H; ++q) ah[q] = al[q] = 0;
+          for (int e = ei; e < ej; ++e) {
+            const float z = ev_d[e] - 0.5f;
+            const float vs = ev_v[e] * scale;
+#pragma unroll
+            for (int q = 0; q < H; ++q) {
+              const int j = half * H + q;
+              if (j < NT) {
+                float w = poly.c[j][kPolyDeg];
+#pragma unroll
+                for (int i = kPolyDeg - 1; i >= 0; --i) w = fmaf(w, z, poly.c[j][i]);
+                const float h = fmaf(vs, w, kRoundMagic);      // round(vs w) + 1.5 2^23
+                const float r = fmaf(vs, w, kRoundMagic - h);  // vs w - round(vs w), |r| <= 1/2
+                const float l = fmaf(r, kscale, kRoundMagic);
+                ah[q] += __float_as_int(h) - kRoundMagicBits;
+                al[q] += __float_as_int(l) - kRoundMagicBits;
+              }
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < H; ++q) {
+            const int j = half * H + q;
+            const unsigned c = (unsigned)(c0 + j);
+            if (j < NT && (inside || c < (unsigned)Tlen)) {
+              red_shared_add(hi_s + 4u * c, ah[q]);
+              red_shared_add(lo_s + 4u * c, al[q]);
+            }
+          }
+        }
+      }
+      ei = ej;
     }
   }
   __syncthreads();
