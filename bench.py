@@ -38,7 +38,8 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 NCU_TRAFFIC = {
     # the block workload in its default configuration
     # (profiles/c3_block_D100_N10000_kernels_ncu.md)
-    ("fft", "c3", "bf16x3", "es"): 16451584,
+    ("fft", "c3", "bf16x3", "es"): 16442880,
+    ("spread", "c3", "bf16x3", "es"): 9236224,
     ("prep", "c3", "bf16x3", "es"): 12287488,
     ("gram", "c3", "bf16x3", "es"): 8115712,
     # the pre-split contraction alone at D = 500, N = 14400
@@ -55,7 +56,7 @@ NCU_SOURCE = {
 # M_r = 57600), scaled by the rows of a launch (the traffic is the rows' grid
 # reads and coefficient writes, so it grows with them)
 NCU_TRAFFIC_PER_ROW = {
-    ("fft", "c4", "bf16x3", "es", 57600): 334006.0,
+    ("fft", "c4", "bf16x3", "es", 57600): (590240768 + 264606464) / 2560.0,
 }
 
 # Stages (a)-(c) of the hot path, as the library's profiler names them.
