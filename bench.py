@@ -63,7 +63,7 @@ NCU_TRAFFIC_PER_ROW = {
 COEFF_STAGES = ("prep", "spread", "fft_cols", "fft_rows", "fft", "fused")
 
 
-def hbm_roofline(stage_ms, n_events, D, N, Mr, fp64, peaks, peak_src, traffic_key):
+def hbm_roofline(stage_ms, n_events, D, N, Mr, fp64, peaks, peak_src, traffic_key, resident=False):
     """Roofline of the dominant kernel and of the coefficient chain (a)-(c).
 
     Algorithmic bytes follow the scope table's measurement rule: 16 B per
@@ -72,7 +72,9 @@ def hbm_roofline(stage_ms, n_events, D, N, Mr, fp64, peaks, peak_src, traffic_ke
     the coefficients once. Per kernel: the prep kernel owns the event reads,
     the FFT (or the fused kernel) the coefficient writes, the contraction the
     coefficient reads. Records and grid rows written and read back between
-    kernels are implementation bytes, reported beside them."""
+    kernels are implementation bytes, reported beside them. The resident
+    spread + FFT kernel (after the prep kernel) reads the records and writes
+    the coefficients; the one-CTA fused kernel reads the events itself."""
     cb = 16 if fp64 else 8
     gb = 8 if fp64 else 4
     rb = 4 + 2 * gb  # per-event record (cell, offset, return)
@@ -84,6 +86,9 @@ def hbm_roofline(stage_ms, n_events, D, N, Mr, fp64, peaks, peak_src, traffic_ke
     # bytes as the complex64 coefficients) instead of the coefficients
     impl = {"prep": float(rb * n_events), "spread": rb * n_events + grid, "fft_cols": 2.0 * grid,
             "fft_rows": grid, "fft": grid, "fused": 0.0, "gram": 0.0, "reduce": 0.0, "split": 2.0 * coef}
+    if resident:
+        alg["fused"] = coef
+        impl["fused"] = float(rb * n_events)
     timed = {k: v for k, v in stage_ms.items() if k != "setup" and v > 0}
     dom = max(timed, key=lambda k: timed[k])
     avg = timed[dom]
@@ -334,7 +339,7 @@ def bench_batch(args):
     tt = torch.from_numpy(ev.t).to(dev)
     lp = torch.from_numpy(ev.logp).to(dev)
     b = mm.mm_batch_create(reps, Dg, Nmax, ev.n_events, tol=1e-6, kernel=args.kernel, basis="dirichlet",
-                           prec=args.prec)
+                           prec=args.prec, spread_algo=args.spread_algo)
     tuned = None
     if args.autotune:
         tuned = mm.mm_batch_autotune(b, off, tt, lp, Nmax, reps=2)
@@ -441,7 +446,7 @@ def bench_batch(args):
         Mr = i1["Mr"]
         Dtot = reps * Dg
         roof = hbm_roofline(stage_ms, ev.n_events, Dtot, Nmax, Mr, False, peaks, peak_src,
-                            ("c4", args.prec, args.kernel))
+                            ("c4", args.prec, args.kernel), resident=stage_ms.get("fused", 0.0) > 0)
         per_row = NCU_TRAFFIC_PER_ROW.get((roof["kernel"], "c4", args.prec, args.kernel, int(Mr)))
         if roof["traffic"] is None and per_row is not None:
             roof["traffic"] = per_row * Dtot
@@ -463,7 +468,7 @@ def bench_batch(args):
                        "contraction": "prefix-weighted sweep, float32 accumulate",
                        "l2": "inputs larger than L2 (no flush)", "grid_Mr": Mr,
                        "fft_algo": "per-asset shared-memory" if i1["fft_algo"] == 0 else "two-pass",
-                       "fft_split": i1["fft_split"], "spread_tile": i1["spread_tile"],
+                       "fft_split": i1["fft_split"], "spread_tile": i1["spread_tile"], "spread_algo": args.spread_algo,
                        "graph_kernels": i1["graph_kernels"], "autotuned": tuned is not None, "replicas": world},
             "matrices_per_s": world * reps * J * args.steps / (total_ms * 1e-3),
             "stage_ms": stage_ms,
@@ -860,7 +865,7 @@ def main():
         stage_ms = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in stages.items()}
         Mr = info["Mr"]
         roof = hbm_roofline(stage_ms, ev.n_events, D, N, Mr, args.prec == "fp64", peaks, peak_src,
-                            (args.workload, args.prec, args.kernel))
+                            (args.workload, args.prec, args.kernel), resident=info["res_sub"] > 0)
         ev_c, secs, assets, threads = oracle_rate(ev, N, args.cpu_budget)
         cpu = {"value": ev_c / secs if secs > 0 else 0.0, "unit": "events/s", "cores": threads, "kind": "oracle",
                "sample": f"direct sum of Eq. (4), k=0..N, on {assets} of {D} assets (~{secs:.1f} s, "
@@ -876,8 +881,9 @@ def main():
                        "events": ev.n_events, "kernel": args.kernel, "tol": tol, "basis": "dirichlet",
                        "contraction": args.prec, "l2": "flushed between steps (256 MB write)",
                        "grid_Mr": Mr, "fft": [info["fft_P"], info["fft_Q"]], "gram_splits": info["gram_splits"],
-                       "spread_algo": {1: "scatter", 2: "gather", 3: "fused"}.get(info["spread_algo"]),
-                       "spread_tile": info["spread_tile"], "fft_blocking": [info["fft_lg_cols"], info["fft_rowblk"]],
+                       "spread_algo": ("resident" if info["res_sub"] > 0 else
+                                       {1: "scatter", 2: "gather", 3: "fused"}.get(info["spread_algo"])),
+                       "spread_tile": info["res_sub"] or info["spread_tile"], "fft_blocking": [info["fft_lg_cols"], info["fft_rowblk"]],
                        "fft_algo": "per-asset shared-memory" if info["fft_algo"] == 0 else "two-pass",
                        "fft_radix": info["fft_radix"], "fft_split": info["fft_split"],
                        "autotuned": tuned is not None,

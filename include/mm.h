@@ -104,9 +104,13 @@ typedef struct {
                            path evaluates the kernel as per-tap polynomials and
                            accumulates exactly in integers); 2 as 1 with a gather per
                            grid cell (no atomics: the FP64 path's sums then come out
-                           in a fixed order); 3 stages (a)-(c) fused in one CTA per
-                           asset when the grid fits in shared memory, else 1. All
-                           compute Eq. (12). */
+                           in a fixed order); 3 stages (a2)-(c) in one launch with
+                           each asset's grid row resident in shared memory (one CTA
+                           per row, or a cluster of two for rows too large for one;
+                           the mixed path with polynomial taps, after the prep
+                           kernel), or, where that does not apply, stages (a)-(c)
+                           in one CTA per asset for a single problem whose grid fits
+                           in shared memory; else 1. All compute Eq. (12). */
   int32_t fft_algo;     /* stages (b)-(c) in the mixed precisions: 0 library default
                            (the grid in shared memory when it fits: as 2 when one
                            asset's row fits one CTA, else as 4; otherwise 1);
@@ -146,7 +150,8 @@ typedef struct {
   int64_t workspace_bytes;
   int64_t launches;      /* kernels launched by this plan since creation */
   int32_t gram_splits;   /* split-K factor of the last contraction */
-  int32_t spread_algo;   /* stage (a)-(c) variant in use: 1 scatter, 2 gather, 3 fused */
+  int32_t spread_algo;   /* stage (a)-(c) variant in use: 1 scatter, 2 gather, 3 fused
+                            (the resident row when res_sub > 0) */
   int32_t spread_tile;   /* grid cells per spreading block in use */
   int32_t fft_lg_cols;   /* FFT pass 1: log2 of the columns per block */
   int32_t fft_rowblk;    /* FFT pass 2: lower rows per block */
@@ -162,7 +167,8 @@ typedef struct {
   int64_t graph_launches; /* mm_estimate calls served by a graph replay since creation */
   int32_t gram_algo;     /* stage (d) of the last contraction: 1 in-register conversion,
                             2 pre-split operand by TMA, 3 FP64 path; 0 before the first */
-  int32_t reserved_info;
+  int32_t res_sub;       /* spread_algo 3 with the grid row resident after the prep kernel:
+                            cells per sub-range of the row; 0 when not in use */
 } mm_plan_info;
 
 /* Create a plan: validates desc, allocates the workspace on the current
@@ -353,7 +359,8 @@ typedef struct {
                             MM_PREC_FP64: the same form in float64 throughout
                             (complex128 coefficients, float64 Sigma and R): the
                             mixed form's comparator */
-  int32_t reserved[5];   /* must be zero */
+  int32_t spread_algo;   /* stages (a)-(c) as mm_plan_desc.spread_algo (0 .. 3) */
+  int32_t reserved[4];   /* must be zero */
 } mm_batch_desc;
 
 typedef struct mm_batch_s* mm_batch;

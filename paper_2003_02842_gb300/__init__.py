@@ -366,14 +366,16 @@ class Batch:
             self.handle = None
 
 
-def mm_batch_create(reps, D, N_max, max_events, tol=1e-6, kernel="es", basis="dirichlet", prec="bf16x3") -> Batch:
+def mm_batch_create(reps, D, N_max, max_events, tol=1e-6, kernel="es", basis="dirichlet", prec="bf16x3",
+                    spread_algo="default") -> Batch:
     d = _lib.BatchDesc()
     d.reps, d.D, d.N_max, d.max_events, d.tol = int(reps), int(D), int(N_max), int(max_events), float(tol)
     d.kernel, d.basis, d.prec = KERNELS[kernel], BASES[basis], PRECISIONS[prec]
+    d.spread_algo = _lib.SPREAD_ALGOS[spread_algo]
     h = ctypes.c_void_p()
     _check(_lib.load().mm_batch_create(ctypes.byref(d), ctypes.byref(h)), "mm_batch_create")
     return Batch(h, dict(reps=int(reps), D=int(D), N_max=int(N_max), max_events=int(max_events), tol=float(tol),
-                         kernel=kernel, basis=basis, prec=prec))
+                         kernel=kernel, basis=basis, prec=prec, spread_algo=spread_algo))
 
 
 def mm_batch_destroy(batch: Batch):

@@ -67,7 +67,7 @@ class PlanInfo(ctypes.Structure):
         ("graphs", ctypes.c_int32),
         ("graph_launches", ctypes.c_int64),
         ("gram_algo", ctypes.c_int32),
-        ("reserved_info", ctypes.c_int32),
+        ("res_sub", ctypes.c_int32),
     ]
 
 
@@ -82,7 +82,8 @@ class BatchDesc(ctypes.Structure):
         ("kernel", ctypes.c_int),
         ("basis", ctypes.c_int),
         ("prec", ctypes.c_int),
-        ("reserved", ctypes.c_int32 * 5),
+        ("spread_algo", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 

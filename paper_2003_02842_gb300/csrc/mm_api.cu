@@ -296,6 +296,7 @@ struct mm_plan_s {
   int tune_split = -1;    // per-asset FFT: 1 one CTA per asset, 3 the cluster pair
   int tune_maxr = -1;     // per-asset FFT: largest radix (16 or 32)
   int tune_perm = -1;     // 1: the scatter stores the grid in the FFT's input order (split 1)
+  int res_sub = 0;        // > 0: stages (a2)-(c) in one launch, grid row resident (cells per sub-range)
   int64_t Mr = 0;
   FftParams fft{};
   AssetFft afft{};
@@ -469,9 +470,14 @@ mm_status configure(mm_plan p, int N) {
   const bool fits = fused_smem(f, Mr, p->fp64) + 2048 <= (size_t)p->smem_optin;
   int algo = p->desc.spread_algo == 2 ? 1 : (p->desc.spread_algo == 3 ? 2 : 0);
   if (p->tune_algo >= 0) algo = p->tune_algo;
-  if (algo == 2 && (!fits || p->G > 1)) algo = 0;
+  // fused stages: the float32 path keeps the grid row resident after the
+  // prep kernel (below, when the row and its sub-range tiles fit); the FP64
+  // path and rows without the polynomial taps use the one-CTA kernel that also
+  // rescales (a single problem whose grid fits)
+  const bool want_fused = algo == 2;
+  if (algo == 2) algo = 0;
   s.algo = algo == 1 ? 1 : 0;
-  s.fused = algo == 2 ? 1 : 0;
+  s.fused = 0;
   s.tile = tile;
   s.ntiles = (int)((Mr + tile - 1) / tile);
   s.es_beta = 2.3 * 2.0 * p->msp;
@@ -482,8 +488,7 @@ mm_status configure(mm_plan p, int N) {
   s.kb_inv_phi0 = kPi * p->msp / sinh(s.kb_b * p->msp);
   p->tau = kPi * lam / ((double)Mr * (double)Mr);
   p->poly_ok = false;
-  if (!p->fp64 && s.algo == 0 && !s.fused && p->tune_poly != 0 &&
-      spread_poly_supported(s.khi - s.klo + 1)) {
+  if (!p->fp64 && s.algo == 0 && p->tune_poly != 0 && spread_poly_supported(s.khi - s.klo + 1)) {
     // the fit must stay far below the NUFFT tolerance and near float32 rounding
     const double err = fit_kernel_poly(s, &p->poly);
     p->poly_ok = err <= std::max(3.0e-7, 0.1 * p->desc.tol);
@@ -558,6 +563,21 @@ mm_status configure(mm_plan p, int N) {
   // pair, whose joining step reads half its values from the partner's shared
   // memory: those reads must be contiguous (natural output order)
   af.dif = !af.pre_perm && !af.pair;
+  // the resident form: decimation in time (the sub-ranges' points go straight
+  // to their digit reversals, the unpacking reads natural order)
+  p->res_sub = 0;
+  if (want_fused && afft && p->poly_ok) {
+    AssetFft rf = af;
+    rf.pre_perm = 0;
+    rf.dif = 0;
+    const int sub = spread_fft_sub(rf, Mr, (size_t)p->smem_optin - kResStaticSmem);
+    if (sub > 0) {
+      p->res_sub = sub;
+      af = rf;
+      s.perm_np = 0;
+    }
+  }
+  if (want_fused && !p->res_sub && fits && p->G == 1) s.fused = 1;
   p->afft = af;
   p->use_afft = afft && !s.fused;
   p->fft = f;
@@ -703,6 +723,13 @@ mm_status coeffs_impl(mm_plan p, const int64_t* off, const double* t, const doub
       else
         MM_CUDA(launch_prep_f32(off, t, logp, p->bounds, gsc, p->gsize, D, p->Mr, p->desc.max_events, p->rec_b0,
                                 p->rec_d, p->rec_v, p->status, st));
+    }
+    if (p->res_sub > 0) {
+      StageScope sc(p, MM_STAGE_FUSED, st);
+      MM_CUDA(launch_spread_fft(off, p->rec_b0, p->rec_d, p->rec_v, p->sp, p->poly, p->res_sub, p->afft, D, p->W,
+                                p->atw, p->U, p->decon, coeffs, p->status, st));
+      if (N_used) *N_used = N;
+      return MM_OK;
     }
     {
       StageScope sc(p, MM_STAGE_SPREAD, st);
@@ -1183,6 +1210,7 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
         if (split == 1) cands.push_back({0, tmax / 2, -1, -1, 0, split, maxr, 1, 1});
         for (int tile : {tmax / 4, tmax / 2}) cands.push_back({0, tile, -1, -1, 0, split, maxr, 0});
         for (int tile : {tmax / 2, tmax}) cands.push_back({1, tile, -1, -1, 0, split, maxr, 1});
+        cands.push_back({2, tmax, -1, -1, 0, split, maxr, 1});  // the resident row
       }
   }
   for (int tile : {tmax / 4, tmax / 2, tmax})
@@ -1210,7 +1238,7 @@ mm_status mm_autotune(mm_plan p, const int64_t* d_offsets, const double* d_t, co
     p->tune_perm = c.perm;
     p->cfg_N = -1;  // force reconfiguration
     if (configure(p, N) != MM_OK) continue;
-    if (c.algo == 2 && !p->sp.fused) continue;  // fused variant does not fit
+    if (c.algo == 2 && !p->sp.fused && !p->res_sub) continue;  // no fused variant fits
     if (c.fft == 0 && (!p->use_afft || p->afft.split != (c.split == 3 ? 2 : c.split) ||
                        p->afft.pair != (c.split == 3 ? 1 : 0)))
       continue;  // not available
@@ -1330,7 +1358,8 @@ mm_status mm_plan_get_info(mm_plan p, mm_plan_info* info) {
   info->workspace_bytes = p->workspace;
   info->launches = p->launches;
   info->gram_splits = p->gram.splits;
-  info->spread_algo = p->sp.fused ? 3 : (p->sp.algo == 1 ? 2 : 1);
+  info->spread_algo = (p->sp.fused || p->res_sub > 0) ? 3 : (p->sp.algo == 1 ? 2 : 1);
+  info->res_sub = p->res_sub;
   info->spread_poly = p->poly_ok ? 1 : 0;
   info->spread_tile = p->sp.tile;
   info->fft_lg_cols = p->fft.lg_cols;
@@ -1452,8 +1481,9 @@ mm_status mm_batch_create(const mm_batch_desc* desc, mm_batch* out) {
   if (!desc) return MM_ERR_INVALID_ARG;
   const mm_batch_desc& d = *desc;
   if (d.reps < 1 || d.D < 1 || d.N_max < 1 || d.max_events < 0 || d.reserved0 != 0) return MM_ERR_INVALID_ARG;
-  for (int i = 0; i < 5; ++i)
+  for (int i = 0; i < 4; ++i)
     if (d.reserved[i] != 0) return MM_ERR_INVALID_ARG;
+  if (d.spread_algo < 0 || d.spread_algo > 3) return MM_ERR_INVALID_ARG;
   if (d.prec < MM_PREC_FP64 || d.prec > MM_PREC_MIXED_3XTF32) return MM_ERR_INVALID_ARG;
   if (d.D > epps_max_assets()) return MM_ERR_UNSUPPORTED;
   if ((int64_t)d.reps * d.D > (int64_t)1 << 30) return MM_ERR_UNSUPPORTED;
@@ -1465,6 +1495,7 @@ mm_status mm_batch_create(const mm_batch_desc* desc, mm_batch* out) {
   pd.kernel = d.kernel;
   pd.basis = d.basis;
   pd.prec = d.prec;
+  pd.spread_algo = d.spread_algo;
   mm_batch b = new mm_batch_s();
   b->desc = d;
   mm_status r = plan_create_impl(&pd, d.D, true, &b->p);

@@ -219,6 +219,17 @@ size_t asset_fft_smem(const AssetFft& f);
 cudaError_t launch_asset_twiddles(const AssetFft& f, void* tw, cudaStream_t s);
 cudaError_t launch_fft_asset(const float* grid, const AssetFft& f, int D, const void* W, const void* tw,
                              const void* U, const void* decon, void* coeffs, int* status, cudaStream_t s);
+// Stages (a2)-(c) in one launch with the grid row resident in shared
+// memory (one CTA per asset, or the cluster pair for f.pair): records in,
+// coefficients out. sub = cells per sub-range from spread_fft_sub (0: the
+// row does not fit with the staging area within smem_limit).
+constexpr int kResStaticSmem = 4096;  // static shared memory of those kernels, rounded up
+int spread_fft_sub(const AssetFft& f, int64_t Mr, size_t smem_limit);
+size_t spread_fft_smem(const AssetFft& f, int sub);
+cudaError_t launch_spread_fft(const int64_t* off, const int* rb0, const void* rd, const void* rv,
+                              const SpreadParams& sp, const KernelPoly& poly, int sub, const AssetFft& f, int D,
+                              const void* W, const void* tw, const void* U, const void* decon, void* coeffs,
+                              const int* status, cudaStream_t s);
 size_t fft_rows_smem(const FftParams& f, bool fp64);
 
 cudaError_t launch_gram_weights(int basis, int N, bool fp64, void* wsq, cudaStream_t s);

@@ -32,6 +32,7 @@
 #include "mm_async.cuh"
 #include "mm_common.cuh"
 #include "mm_fft_dev.cuh"
+#include "mm_spread_dev.cuh"
 
 namespace mmgpu {
 
@@ -332,6 +333,50 @@ constexpr int kUnpackBatch = 8;   // table reads in flight per thread in the unp
 constexpr int kPairBatch = 4;     // the same for the cluster variant (more values per mode)
 constexpr int kPairThreads = 512; // one CTA of a pair per SM (each holds half an asset's grid)
 
+// The local transform of a row held whole by one CTA, then the unpacking
+// of the real-input transform and the deconvolution of the modes k <= N.
+template <int NTH>
+__device__ __forceinline__ void single_finish(const AssetFft& f, Cplx<float>* s, const float4* anc, int a,
+                                              const RevTab& rt, const Cplx<float>* __restrict__ U,
+                                              const float* __restrict__ decon, Cplx<float>* __restrict__ out) {
+  const int L = f.nl;
+  run_passes(f, s, anc, NTH);
+
+  // unpack the real-input transform and deconvolve (Eq. (14)):
+  // G(k) = (Z_k + conj Z_{n-k}) / 2 + w_{2n}^k (Z_k - conj Z_{n-k}) / (2i)
+  //      = alpha_k Z_k + beta_k conj Z_{n-k},
+  // alpha_k = (1 - i w_{2n}^k) / 2, beta_k = (1 + i w_{2n}^k) / 2, for the
+  // modes k <= N (Z_0 pairs with itself). U[k] = w_{2n}^k and the
+  // deconvolution factors are read kUnpackBatch at a time per thread.
+  Cplx<float>* oa = out + (size_t)a * (f.N + 1);
+  for (int k0 = threadIdx.x; k0 <= f.N; k0 += NTH * kUnpackBatch) {
+    float dk[kUnpackBatch];
+    Cplx<float> Uk[kUnpackBatch];
+#pragma unroll
+    for (int u = 0; u < kUnpackBatch; ++u) {
+      const int k = k0 + u * NTH;
+      if (k <= f.N) {
+        dk[u] = __ldg(decon + k);
+        Uk[u] = U[k];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnpackBatch; ++u) {
+      const int k = k0 + u * NTH;
+      if (k <= f.N) {
+        const int kn = k == 0 ? 0 : L - k;
+        const Cplx<float> Zk = s[out_pos(k, f, rt)];
+        const Cplx<float> Zc = cconj(s[out_pos(kn, f, rt)]);
+        const Cplx<float> E = {0.5f * (Zk.x + Zc.x), 0.5f * (Zk.y + Zc.y)};
+        const Cplx<float> dlt = csub(Zk, Zc);
+        const Cplx<float> O = {0.5f * dlt.y, -0.5f * dlt.x};  // (Z_k - conj Z_{n-k}) / (2i)
+        const Cplx<float> G = cadd(E, cmul(Uk[u], O));
+        oa[k] = Cplx<float>{G.x * dk[u], G.y * dk[u]};
+      }
+    }
+  }
+}
+
 template <int NTH>
 __global__ void __launch_bounds__(NTH, 512 / NTH)
     k_fft_asset(const float* __restrict__ grid, AssetFft f, const Cplx<float>* __restrict__ W,
@@ -402,83 +447,18 @@ __global__ void __launch_bounds__(NTH, 512 / NTH)
   }
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
   __syncthreads();
-  run_passes(f, s, anc, NTH);
-
-  // unpack the real-input transform and deconvolve (Eq. (14)):
-  // G(k) = (Z_k + conj Z_{n-k}) / 2 + w_{2n}^k (Z_k - conj Z_{n-k}) / (2i)
-  //      = alpha_k Z_k + beta_k conj Z_{n-k},
-  // alpha_k = (1 - i w_{2n}^k) / 2, beta_k = (1 + i w_{2n}^k) / 2, for the
-  // modes k <= N (Z_0 pairs with itself). U[k] = w_{2n}^k and the
-  // deconvolution factors are read kUnpackBatch at a time per thread.
-  Cplx<float>* oa = out + (size_t)a * (f.N + 1);
-  for (int k0 = threadIdx.x; k0 <= f.N; k0 += NTH * kUnpackBatch) {
-    float dk[kUnpackBatch];
-    Cplx<float> Uk[kUnpackBatch];
-#pragma unroll
-    for (int u = 0; u < kUnpackBatch; ++u) {
-      const int k = k0 + u * NTH;
-      if (k <= f.N) {
-        dk[u] = __ldg(decon + k);
-        Uk[u] = U[k];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kUnpackBatch; ++u) {
-      const int k = k0 + u * NTH;
-      if (k <= f.N) {
-        const int kn = k == 0 ? 0 : L - k;
-        const Cplx<float> Zk = s[out_pos(k, f, rt)];
-        const Cplx<float> Zc = cconj(s[out_pos(kn, f, rt)]);
-        const Cplx<float> E = {0.5f * (Zk.x + Zc.x), 0.5f * (Zk.y + Zc.y)};
-        const Cplx<float> dlt = csub(Zk, Zc);
-        const Cplx<float> O = {0.5f * dlt.y, -0.5f * dlt.x};  // (Z_k - conj Z_{n-k}) / (2i)
-        const Cplx<float> G = cadd(E, cmul(Uk[u], O));
-        oa[k] = Cplx<float>{G.x * dk[u], G.y * dk[u]};
-      }
-    }
-  }
+  single_finish<NTH>(f, s, anc, a, rt, U, decon, out);
 }
 
-// Two CTAs per asset as a thread-block cluster (decimation in time by 2):
-// CTA c transforms x_c[m] = z[2m + c], m < L = n/2, loaded straight into
-// its shared memory by asynchronous copies; then
-//   Z_k = X_0[k mod L] + w_n^k X_1[k mod L]
-// joins the halves, each CTA reading its partner's X through distributed
-// shared memory while it unpacks and deconvolves every other mode.
+// The pair's local transform, the join of the two halves through
+// distributed shared memory and the unpacking and deconvolution of the
+// modes k = c, c + 2, ... <= N (CTA c of the cluster).
 template <int NTH>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
-    k_fft_asset_pair(const float* __restrict__ grid, AssetFft f, const Cplx<float>* __restrict__ W,
-                     const Cplx<float>* __restrict__ tw, const Cplx<float>* __restrict__ U,
-                     const float* __restrict__ decon, Cplx<float>* __restrict__ out, const int* __restrict__ gate) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Cplx<float>* s = reinterpret_cast<Cplx<float>*>(smem_raw);
-  float4* anc = reinterpret_cast<float4*>(smem_raw + anchor_offset(f.nl));
-  unsigned c;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(c));
-  const int a = blockIdx.y;
+__device__ __forceinline__ void pair_finish(const AssetFft& f, Cplx<float>* s, const float4* anc, unsigned c, int a,
+                                            const RevTab& rt, const Cplx<float>* __restrict__ W,
+                                            const Cplx<float>* __restrict__ U, const float* __restrict__ decon,
+                                            Cplx<float>* __restrict__ out) {
   const int L = f.nl;
-  unsigned mr[kMaxAssetPasses];
-#pragma unroll
-  for (int p = 0; p < kMaxAssetPasses; ++p) mr[p] = magic_of((unsigned)f.rad[p]);
-  const RevTab rt = build_rev_tables<NTH>(f, smem_raw, mr);
-  pdl_wait();  // the grid comes from the spreading kernel
-  // every CTA of the cluster reads the same gate word: both leave or neither
-  if (*gate) return;
-  pdl_trigger();
-  {
-    const float4* src = reinterpret_cast<const float4*>(tw);
-    for (int i = threadIdx.x; i < 2 * f.tw_rows; i += NTH) {
-      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(anc + i);
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src + i) : "memory");
-    }
-  }
-  const Cplx<float>* z = reinterpret_cast<const Cplx<float>*>(grid) + (size_t)a * f.n + c;
-  for (int m = threadIdx.x; m < L; m += NTH) {
-    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s + (f.dif ? m : digit_rev(m, f, mr)));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(z + 2 * (size_t)m) : "memory");
-  }
-  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-  __syncthreads();
   run_passes(f, s, anc, NTH);
   cluster_sync_all();  // both halves transformed and visible to the partner
   const uint32_t peer = peer_addr(s, c ^ 1u);
@@ -522,6 +502,227 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
   cluster_sync_all();  // the partner has finished reading this CTA's shared memory
 }
 
+// Two CTAs per asset as a thread-block cluster (decimation in time by 2):
+// CTA c transforms x_c[m] = z[2m + c], m < L = n/2, loaded straight into
+// its shared memory by asynchronous copies; then
+//   Z_k = X_0[k mod L] + w_n^k X_1[k mod L]
+// joins the halves, each CTA reading its partner's X through distributed
+// shared memory while it unpacks and deconvolves every other mode.
+template <int NTH>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
+    k_fft_asset_pair(const float* __restrict__ grid, AssetFft f, const Cplx<float>* __restrict__ W,
+                     const Cplx<float>* __restrict__ tw, const Cplx<float>* __restrict__ U,
+                     const float* __restrict__ decon, Cplx<float>* __restrict__ out, const int* __restrict__ gate) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cplx<float>* s = reinterpret_cast<Cplx<float>*>(smem_raw);
+  float4* anc = reinterpret_cast<float4*>(smem_raw + anchor_offset(f.nl));
+  unsigned c;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(c));
+  const int a = blockIdx.y;
+  const int L = f.nl;
+  unsigned mr[kMaxAssetPasses];
+#pragma unroll
+  for (int p = 0; p < kMaxAssetPasses; ++p) mr[p] = magic_of((unsigned)f.rad[p]);
+  const RevTab rt = build_rev_tables<NTH>(f, smem_raw, mr);
+  pdl_wait();  // the grid comes from the spreading kernel
+  // every CTA of the cluster reads the same gate word: both leave or neither
+  if (*gate) return;
+  pdl_trigger();
+  {
+    const float4* src = reinterpret_cast<const float4*>(tw);
+    for (int i = threadIdx.x; i < 2 * f.tw_rows; i += NTH) {
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(anc + i);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src + i) : "memory");
+    }
+  }
+  const Cplx<float>* z = reinterpret_cast<const Cplx<float>*>(grid) + (size_t)a * f.n + c;
+  for (int m = threadIdx.x; m < L; m += NTH) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s + (f.dif ? m : digit_rev(m, f, mr)));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(z + 2 * (size_t)m) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  pair_finish<NTH>(f, s, anc, c, a, rt, W, U, decon, out);
+}
+
+// Stages (a2)-(c) in one launch with the grid row resident in shared
+// memory: each CTA spreads its asset's records (Eq. (12)) straight into the
+// complex points of the row it transforms, so only the records come in and
+// only the coefficients go out. One CTA per asset holds the whole row; for
+// rows too large for one CTA, CTA c of a cluster pair holds the points
+// z[2m + c] (cells 4m + 2c, 4m + 2c + 1) and adds only the taps that land in
+// its own cells. The row's cells are taken in sub-ranges [A, A + sub): the
+// records whose stencils reach a sub-range (found for all sub-ranges at once
+// before the first) are scaled and accumulated exactly as for a spreading
+// tile (the same per-tap polynomials, the same hi/lo int32 accumulation),
+// then the sub-range's points become float32 in the row at their positions
+// for the transform. The staging area and integer tiles live where the
+// twiddle anchors (and digit-reversal tables) go afterwards.
+constexpr int kResChunk = 1024;   // records staged per pass
+constexpr int kResMaxSub = 64;    // sub-ranges per row
+
+template <int NT, int NTH, class Cells>
+__device__ __forceinline__ void spread_resident(const int64_t* __restrict__ off, const int* __restrict__ rb0,
+                                                const float* __restrict__ rd, const float* __restrict__ rv,
+                                                const SpreadParams& sp, const KernelPoly& poly, int sub,
+                                                const AssetFft& f, const unsigned* mr, int a, Cells cells,
+                                                Cplx<float>* s, unsigned char* work) {
+  constexpr int EC = kResChunk;
+  constexpr int kPer = Cells::kAll ? 2 : 4;  // cells per complex point of this CTA
+  int* ev_p = reinterpret_cast<int*>(work);
+  float* ev_d = reinterpret_cast<float*>(ev_p + EC);
+  float* ev_v = ev_d + EC;
+  const int nslot = sub / (kPer / 2);  // integer cells per tile held by this CTA
+  int* tile_hi = reinterpret_cast<int*>(ev_v + EC);
+  int* tile_lo = tile_hi + nslot;
+  const uint32_t hi_s = (uint32_t)__cvta_generic_to_shared(tile_hi);
+  const uint32_t lo_s = (uint32_t)__cvta_generic_to_shared(tile_lo);
+  __shared__ float s_sum[NTH / 32], s_max[NTH / 32];
+  __shared__ int64_t s_rng[kResMaxSub][6];
+  const int nsub = (int)((sp.Mr + sub - 1) / sub);
+  // record ranges of every sub-range: for image m = w/2 - 1 the returns with
+  // b0 in [A - khi + m M_r, A + Tlen - klo + m M_r), clipped to [0, M_r + 1)
+  // (a search per bound and one warp per search; empty images skipped)
+  {
+    const int64_t e0 = off[a], eend = off[a + 1];
+    const int64_t e1 = eend > e0 ? eend - 1 : e0;  // returns live at h in [e0, e1)
+    for (int job = threadIdx.x >> 5; job < 6 * nsub; job += NTH / 32) {
+      const int r = job / 6, w = job - 6 * (job / 6);
+      const int64_t A = (int64_t)r * sub;
+      const int Tlen = (int)min((int64_t)sub, sp.Mr - A);
+      const int m = w / 2 - 1;
+      long long lo = A - sp.khi + (long long)m * sp.Mr;
+      long long hi = A + Tlen - sp.klo + (long long)m * sp.Mr;
+      if (lo < 0) lo = 0;
+      if (hi > sp.Mr + 1) hi = sp.Mr + 1;
+      const int64_t res = lo < hi ? warp_first_ge(rb0, e0, e1, (w & 1) ? hi : lo) : -1;
+      if ((threadIdx.x & 31) == 0) s_rng[r][w] = res;
+    }
+  }
+  __syncthreads();
+  for (int r = 0; r < nsub; ++r) {
+    const int64_t A = (int64_t)r * sub;
+    const int Tlen = (int)min((int64_t)sub, sp.Mr - A);  // even (a multiple of 4 for the pair)
+    {
+      int4* t4 = reinterpret_cast<int4*>(tile_hi);
+      for (int i = threadIdx.x; i < nslot / 2; i += NTH) t4[i] = make_int4(0, 0, 0, 0);  // both tiles
+    }
+    TileRanges tr;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const bool empty = s_rng[r][2 * q] < 0;
+      tr.lo[q] = empty ? 0 : s_rng[r][2 * q];
+      tr.hi[q] = empty ? 0 : s_rng[r][2 * q + 1];
+    }
+    tr.n2 = tr.hi[2] - tr.lo[2];
+    tr.n1 = tr.hi[1] - tr.lo[1];
+    tr.n0 = tr.hi[0] - tr.lo[0];
+    const int64_t ntot = tr.n2 + tr.n1 + tr.n0;
+    float part = 0.f, pmax = 0.f;
+    const int n_first = (int)min((int64_t)EC, ntot);
+    for (int i = threadIdx.x; i < n_first; i += NTH) {
+      load_record<float>(rb0, rd, rv, sp, tr, A, i, ev_p[i], ev_d[i], ev_v[i]);
+      part += fabsf(ev_v[i]);
+      pmax = fmaxf(pmax, fabsf(ev_v[i]));
+    }
+    for (int64_t i = EC + threadIdx.x; i < ntot; i += NTH) {
+      int pp;
+      float dd, vv;
+      load_record<float>(rb0, rd, rv, sp, tr, A, i, pp, dd, vv);
+      part += fabsf(vv);
+      pmax = fmaxf(pmax, fabsf(vv));
+    }
+    const TileScales ts = tile_scales<NTH>(part, pmax, ntot, s_sum, s_max);
+    for (int64_t cs = 0; cs < ntot; cs += EC) {
+      const int n = (int)min((int64_t)EC, ntot - cs);
+      if (cs > 0) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += NTH)
+          load_record<float>(rb0, rd, rv, sp, tr, A, cs + i, ev_p[i], ev_d[i], ev_v[i]);
+      }
+      __syncthreads();
+      spread_chunk<NT, NTH>(ev_p, ev_d, ev_v, n, Tlen, sp.klo, poly, ts, hi_s, lo_s, cells);
+    }
+    __syncthreads();
+    // this CTA's points of the sub-range, m = A / kPer + i (two integer cells each)
+    const int m0 = (int)(A / kPer);
+    const int2* h2 = reinterpret_cast<const int2*>(tile_hi);
+    const int2* l2 = reinterpret_cast<const int2*>(tile_lo);
+    for (int i = threadIdx.x; i < Tlen / kPer; i += NTH) {
+      const int2 hv = h2[i], lv = l2[i];
+      const int m = m0 + i;
+      s[f.dif ? m : digit_rev(m, f, mr)] = Cplx<float>{fmaf((float)lv.x, ts.inv_l, (float)hv.x * ts.inv_h),
+                                                       fmaf((float)lv.y, ts.inv_l, (float)hv.y * ts.inv_h)};
+    }
+    __syncthreads();  // the tiles are cleared for the next sub-range
+  }
+}
+
+// Anchor rows (16-byte asynchronous copies) into their place after the row.
+template <int NTH>
+__device__ __forceinline__ void load_anchors(const AssetFft& f, const Cplx<float>* __restrict__ tw, float4* anc) {
+  const float4* src = reinterpret_cast<const float4*>(tw);
+  for (int i = threadIdx.x; i < 2 * f.tw_rows; i += NTH) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(anc + i);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src + i) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+template <int NT>
+__global__ void __launch_bounds__(512, 1)
+    k_spread_fft(const int64_t* __restrict__ off, const int* __restrict__ rb0, const float* __restrict__ rd,
+                 const float* __restrict__ rv, SpreadParams sp, KernelPoly poly, int sub, AssetFft f,
+                 const Cplx<float>* __restrict__ tw, const Cplx<float>* __restrict__ U,
+                 const float* __restrict__ decon, Cplx<float>* __restrict__ out, const int* __restrict__ gate) {
+  constexpr int NTH = 512;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cplx<float>* s = reinterpret_cast<Cplx<float>*>(smem_raw);
+  float4* anc = reinterpret_cast<float4*>(smem_raw + anchor_offset(f.nl));
+  const int a = blockIdx.y;
+  unsigned mr[kMaxAssetPasses];
+#pragma unroll
+  for (int p = 0; p < kMaxAssetPasses; ++p) mr[p] = magic_of((unsigned)f.rad[p]);
+  pdl_wait();         // the records come from the prep kernel
+  if (*gate) return;  // uniform: the whole block leaves
+  pdl_trigger();
+  spread_resident<NT, NTH>(off, rb0, rd, rv, sp, poly, sub, f, mr, a, AllCells{}, s,
+                           smem_raw + anchor_offset(f.nl));
+  load_anchors<NTH>(f, tw, anc);
+  const RevTab rt = build_rev_tables<NTH>(f, smem_raw, mr);
+  __syncthreads();
+  single_finish<NTH>(f, s, anc, a, rt, U, decon, out);
+}
+
+template <int NT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
+    k_spread_fft_pair(const int64_t* __restrict__ off, const int* __restrict__ rb0, const float* __restrict__ rd,
+                      const float* __restrict__ rv, SpreadParams sp, KernelPoly poly, int sub, AssetFft f,
+                      const Cplx<float>* __restrict__ W, const Cplx<float>* __restrict__ tw,
+                      const Cplx<float>* __restrict__ U, const float* __restrict__ decon,
+                      Cplx<float>* __restrict__ out, const int* __restrict__ gate) {
+  constexpr int NTH = kPairThreads;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cplx<float>* s = reinterpret_cast<Cplx<float>*>(smem_raw);
+  float4* anc = reinterpret_cast<float4*>(smem_raw + anchor_offset(f.nl));
+  unsigned c;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(c));
+  const int a = blockIdx.y;
+  unsigned mr[kMaxAssetPasses];
+#pragma unroll
+  for (int p = 0; p < kMaxAssetPasses; ++p) mr[p] = magic_of((unsigned)f.rad[p]);
+  pdl_wait();  // the records come from the prep kernel
+  // every CTA of the cluster reads the same gate word: both leave or neither
+  if (*gate) return;
+  pdl_trigger();
+  spread_resident<NT, NTH>(off, rb0, rd, rv, sp, poly, sub, f, mr, a, PairCells{c}, s,
+                           smem_raw + anchor_offset(f.nl));
+  load_anchors<NTH>(f, tw, anc);
+  const RevTab rt = build_rev_tables<NTH>(f, smem_raw, mr);  // none: decimation in time
+  __syncthreads();
+  pair_finish<NTH>(f, s, anc, c, a, rt, W, U, decon, out);
+}
+
 // Twiddle anchors of each pass: row j < m_p holds w^1..w^4 of w = w_{L_p}^j,
 // from float64 angles.
 __global__ void k_asset_twiddles(AssetFft f, Cplx<float>* tw) {
@@ -561,6 +762,61 @@ cudaError_t launch_asset_twiddles(const AssetFft& f, void* tw, cudaStream_t s) {
   for (int p = 0; p < f.npass; ++p) cnt = std::max(cnt, 4 * f.stride[p]);
   k_asset_twiddles<<<(cnt + 255) / 256, 256, 0, s>>>(f, (Cplx<float>*)tw);
   return cudaGetLastError();
+}
+
+// Cells per sub-range of the resident spread + FFT kernels (a multiple of
+// 8) for a shared-memory limit on the dynamic allocation; 0 when the row
+// leaves no room for the staging area and a useful sub-range, or when the row
+// would take more than kResMaxSub sub-ranges.
+int spread_fft_sub(const AssetFft& f, int64_t Mr, size_t smem_limit) {
+  const size_t row = anchor_offset(f.nl) + (size_t)kResChunk * 12;
+  const size_t per_cell = f.pair ? 4 : 8;  // hi + lo of this CTA's cells
+  if (row + 1024 * per_cell > smem_limit) return 0;
+  int64_t sub = (int64_t)((smem_limit - row) / per_cell) / 8 * 8;
+  sub = std::min<int64_t>(sub, (Mr + 7) / 8 * 8);
+  if ((Mr + sub - 1) / sub > kResMaxSub) return 0;
+  if (asset_fft_smem(f) > smem_limit) return 0;
+  return (int)sub;
+}
+
+size_t spread_fft_smem(const AssetFft& f, int sub) {
+  const size_t work = anchor_offset(f.nl) + (size_t)kResChunk * 12 + (size_t)sub * (f.pair ? 4 : 8);
+  return std::max(work, asset_fft_smem(f));
+}
+
+cudaError_t launch_spread_fft(const int64_t* off, const int* rb0, const void* rd, const void* rv,
+                              const SpreadParams& sp, const KernelPoly& poly, int sub, const AssetFft& f, int D,
+                              const void* W, const void* tw, const void* U, const void* decon, void* coeffs,
+                              const int* status, cudaStream_t s) {
+  if (sub < 8 || sub % 8 || (f.pair && f.dif) || f.split != (f.pair ? 2 : 1)) return cudaErrorInvalidValue;
+  const size_t smem = spread_fft_smem(f, sub);
+  const int nt = sp.khi - sp.klo + 1;
+  auto go = [&](auto single, auto pair) -> cudaError_t {
+    cudaError_t e;
+    if (f.pair) {
+      if ((e = cudaFuncSetAttribute(pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
+      return launch_pdl(pair, dim3(2, D), dim3(kPairThreads), smem, s, off, rb0, (const float*)rd, (const float*)rv,
+                        sp, poly, sub, f, (const Cplx<float>*)W, (const Cplx<float>*)tw, (const Cplx<float>*)U,
+                        (const float*)decon, (Cplx<float>*)coeffs, status + 1);
+    }
+    if ((e = cudaFuncSetAttribute(single, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
+    return launch_pdl(single, dim3(1, D), dim3(512), smem, s, off, rb0, (const float*)rd, (const float*)rv, sp, poly,
+                      sub, f, (const Cplx<float>*)tw, (const Cplx<float>*)U, (const float*)decon,
+                      (Cplx<float>*)coeffs, status + 1);
+  };
+  switch (nt) {
+    case 9: return go(k_spread_fft<9>, k_spread_fft_pair<9>);
+    case 13: return go(k_spread_fft<13>, k_spread_fft_pair<13>);
+    case 14: return go(k_spread_fft<14>, k_spread_fft_pair<14>);
+    default: break;
+  }
+  if (nt <= 8) return go(k_spread_fft<8>, k_spread_fft_pair<8>);
+  if (nt <= 16) return go(k_spread_fft<16>, k_spread_fft_pair<16>);
+  if (nt <= 24) return go(k_spread_fft<24>, k_spread_fft_pair<24>);
+  if (nt <= 32) return go(k_spread_fft<32>, k_spread_fft_pair<32>);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fft_asset(const float* grid, const AssetFft& f, int D, const void* W, const void* tw,

@@ -237,7 +237,6 @@ cudaError_t launch_min_gap(const int64_t* off, const double* t, int D, const Res
 }
 
 constexpr int kSpreadThreads = 256;
-constexpr int kNoCell = -0x40000000;  // cell of a skipped event (outside every window)
 
 // ------------------------------------------------------------------ prep
 // Steps a0 / a1 of the hot path: for each event h, the rescaled cell
@@ -458,86 +457,6 @@ cudaError_t launch_prep_f64(const int64_t* off, const double* t, const double* l
 // ------------------------------------------------------------------ spread
 template <typename T> struct EvChunk { static constexpr int n = 1536; };  // 6 spreading blocks per SM
 
-// Event ranges of a tile [L, L + Tlen): image m = r - 1 (r = 0, 1, 2) holds
-// the returns with b0 in [L - khi + m M_r, L + Tlen - klo + m M_r); taken in
-// the order r = 2, 1, 0 their tile-relative positions p = b0 - L - m M_r are
-// sorted. An event may sit in two images (a small grid seen through both of
-// its periodic copies); each image feeds different cells.
-struct TileRanges {
-  int64_t lo[3], hi[3];
-  int64_t n2, n1, n0;
-};
-
-// First index h in [e0, e1) with key[h] >= x (e1 if none), by one warp: each
-// step the 32 lanes sample the bracket at 32 evenly spaced points and a
-// ballot keeps the segment where the predicate turns true (32-ary search).
-__device__ __forceinline__ int64_t warp_first_ge(const int* __restrict__ key, int64_t e0, int64_t e1, long long x) {
-  const int lane = threadIdx.x & 31;
-  int64_t lo = e0, hi = e1;  // answer in [lo, hi]
-  for (int it = 0; it < 16 && hi > lo; ++it) {
-    const int64_t len = hi - lo;
-    const int64_t stride = (len + 31) / 32;
-    const int64_t o = (int64_t)lane * stride;
-    const bool below = o < len && (long long)key[lo + o] < x;
-    const unsigned bal = __ballot_sync(0xffffffffu, below);
-    const int c = __popc(bal);  // samples below x (a prefix when key is sorted)
-    if (c == 0) {
-      hi = lo;
-    } else {
-      const int64_t nlo = lo + (int64_t)(c - 1) * stride + 1;
-      const int64_t nhi = min(lo + (int64_t)c * stride, hi);
-      lo = min(nlo, nhi);
-      hi = nhi;
-    }
-  }
-  return lo;
-}
-
-__device__ __forceinline__ void tile_ranges(const int64_t* __restrict__ off, const int* __restrict__ rb0,
-                                            const SpreadParams& p, int a, int64_t L, int Tlen, TileRanges& tr) {
-  __shared__ int64_t s_res[6];
-  const int64_t e0 = off[a], eend = off[a + 1];
-  const int64_t e1 = eend > e0 ? eend - 1 : e0;  // returns live at h in [e0, e1)
-  const int w = threadIdx.x >> 5;
-  if (w < 6) {
-    // warp w: threshold w of image m = w/2 - 1 (lower bound for even w)
-    const int m = w / 2 - 1;
-    long long A = L - p.khi + (long long)m * p.Mr;
-    long long B = L + Tlen - p.klo + (long long)m * p.Mr;
-    if (A < 0) A = 0;
-    if (B > p.Mr + 1) B = p.Mr + 1;
-    int64_t r = 0;
-    if (A < B) r = warp_first_ge(rb0, e0, e1, (w & 1) ? B : A);
-    else r = -1;  // empty image
-    if ((threadIdx.x & 31) == 0) s_res[w] = r;
-  }
-  __syncthreads();
-  for (int r = 0; r < 3; ++r) {
-    const bool empty = s_res[2 * r] < 0;
-    tr.lo[r] = empty ? 0 : s_res[2 * r];
-    tr.hi[r] = empty ? 0 : s_res[2 * r + 1];
-  }
-  tr.n2 = tr.hi[2] - tr.lo[2];
-  tr.n1 = tr.hi[1] - tr.lo[1];
-  tr.n0 = tr.hi[0] - tr.lo[0];
-}
-
-// Record qi of the concatenation (r = 2, 1, 0) with its tile-relative position.
-template <typename T>
-__device__ __forceinline__ void load_record(const int* __restrict__ rb0, const T* __restrict__ rd,
-                                            const T* __restrict__ rv, const SpreadParams& p, const TileRanges& tr,
-                                            int64_t L, int64_t qi, int& pos, T& d, T& v) {
-  int64_t h;
-  long long shift;  // p = b0 - L - m M_r
-  if (qi < tr.n2) { h = tr.lo[2] + qi; shift = -(long long)p.Mr; }
-  else if (qi < tr.n2 + tr.n1) { h = tr.lo[1] + (qi - tr.n2); shift = 0; }
-  else { h = tr.lo[0] + (qi - tr.n2 - tr.n1); shift = p.Mr; }
-  const int b0 = rb0[h];
-  pos = b0 == kNoCell ? kNoCell : (int)(b0 - L + shift);
-  d = rd[h];
-  v = rv[h];
-}
-
 // Gather spreading (Eq. (12)): thread t owns cells c = t CPT .. t CPT + CPT-1
 // of the tile and sums, in registers, delta_e phi(c - p_e - d_e) over the
 // events with c - p_e in [klo, khi], a sliding window over the sorted
@@ -656,11 +575,6 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_scatter(const int64_t
   }
 }
 
-// Shared-memory integer reduction without a returned value.
-__device__ __forceinline__ void red_shared_add(uint32_t addr, int v) {
-  asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-
 // Float32 scatter with polynomial taps and exact integer accumulation.
 // Shared-memory float atomics run as compare-and-swap loops and 64-bit
 // integer reductions are slower still (3.4x and 5.6x the time of an int32
@@ -682,10 +596,7 @@ __device__ __forceinline__ void red_shared_add(uint32_t addr, int v) {
 // it) this is negligible up to about 2^20 events per tile.
 //
 // round(y) for |y| < 2^22 is taken as y + 1.5 2^23, whose float spacing is 1
-// (one FMA, no conversion instruction); the integer is the result's bits
-// minus those of 1.5 2^23.
-constexpr float kRoundMagic = 12582912.0f;  // 1.5 * 2^23
-constexpr int kRoundMagicBits = 0x4B400000;
+// (one FMA, no conversion instruction; kRoundMagic).
 
 // Records staged per pass of the polynomial scatter: with two 4096-cell
 // tiles, 44 KB of shared memory per block and five blocks per SM. On the
@@ -724,7 +635,6 @@ __global__ void __launch_bounds__(kSpreadThreads, 5) k_spread_poly(const int64_t
   TileRanges tr;
   tile_ranges(off, rb0, p, a, L, Tlen, tr);
   const int64_t ntot = tr.n2 + tr.n1 + tr.n0;
-  const int klo = p.klo;
   // the tile's scales: sum and maximum of |v| over its records (staged with
   // the first chunk when one chunk holds them all, else a pass over the returns)
   float part = 0.f, pmax = 0.f;
@@ -741,33 +651,8 @@ __global__ void __launch_bounds__(kSpreadThreads, 5) k_spread_poly(const int64_t
     part += fabsf(vv);
     pmax = fmaxf(pmax, fabsf(vv));
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    part += __shfl_xor_sync(0xffffffffu, part, o);
-    pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    s_sum[threadIdx.x >> 5] = part;
-    s_max[threadIdx.x >> 5] = pmax;
-  }
-  __syncthreads();
-  float B = 0.f, V = 0.f;
-#pragma unroll
-  for (int w = 0; w < kSpreadThreads / 32; ++w) {
-    B += s_sum[w];
-    V = fmaxf(V, s_max[w]);
-  }
-  int eh = 0, k = 0;
-  if (B > 0.f && B < 3.0e38f) {
-    int exB, exV;
-    frexpf(B, &exB);  // B < 2^exB
-    frexpf(V, &exV);  // V < 2^exV
-    eh = min(29 - exB, 21 - exV);
-    const int bitlen = 64 - __clzll((long long)ntot);
-    k = max(0, min(20, 30 - bitlen));
-  }
-  const float scale = ldexpf(1.0f, eh), kscale = ldexpf(1.0f, k);
-  const float inv_h = ldexpf(1.0f, -eh), inv_l = ldexpf(1.0f, -(eh + k));
+  const TileScales ts = tile_scales<kSpreadThreads>(part, pmax, ntot, s_sum, s_max);
+  const float inv_h = ts.inv_h, inv_l = ts.inv_l;
   for (int64_t cs = 0; cs < ntot; cs += EC) {
     const int n = (int)min((int64_t)EC, ntot - cs);
     if (cs > 0) {
@@ -776,88 +661,7 @@ __global__ void __launch_bounds__(kSpreadThreads, 5) k_spread_poly(const int64_t
         load_record<float>(rb0, rd, rv, p, tr, L, cs + i, ev_p[i], ev_d[i], ev_v[i]);
     }
     __syncthreads();
-    if (2 * n < Tlen) {
-      // sparse: one record per lane, its taps added at once (neighbouring
-      // lanes' records rarely share a cell)
-      for (int ei = threadIdx.x; ei < n; ei += kSpreadThreads) {
-        const int pe = ev_p[ei];
-        if (pe == kNoCell) continue;
-        const float z = ev_d[ei] - 0.5f;
-        const float vs = ev_v[ei] * scale;
-        const int c0 = pe + klo;
-        const bool inside = c0 >= 0 && c0 + NT <= Tlen;  // else test each tap's cell
-#pragma unroll
-        for (int j = 0; j < NT; ++j) {
-          float w = poly.c[j][kPolyDeg];
-#pragma unroll
-          for (int i = kPolyDeg - 1; i >= 0; --i) w = fmaf(w, z, poly.c[j][i]);
-          const float h = fmaf(vs, w, kRoundMagic);      // round(vs w) + 1.5 2^23
-          const float r = fmaf(vs, w, kRoundMagic - h);  // vs w - round(vs w), |r| <= 1/2
-          const float l = fmaf(r, kscale, kRoundMagic);
-          const unsigned c = (unsigned)(c0 + j);
-          if (inside || c < (unsigned)Tlen) {
-            red_shared_add(hi_s + 4u * c, __float_as_int(h) - kRoundMagicBits);
-            red_shared_add(lo_s + 4u * c, __float_as_int(l) - kRoundMagicBits);
-          }
-        }
-      }
-      continue;
-    }
-    // dense (at least one record per two cells): each thread takes a
-    // contiguous stretch of the staged (cell-sorted) records and, for each
-    // run of records in one cell, sums their taps in registers (exact integer
-    // sums, within the same per-cell bounds) before adding them to the tiles;
-    // one record per lane would have the lanes of a warp reduce into the same
-    // few cells at once. A run is swept twice, for the first and the second
-    // half of the taps, so that only half the sums are live. An odd stretch
-    // keeps the lanes' staged reads on distinct banks.
-    constexpr int H = (NT + 1) / 2;
-    int cnt = (n + kSpreadThreads - 1) / kSpreadThreads;
-    cnt |= 1;
-    const int e0 = min(n, (int)threadIdx.x * cnt), e1 = min(n, e0 + cnt);
-    for (int ei = e0; ei < e1;) {
-      const int pe = ev_p[ei];
-      int ej = ei + 1;
-      while (ej < e1 && ev_p[ej] == pe) ++ej;
-      if (pe != kNoCell) {
-        const int c0 = pe + klo;
-        const bool inside = c0 >= 0 && c0 + NT <= Tlen;  // else test each tap's cell
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          int ah[H], al[H];
-#pragma unroll
-          for (int q = 0; q < H; ++q) ah[q] = al[q] = 0;
-          for (int e = ei; e < ej; ++e) {
-            const float z = ev_d[e] - 0.5f;
-            const float vs = ev_v[e] * scale;
-#pragma unroll
-            for (int q = 0; q < H; ++q) {
-              const int j = half * H + q;
-              if (j < NT) {
-                float w = poly.c[j][kPolyDeg];
-#pragma unroll
-                for (int i = kPolyDeg - 1; i >= 0; --i) w = fmaf(w, z, poly.c[j][i]);
-                const float h = fmaf(vs, w, kRoundMagic);      // round(vs w) + 1.5 2^23
-                const float r = fmaf(vs, w, kRoundMagic - h);  // vs w - round(vs w), |r| <= 1/2
-                const float l = fmaf(r, kscale, kRoundMagic);
-                ah[q] += __float_as_int(h) - kRoundMagicBits;
-                al[q] += __float_as_int(l) - kRoundMagicBits;
-              }
-            }
-          }
-#pragma unroll
-          for (int q = 0; q < H; ++q) {
-            const int j = half * H + q;
-            const unsigned c = (unsigned)(c0 + j);
-            if (j < NT && (inside || c < (unsigned)Tlen)) {
-              red_shared_add(hi_s + 4u * c, ah[q]);
-              red_shared_add(lo_s + 4u * c, al[q]);
-            }
-          }
-        }
-      }
-      ei = ej;
-    }
+    spread_chunk<NT, kSpreadThreads>(ev_p, ev_d, ev_v, n, Tlen, p.klo, poly, ts, hi_s, lo_s, AllCells{});
   }
   __syncthreads();
   if (p.perm_np > 0) {

@@ -85,7 +85,7 @@ def test_binding_refuses_missing_library(monkeypatch, tmp_path):
 
 @pytest.mark.parametrize("field,value,code", [
     ("reps", 0, 1), ("D", 0, 1), ("N_max", 0, 1), ("max_events", -1, 1), ("reserved0", 1, 1),
-    ("D", 13, 11), ("prec", 7, 1),
+    ("D", 13, 11), ("prec", 7, 1), ("spread_algo", 4, 1), ("spread_algo", -1, 1),
 ])
 def test_bad_batch_desc_rejected_on_host(lib, field, value, code):
     from paper_2003_02842_gb300 import _lib
