@@ -38,7 +38,7 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 NCU_TRAFFIC = {
     # the block workload in its default configuration
     # (profiles/c3_block_D100_N10000_kernels_ncu.md)
-    ("fft", "c3", "bf16x3", "es"): 16442880,
+    ("fft", "c3", "bf16x3", "es"): 16438016,
     ("spread", "c3", "bf16x3", "es"): 9236224,
     ("prep", "c3", "bf16x3", "es"): 12287488,
     ("gram", "c3", "bf16x3", "es"): 8115712,

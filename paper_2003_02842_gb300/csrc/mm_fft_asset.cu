@@ -201,8 +201,20 @@ __device__ __forceinline__ void fft_pass(Cplx<float>* __restrict__ s, int L, int
   }
 }
 
-template <bool DIF>
+template <bool DIF, bool BIG>
 __device__ __forceinline__ void run_pass_t(int R, Cplx<float>* s, int L, int m, const float4* anc, int nth) {
+  if constexpr (BIG) {
+    switch (R) {
+      case 18: fft_pass<18, DIF>(s, L, m, anc, nth); return;
+      case 20: fft_pass<20, DIF>(s, L, m, anc, nth); return;
+      case 24: fft_pass<24, DIF>(s, L, m, anc, nth); return;
+      case 25: fft_pass<25, DIF>(s, L, m, anc, nth); return;
+      case 27: fft_pass<27, DIF>(s, L, m, anc, nth); return;
+      case 30: fft_pass<30, DIF>(s, L, m, anc, nth); return;
+      case 32: fft_pass<32, DIF>(s, L, m, anc, nth); return;
+      default: break;
+    }
+  }
   switch (R) {
     case 2: fft_pass<2, DIF>(s, L, m, anc, nth); break;
     case 3: fft_pass<3, DIF>(s, L, m, anc, nth); break;
@@ -215,13 +227,6 @@ __device__ __forceinline__ void run_pass_t(int R, Cplx<float>* s, int L, int m, 
     case 12: fft_pass<12, DIF>(s, L, m, anc, nth); break;
     case 15: fft_pass<15, DIF>(s, L, m, anc, nth); break;
     case 16: fft_pass<16, DIF>(s, L, m, anc, nth); break;
-    case 18: fft_pass<18, DIF>(s, L, m, anc, nth); break;
-    case 20: fft_pass<20, DIF>(s, L, m, anc, nth); break;
-    case 24: fft_pass<24, DIF>(s, L, m, anc, nth); break;
-    case 25: fft_pass<25, DIF>(s, L, m, anc, nth); break;
-    case 27: fft_pass<27, DIF>(s, L, m, anc, nth); break;
-    case 30: fft_pass<30, DIF>(s, L, m, anc, nth); break;
-    case 32: fft_pass<32, DIF>(s, L, m, anc, nth); break;
     default: break;  // the host plans only the radices above
   }
 }
@@ -234,13 +239,14 @@ __device__ __forceinline__ int pick(const int (&a)[kMaxAssetPasses], int p) {
 }
 
 // All passes of the local transform in the plan's order for its direction.
+template <bool BIG>
 __device__ __forceinline__ void run_passes(const AssetFft& f, Cplx<float>* s, const float4* anc, int nth) {
   for (int i = 0; i < f.npass; ++i) {
     const int p = f.dif ? i : f.npass - 1 - i;
     const int R = pick(f.rad, p), m = pick(f.stride, p);
     const float4* a = anc + 2 * pick(f.tw_off, p);
-    if (f.dif) run_pass_t<true>(R, s, f.nl, m, a, nth);
-    else run_pass_t<false>(R, s, f.nl, m, a, nth);
+    if (f.dif) run_pass_t<true, BIG>(R, s, f.nl, m, a, nth);
+    else run_pass_t<false, BIG>(R, s, f.nl, m, a, nth);
     __syncthreads();
   }
 }
@@ -329,31 +335,33 @@ __device__ __forceinline__ void cluster_sync_all() {
 }
 
 constexpr uint32_t kBulkChunk = 32768;  // bytes per bulk copy instruction
-constexpr int kUnpackBatch = 8;   // table reads in flight per thread in the unpacking step
-constexpr int kPairBatch = 4;     // the same for the cluster variant (more values per mode)
+// table reads in flight per thread in the unpacking step (fewer with more threads)
+template <int NTH> constexpr int kUnpackBatch = NTH >= 1024 ? 4 : 8;
+template <int NTH> constexpr int kPairBatch = NTH >= 1024 ? 2 : 4;  // the cluster variant (more values per mode)
 constexpr int kPairThreads = 512; // one CTA of a pair per SM (each holds half an asset's grid)
 
 // The local transform of a row held whole by one CTA, then the unpacking
 // of the real-input transform and the deconvolution of the modes k <= N.
-template <int NTH>
+template <int NTH, bool BIG>
 __device__ __forceinline__ void single_finish(const AssetFft& f, Cplx<float>* s, const float4* anc, int a,
                                               const RevTab& rt, const Cplx<float>* __restrict__ U,
                                               const float* __restrict__ decon, Cplx<float>* __restrict__ out) {
+  constexpr int kUB = kUnpackBatch<NTH>;
   const int L = f.nl;
-  run_passes(f, s, anc, NTH);
+  run_passes<BIG>(f, s, anc, NTH);
 
   // unpack the real-input transform and deconvolve (Eq. (14)):
   // G(k) = (Z_k + conj Z_{n-k}) / 2 + w_{2n}^k (Z_k - conj Z_{n-k}) / (2i)
   //      = alpha_k Z_k + beta_k conj Z_{n-k},
   // alpha_k = (1 - i w_{2n}^k) / 2, beta_k = (1 + i w_{2n}^k) / 2, for the
   // modes k <= N (Z_0 pairs with itself). U[k] = w_{2n}^k and the
-  // deconvolution factors are read kUnpackBatch at a time per thread.
+  // deconvolution factors are read kUB at a time per thread.
   Cplx<float>* oa = out + (size_t)a * (f.N + 1);
-  for (int k0 = threadIdx.x; k0 <= f.N; k0 += NTH * kUnpackBatch) {
-    float dk[kUnpackBatch];
-    Cplx<float> Uk[kUnpackBatch];
+  for (int k0 = threadIdx.x; k0 <= f.N; k0 += NTH * kUB) {
+    float dk[kUB];
+    Cplx<float> Uk[kUB];
 #pragma unroll
-    for (int u = 0; u < kUnpackBatch; ++u) {
+    for (int u = 0; u < kUB; ++u) {
       const int k = k0 + u * NTH;
       if (k <= f.N) {
         dk[u] = __ldg(decon + k);
@@ -361,7 +369,7 @@ __device__ __forceinline__ void single_finish(const AssetFft& f, Cplx<float>* s,
       }
     }
 #pragma unroll
-    for (int u = 0; u < kUnpackBatch; ++u) {
+    for (int u = 0; u < kUB; ++u) {
       const int k = k0 + u * NTH;
       if (k <= f.N) {
         const int kn = k == 0 ? 0 : L - k;
@@ -377,8 +385,8 @@ __device__ __forceinline__ void single_finish(const AssetFft& f, Cplx<float>* s,
   }
 }
 
-template <int NTH>
-__global__ void __launch_bounds__(NTH, 512 / NTH)
+template <int NTH, bool BIG>
+__global__ void __launch_bounds__(NTH, 1)
     k_fft_asset(const float* __restrict__ grid, AssetFft f, const Cplx<float>* __restrict__ W,
                 const Cplx<float>* __restrict__ tw, const Cplx<float>* __restrict__ U,
                 const float* __restrict__ decon, Cplx<float>* __restrict__ out, const int* __restrict__ gate,
@@ -447,28 +455,29 @@ __global__ void __launch_bounds__(NTH, 512 / NTH)
   }
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
   __syncthreads();
-  single_finish<NTH>(f, s, anc, a, rt, U, decon, out);
+  single_finish<NTH, BIG>(f, s, anc, a, rt, U, decon, out);
 }
 
 // The pair's local transform, the join of the two halves through
 // distributed shared memory and the unpacking and deconvolution of the
 // modes k = c, c + 2, ... <= N (CTA c of the cluster).
-template <int NTH>
+template <int NTH, bool BIG>
 __device__ __forceinline__ void pair_finish(const AssetFft& f, Cplx<float>* s, const float4* anc, unsigned c, int a,
                                             const RevTab& rt, const Cplx<float>* __restrict__ W,
                                             const Cplx<float>* __restrict__ U, const float* __restrict__ decon,
                                             Cplx<float>* __restrict__ out) {
+  constexpr int kPB = kPairBatch<NTH>;
   const int L = f.nl;
-  run_passes(f, s, anc, NTH);
+  run_passes<BIG>(f, s, anc, NTH);
   cluster_sync_all();  // both halves transformed and visible to the partner
   const uint32_t peer = peer_addr(s, c ^ 1u);
   Cplx<float>* oa = out + (size_t)a * (f.N + 1);
-  for (int k0 = (int)c + 2 * (int)threadIdx.x; k0 <= f.N; k0 += 2 * NTH * kPairBatch) {
-    float dk[kPairBatch];
-    Cplx<float> Uk[kPairBatch], Wk[kPairBatch], A0[kPairBatch], A1[kPairBatch], B0[kPairBatch],
-        B1[kPairBatch];
+  for (int k0 = (int)c + 2 * (int)threadIdx.x; k0 <= f.N; k0 += 2 * NTH * kPB) {
+    float dk[kPB];
+    Cplx<float> Uk[kPB], Wk[kPB], A0[kPB], A1[kPB], B0[kPB],
+        B1[kPB];
 #pragma unroll
-    for (int u = 0; u < kPairBatch; ++u) {
+    for (int u = 0; u < kPB; ++u) {
       const int k = k0 + u * 2 * NTH;
       if (k <= f.N) {
         const int j = k == 0 ? 0 : L - k;  // (n - k) mod L
@@ -485,7 +494,7 @@ __device__ __forceinline__ void pair_finish(const AssetFft& f, Cplx<float>* s, c
       }
     }
 #pragma unroll
-    for (int u = 0; u < kPairBatch; ++u) {
+    for (int u = 0; u < kPB; ++u) {
       const int k = k0 + u * 2 * NTH;
       if (k <= f.N) {
         const Cplx<float> Zk = cadd(A0[u], cmul(Wk[u], A1[u]));
@@ -508,7 +517,7 @@ __device__ __forceinline__ void pair_finish(const AssetFft& f, Cplx<float>* s, c
 //   Z_k = X_0[k mod L] + w_n^k X_1[k mod L]
 // joins the halves, each CTA reading its partner's X through distributed
 // shared memory while it unpacks and deconvolves every other mode.
-template <int NTH>
+template <int NTH, bool BIG>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
     k_fft_asset_pair(const float* __restrict__ grid, AssetFft f, const Cplx<float>* __restrict__ W,
                      const Cplx<float>* __restrict__ tw, const Cplx<float>* __restrict__ U,
@@ -542,7 +551,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
   }
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
   __syncthreads();
-  pair_finish<NTH>(f, s, anc, c, a, rt, W, U, decon, out);
+  pair_finish<NTH, BIG>(f, s, anc, c, a, rt, W, U, decon, out);
 }
 
 // Stages (a2)-(c) in one launch with the grid row resident in shared
@@ -691,7 +700,7 @@ __global__ void __launch_bounds__(512, 1)
   load_anchors<NTH>(f, tw, anc);
   const RevTab rt = build_rev_tables<NTH>(f, smem_raw, mr);
   __syncthreads();
-  single_finish<NTH>(f, s, anc, a, rt, U, decon, out);
+  single_finish<NTH, true>(f, s, anc, a, rt, U, decon, out);
 }
 
 template <int NT>
@@ -720,7 +729,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
   load_anchors<NTH>(f, tw, anc);
   const RevTab rt = build_rev_tables<NTH>(f, smem_raw, mr);  // none: decimation in time
   __syncthreads();
-  pair_finish<NTH>(f, s, anc, c, a, rt, W, U, decon, out);
+  pair_finish<NTH, true>(f, s, anc, c, a, rt, W, U, decon, out);
 }
 
 // Twiddle anchors of each pass: row j < m_p holds w^1..w^4 of w = w_{L_p}^j,
@@ -819,21 +828,35 @@ cudaError_t launch_spread_fft(const int64_t* off, const int* rb0, const void* rd
   return cudaErrorInvalidValue;
 }
 
+int asset_fft_max_radix(const AssetFft& f) {
+  int r = 1;
+  for (int p = 0; p < f.npass; ++p) r = std::max(r, f.rad[p]);
+  return r;
+}
+
 cudaError_t launch_fft_asset(const float* grid, const AssetFft& f, int D, const void* W, const void* tw,
                              const void* U, const void* decon, void* coeffs, int* status, cudaStream_t s) {
   const size_t smem = asset_fft_smem(f);
-  auto set = [&](auto fn) { return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); };
-  cudaError_t e;
+  auto go = [&](auto fn, dim3 grd, int nth, auto... extra) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(fn, grd, dim3(nth), smem, s, grid, f, (const Cplx<float>*)W, (const Cplx<float>*)tw,
+                      (const Cplx<float>*)U, (const float*)decon, (Cplx<float>*)coeffs, (const int*)(status + 1),
+                      extra...);
+  };
+  // plans of radices up to 16 run a kernel without the larger codelets
+  // (fewer registers); the one-CTA kernel then runs 1024 threads, twice the
+  // warps to hide its shared-memory and barrier latency (measured on the
+  // block workload: 28.5 us with 512 threads and every codelet, 26.7 us
+  // without the large ones, 25.3 us with 1024 threads). The cluster pair
+  // measured fastest with 512 threads and radices up to 32.
+  const bool big = asset_fft_max_radix(f) > 16;
   if (f.pair) {
-    if ((e = set(k_fft_asset_pair<kPairThreads>)) != cudaSuccess) return e;
-    return launch_pdl(k_fft_asset_pair<kPairThreads>, dim3(2, D), dim3(kPairThreads), smem, s, grid, f,
-                      (const Cplx<float>*)W, (const Cplx<float>*)tw, (const Cplx<float>*)U, (const float*)decon,
-                      (Cplx<float>*)coeffs, (const int*)(status + 1));
+    if (big) return go(k_fft_asset_pair<kPairThreads, true>, dim3(2, D), kPairThreads);
+    return go(k_fft_asset_pair<kPairThreads, false>, dim3(2, D), kPairThreads);
   }
-  if ((e = set(k_fft_asset<512>)) != cudaSuccess) return e;
-  return launch_pdl(k_fft_asset<512>, dim3(1, D), dim3(512), smem, s, grid, f, (const Cplx<float>*)W,
-                    (const Cplx<float>*)tw, (const Cplx<float>*)U, (const float*)decon, (Cplx<float>*)coeffs,
-                    (const int*)(status + 1), status);
+  if (big) return go(k_fft_asset<512, true>, dim3(1, D), 512, status);
+  return go(k_fft_asset<1024, false>, dim3(1, D), 1024, status);
 }
 
 }  // namespace mmgpu
