@@ -258,11 +258,14 @@ mm_status mm_estimate(mm_plan plan, const int64_t* d_offsets, const double* d_t,
                       const double* d_logp, int32_t N, double t0, double t1, void* d_coeffs,
                       void* d_sigma_or_null, void* d_R, int32_t* N_used, void* stream);
 
-/* Whole Algorithm 3 from host buffers: copies h_offsets (D+1), h_t and h_logp
- * (h_offsets[D] each, <= max_events) to the plan's device staging buffers,
- * runs mm_estimate, copies Sigma and R (and the coefficients when h_coeffs is
- * not NULL) back, and synchronises the stream before returning. Returns the
- * device status word as mm_plan_sync would. */
+/* Whole Algorithm 3 from host buffers: copies h_offsets (D+1) to the plan's
+ * device staging buffer; h_t and h_logp (h_offsets[D] each, <= max_events)
+ * are read by the kernels in place when both are pinned, mapped host memory
+ * (cudaHostAlloc / cudaMallocHost, or cudaHostRegister) and are copied to
+ * staging buffers otherwise; runs mm_estimate, copies Sigma and R (and the
+ * coefficients when h_coeffs is not NULL) back, and synchronises the stream
+ * before returning. The host buffers must not change until the call returns.
+ * Returns the device status word as mm_plan_sync would. */
 mm_status mm_estimate_host(mm_plan plan, const int64_t* h_offsets, const double* h_t,
                            const double* h_logp, int32_t N, double t0, double t1,
                            void* h_coeffs_or_null, void* h_sigma_or_null, void* h_R,

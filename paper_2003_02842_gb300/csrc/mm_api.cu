@@ -1152,6 +1152,30 @@ mm_status mm_estimate(mm_plan p, const int64_t* d_offsets, const double* d_t, co
                        (cudaStream_t)stream);
 }
 
+// Device address of a host buffer of `bytes` bytes that kernels on device
+// `dev` may read directly: pinned and mapped from its first to its last byte
+// (page-locked memory from cudaHostAlloc or cudaMallocHost, or registered
+// with cudaHostRegister); nullptr for pageable memory or anything else.
+static const void* mapped_alias(const void* h, size_t bytes, int dev) {
+  if (bytes == 0) return nullptr;
+  cudaPointerAttributes a0{}, a1{};
+  if (cudaPointerGetAttributes(&a0, h) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a0.type != cudaMemoryTypeHost || !a0.devicePointer || a0.device != dev) return nullptr;
+  const char* last = static_cast<const char*>(h) + (bytes - 1);
+  if (cudaPointerGetAttributes(&a1, last) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a1.type != cudaMemoryTypeHost || !a1.devicePointer ||
+      static_cast<const char*>(a1.devicePointer) - static_cast<const char*>(a0.devicePointer) !=
+          static_cast<ptrdiff_t>(bytes - 1))
+    return nullptr;
+  return a0.devicePointer;
+}
+
 mm_status mm_estimate_host(mm_plan p, const int64_t* h_offsets, const double* h_t, const double* h_logp, int32_t N,
                            double t0, double t1, void* h_coeffs_or_null, void* h_sigma_or_null, void* h_R,
                            int32_t* N_used, void* stream) {
@@ -1163,12 +1187,27 @@ mm_status mm_estimate_host(mm_plan p, const int64_t* h_offsets, const double* h_
   if (h_offsets[0] != 0 || ne < 0 || ne > p->desc.max_events) return MM_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   MM_CUDA(cudaMemcpyAsync(p->s_off, h_offsets, (size_t)(D + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  // Pinned, mapped event buffers are read by the kernels in place: on GB300
+  // the host link is coherent and the kernels that read the events (bounds,
+  // prep, Nyquist gaps) stream them from host memory at a higher rate than a
+  // staging copy, and without a copy ahead of them. Pageable buffers are
+  // copied to the plan's staging buffers first.
+  const double* dt_ = p->s_t;
+  const double* dp_ = p->s_p;
   if (ne > 0) {
-    MM_CUDA(cudaMemcpyAsync(p->s_t, h_t, (size_t)ne * sizeof(double), cudaMemcpyHostToDevice, st));
-    MM_CUDA(cudaMemcpyAsync(p->s_p, h_logp, (size_t)ne * sizeof(double), cudaMemcpyHostToDevice, st));
+    const size_t eb = (size_t)ne * sizeof(double);
+    const void* at = mapped_alias(h_t, eb, p->dev);
+    const void* ap = at ? mapped_alias(h_logp, eb, p->dev) : nullptr;
+    if (at && ap) {
+      dt_ = static_cast<const double*>(at);
+      dp_ = static_cast<const double*>(ap);
+    } else {
+      MM_CUDA(cudaMemcpyAsync(p->s_t, h_t, eb, cudaMemcpyHostToDevice, st));
+      MM_CUDA(cudaMemcpyAsync(p->s_p, h_logp, eb, cudaMemcpyHostToDevice, st));
+    }
   }
   int32_t Nu = 0;
-  r = mm_estimate(p, p->s_off, p->s_t, p->s_p, N, t0, t1, p->s_coef, p->s_sigma, p->s_R, &Nu, stream);
+  r = mm_estimate(p, p->s_off, dt_, dp_, N, t0, t1, p->s_coef, p->s_sigma, p->s_R, &Nu, stream);
   if (r != MM_OK) {
     cudaStreamSynchronize(st);
     return r;

@@ -285,7 +285,10 @@ def test_bad_offsets_rejected_without_touching_events():
     mm.mm_destroy(plan)
 
 
-def test_host_buffer_entry_point_matches_device_path():
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_entry_point_matches_device_path(pinned):
+    # pinned event buffers are read by the kernels in place, pageable ones
+    # are copied to staging buffers first; repeated calls replay the graph
     import torch
     import paper_2003_02842_gb300 as mm
     ev = synth.c2_async(2)
@@ -293,19 +296,30 @@ def test_host_buffer_entry_point_matches_device_path():
     plan = mm.mm_plan_create(D=2, N_max=N, max_events=ev.n_events, tol=1e-6, kernel="es", prec="bf16x3")
     off, t, p = to_dev(ev)
     F, S, R, _ = mm.mm_estimate(plan, off, t, p, N)
-    hoff = torch.from_numpy(ev.offsets).pin_memory()
-    ht = torch.from_numpy(ev.t).pin_memory()
-    hp = torch.from_numpy(ev.logp).pin_memory()
+    pin = (lambda x: x.pin_memory()) if pinned else (lambda x: x)
+    hoff = pin(torch.from_numpy(ev.offsets.copy()))
+    ht = pin(torch.from_numpy(ev.t.copy()))
+    hp = pin(torch.from_numpy(ev.logp.copy()))
     hR = torch.empty((2, 2), dtype=torch.float32).pin_memory()
     hS = torch.empty((2, 2), dtype=torch.float32).pin_memory()
     hF = torch.empty((2, N + 1), dtype=torch.complex64).pin_memory()
-    st, Nu = mm.mm_estimate_host(plan, hoff, ht, hp, N, coeffs=hF, sigma=hS, R=hR)
-    assert st == 0 and Nu == N
-    # shared-memory atomics make the FP32 spreading order vary between runs,
-    # so the two paths agree to rounding, not bit for bit
-    assert torch.allclose(hF, F.cpu(), rtol=0, atol=1e-6 * float(F.abs().max()))
-    assert torch.allclose(hS, S.cpu(), rtol=1e-5, atol=0)
-    assert torch.allclose(hR, R.cpu(), rtol=0, atol=1e-6)
+    for _ in range(3):
+        hR.zero_()
+        st, Nu = mm.mm_estimate_host(plan, hoff, ht, hp, N, coeffs=hF, sigma=hS, R=hR)
+        assert st == 0 and Nu == N
+        # shared-memory atomics make the FP32 spreading order vary between runs,
+        # so the two paths agree to rounding, not bit for bit
+        assert torch.allclose(hF, F.cpu(), rtol=0, atol=1e-6 * float(F.abs().max()))
+        assert torch.allclose(hS, S.cpu(), rtol=1e-5, atol=0)
+        assert torch.allclose(hR, R.cpu(), rtol=0, atol=1e-6)
+    # new data in the same pinned buffers: the in-place reads see it
+    ht2 = torch.from_numpy(ev.t.copy())
+    hp2 = torch.from_numpy(ev.logp[::-1].copy())
+    hp.copy_(hp2)
+    st, _ = mm.mm_estimate_host(plan, hoff, ht, hp, N, coeffs=hF, sigma=hS, R=hR)
+    assert st == 0
+    ref = oracle.coeffs_F(ev.offsets, ht2.numpy(), hp2.numpy(), N)
+    assert np.all(rel_l2_rows(hF.numpy(), ref) <= TOL["bf16x3"]["coef"])
     mm.mm_destroy(plan)
 
 
