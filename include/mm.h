@@ -262,9 +262,11 @@ mm_status mm_estimate(mm_plan plan, const int64_t* d_offsets, const double* d_t,
  * device staging buffer; h_t and h_logp (h_offsets[D] each, <= max_events)
  * are read by the kernels in place when both are pinned, mapped host memory
  * (cudaHostAlloc / cudaMallocHost, or cudaHostRegister) and are copied to
- * staging buffers otherwise; runs mm_estimate, copies Sigma and R (and the
- * coefficients when h_coeffs is not NULL) back, and synchronises the stream
- * before returning. The host buffers must not change until the call returns.
+ * staging buffers otherwise; runs mm_estimate; Sigma and R are written in
+ * place when their buffers are pinned and mapped, else copied back (the
+ * coefficients, when h_coeffs is not NULL, are always copied back); and
+ * synchronises the stream before returning. The host buffers must not
+ * change (inputs) or be read (outputs) until the call returns.
  * Returns the device status word as mm_plan_sync would. */
 mm_status mm_estimate_host(mm_plan plan, const int64_t* h_offsets, const double* h_t,
                            const double* h_logp, int32_t N, double t0, double t1,

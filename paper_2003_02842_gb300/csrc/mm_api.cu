@@ -1206,15 +1206,22 @@ mm_status mm_estimate_host(mm_plan p, const int64_t* h_offsets, const double* h_
       MM_CUDA(cudaMemcpyAsync(p->s_p, h_logp, eb, cudaMemcpyHostToDevice, st));
     }
   }
+  // pinned, mapped Sigma and R buffers are written by the correlation
+  // epilogue in place; the coefficients stay in device memory (the
+  // contraction reads them back) and are copied out when asked for
+  const size_t dd = (size_t)D * D * p->rs;
+  void* oR = const_cast<void*>(mapped_alias(h_R, dd, p->dev));
+  void* oS = h_sigma_or_null ? const_cast<void*>(mapped_alias(h_sigma_or_null, dd, p->dev)) : nullptr;
   int32_t Nu = 0;
-  r = mm_estimate(p, p->s_off, dt_, dp_, N, t0, t1, p->s_coef, p->s_sigma, p->s_R, &Nu, stream);
+  r = mm_estimate(p, p->s_off, dt_, dp_, N, t0, t1, p->s_coef, oS ? oS : p->s_sigma, oR ? oR : p->s_R, &Nu,
+                  stream);
   if (r != MM_OK) {
     cudaStreamSynchronize(st);
     return r;
   }
-  const size_t dd = (size_t)D * D * p->rs;
-  MM_CUDA(cudaMemcpyAsync(h_R, p->s_R, dd, cudaMemcpyDeviceToHost, st));
-  if (h_sigma_or_null) MM_CUDA(cudaMemcpyAsync(h_sigma_or_null, p->s_sigma, dd, cudaMemcpyDeviceToHost, st));
+  if (!oR) MM_CUDA(cudaMemcpyAsync(h_R, p->s_R, dd, cudaMemcpyDeviceToHost, st));
+  if (h_sigma_or_null && !oS)
+    MM_CUDA(cudaMemcpyAsync(h_sigma_or_null, p->s_sigma, dd, cudaMemcpyDeviceToHost, st));
   if (h_coeffs_or_null)
     MM_CUDA(cudaMemcpyAsync(h_coeffs_or_null, p->s_coef, (size_t)D * (Nu + 1) * p->cs, cudaMemcpyDeviceToHost, st));
   if (N_used) *N_used = Nu;
