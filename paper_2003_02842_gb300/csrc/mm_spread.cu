@@ -68,6 +68,25 @@ __global__ void k_bounds(const int64_t* __restrict__ off, const double* __restri
     }
     return;
   }
+  // 2) t_min / t_max from each asset's first and last event (Algorithm 4);
+  //    the first asset's two times are loaded before the ranking below and
+  //    used after it, so that the load latency overlaps the ranking
+  const bool window = w1 > w0;
+  double lo = INFINITY, hi = -INFINITY;
+  int outwin = 0;
+  double f0 = INFINITY, l0 = -INFINITY;
+  bool has0 = false;
+  {
+    const int i = i0 + (int)threadIdx.x;
+    if (i < i1) {
+      const int64_t a = off[i], b = off[i + 1];
+      if (b > a) {
+        f0 = t[a];
+        l0 = t[b - 1];
+        has0 = true;
+      }
+    }
+  }
   // the spreading tiles' dispatch order: assets ranked by event count,
   // heaviest first (ties by index), so that the longest tiles start first
   if (order) {  // uniform: a single problem, D <= kOrderMaxAssets
@@ -87,11 +106,12 @@ __global__ void k_bounds(const int64_t* __restrict__ off, const double* __restri
       order[r] = i;
     }
   }
-  // 2) t_min / t_max from each asset's first and last event (Algorithm 4)
-  const bool window = w1 > w0;
-  double lo = INFINITY, hi = -INFINITY;
-  int outwin = 0;
-  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+  if (has0) {
+    lo = fmin(lo, f0);
+    hi = fmax(hi, l0);
+    if (window && (f0 < w0 || l0 > w1)) outwin = 1;
+  }
+  for (int i = i0 + (int)threadIdx.x + (int)blockDim.x; i < i1; i += blockDim.x) {
     const int64_t a = off[i], b = off[i + 1];
     if (b > a) {
       const double f = t[a], l = t[b - 1];
