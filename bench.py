@@ -138,6 +138,8 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison path")
     ap.add_argument("--spread-algo", default="default", choices=["default", "scatter", "gather", "fused"])
+    ap.add_argument("--fft-algo", default="default", choices=["default", "two_pass", "asset", "asset_pair", "asset_perm"],
+                    help="c3: stages (b)-(c) variant (default: the library's choice)")
     ap.add_argument("--autotune", action="store_true",
                     help="time the library's spreading / FFT variants on this workload first and keep the fastest "
                          "(off by default: the default configuration is deterministic, so a profiler run of the "
@@ -746,7 +748,8 @@ def main():
     D = ev.D
     tol = 1e-12 if args.prec == "fp64" else 1e-6
     plan = mm.mm_plan_create(D=D, N_max=N, max_events=ev.n_events, tol=tol, kernel=args.kernel,
-                             basis="dirichlet", prec=args.prec, spread_algo=args.spread_algo)
+                             basis="dirichlet", prec=args.prec, spread_algo=args.spread_algo,
+                             fft_algo=args.fft_algo)
     coef = torch.empty((D, N + 1), dtype=torch.complex128 if args.prec == "fp64" else torch.complex64, device=dev)
     rdt = torch.float64 if args.prec == "fp64" else torch.float32
     S = torch.empty((D, D), dtype=rdt, device=dev)
