@@ -324,17 +324,18 @@ def test_host_buffer_entry_point_matches_device_path(pinned):
 
 
 def test_one_cta_plan_with_a_radix_above_16():
-    # n = 3125 = 5^5 has no four-pass plan of radices up to 16 (5, 5, 5, 25):
+    # the grid n is the smallest even 5-smooth number >= 2N + 1: n = 6250 =
+    # 2 5^5 has no four-pass plan of radices up to 16 (it takes 25, 25, 10):
     # the one-CTA kernel with the large codelets; the other tests' plans run
     # the kernel without them
     ev = synth.random_events(14, D=3, n_range=(200, 1500), T=5000.0)
-    N = 1550
+    N = 3100
     tl = TOL["bf16x3"]
     ref = oracle.coeffs_F(ev.offsets, ev.t, ev.logp, N)
     for kernel in ("gauss", "es"):
         out = run(dict(tol=tl["tol"], kernel=kernel, basis="dirichlet", prec="bf16x3"), ev, N)
         info = out["info"]
-        assert info["Mr"] == 6250 and info["fft_algo"] == 0 and info["fft_split"] == 1, info
+        assert info["Mr"] == 12500 and info["fft_algo"] == 0 and info["fft_split"] == 1, info
         assert max(info["fft_radix"]) > 16, info["fft_radix"]
         assert np.all(rel_l2_rows(out["F"], ref) <= tl["coef"])
 
