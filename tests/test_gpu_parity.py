@@ -285,6 +285,37 @@ def test_bad_offsets_rejected_without_touching_events():
     mm.mm_destroy(plan)
 
 
+def test_host_buffer_entry_point_with_registered_memory_and_fp64():
+    # events in page-locked memory registered by the caller (cudaHostRegister)
+    # are read in place like memory from cudaHostAlloc; the FP64 path too
+    import torch
+    import paper_2003_02842_gb300 as mm
+    ev = synth.c2_async(3)
+    N = ev.meta["N"]
+    t = np.ascontiguousarray(ev.t.copy())
+    lp = np.ascontiguousarray(ev.logp.copy())
+    cr = torch.cuda.cudart()
+    for arr in (t, lp):
+        assert int(cr.cudaHostRegister(arr.ctypes.data, arr.nbytes, 0)) == 0
+    try:
+        for prec, tl in (("fp64", TOL["fp64"]), ("bf16x3", TOL["bf16x3"])):
+            plan = mm.mm_plan_create(D=2, N_max=N, max_events=ev.n_events, tol=tl["tol"], kernel="es", prec=prec)
+            dt = torch.float64 if prec == "fp64" else torch.float32
+            ct = torch.complex128 if prec == "fp64" else torch.complex64
+            hR = torch.empty((2, 2), dtype=dt)
+            hF = torch.empty((2, N + 1), dtype=ct)
+            st, Nu = mm.mm_estimate_host(plan, torch.from_numpy(ev.offsets.copy()), torch.from_numpy(t),
+                                         torch.from_numpy(lp), N, coeffs=hF, R=hR)
+            assert st == 0 and Nu == N
+            ref = oracle.estimate(ev.offsets, ev.t, ev.logp, N=N, basis="dirichlet")
+            assert np.all(rel_l2_rows(hF.numpy(), ref["F"]) <= tl["coef"])
+            assert np.max(np.abs(hR.numpy().astype(np.float64) - ref["R"])) <= tl["R"]
+            mm.mm_destroy(plan)
+    finally:
+        for arr in (t, lp):
+            cr.cudaHostUnregister(arr.ctypes.data)
+
+
 @pytest.mark.parametrize("pinned", [True, False])
 def test_host_buffer_entry_point_matches_device_path(pinned):
     # pinned event buffers are read by the kernels in place, pageable ones
