@@ -476,6 +476,35 @@ def test_full_size_block_workload_in_the_bench_configuration():
     torch.cuda.synchronize()
 
 
+def test_paper_timing_configuration_at_full_size():
+    # the paper's own timing case: two synchronous assets of n = 10^5 points
+    # at N = n/2 (ES at 1e-12 on the FP64 path, at 1e-6 on the mixed path;
+    # grids of M_r = 2e5, beyond one CTA's shared memory, so the two-pass
+    # FFT): every coefficient against the direct sum, R against the oracle's
+    # contraction of the oracle's coefficients, both bases
+    import paper_2003_02842_gb300 as mm
+    ev = synth.c1_sync(0, n=100000)
+    N = 50000
+    off, t, p = to_dev(ev)
+    Fo = oracle.coeffs_F(ev.offsets, ev.t, ev.logp, N)
+    c = np.concatenate([np.conj(Fo[:, :0:-1]), Fo], axis=1) * (2 * np.pi)
+    for basis in ("dirichlet", "fejer"):
+        So, _ = oracle.cov_from_coeffs(c, N, basis)
+        Ro = oracle.corr(So)
+        for prec in ("fp64", "bf16x3"):
+            tl = TOL[prec]
+            plan = mm.mm_plan_create(D=2, N_max=N, max_events=ev.n_events, tol=tl["tol"], kernel="es",
+                                     basis=basis, prec=prec)
+            F, S, R, _ = mm.mm_estimate(plan, off, t, p, N)
+            assert mm.mm_plan_sync(plan) == 0
+            assert mm.mm_plan_get_info(plan)["fft_algo"] == 1
+            err = rel_l2_rows(F.cpu().numpy(), Fo)
+            assert np.all(err <= tl["coef"]), (prec, basis, err.max())
+            assert sigma_err(S.cpu().numpy(), So) <= tl["sig"], (prec, basis)
+            assert np.max(np.abs(R.cpu().numpy().astype(np.float64) - Ro)) <= tl["R"], (prec, basis)
+            mm.mm_destroy(plan)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3", "3xtf32"])
 @pytest.mark.parametrize("D", [3, 40, 150])
 def test_covariance_call_without_correlation(prec, D):
